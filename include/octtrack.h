@@ -1,0 +1,270 @@
+/*
+ * octtrack.h -- C ABI of the GB300 octree Lagrangian-Eulerian coupling library.
+ *
+ * The library locates Lagrangian points (IBM markers and point particles) in a 2:1
+ * balanced linear octree stored as a Morton-sorted array of leaves, interpolates a
+ * cell-centred velocity field to them, and spreads marker forces back to the cells as the
+ * exact adjoint of the interpolation.
+ *
+ * Conventions (every entry point):
+ *   - Pointers prefixed d_ are device pointers owned and allocated by the caller; h_ are
+ *     host pointers.  The library owns what it creates (octrees, indexes, batches) and
+ *     frees it in the matching *_destroy call.
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Calls are asynchronous on
+ *     it unless stated otherwise; outputs are valid once the stream has reached them.
+ *   - Arguments are validated on the host; a bad argument returns OT_ERR_ARG and launches
+ *     nothing.  No C++ exception crosses this boundary.
+ *   - Output order always equals input order.
+ *   - Device-side findings (a point outside the unit cube, a stencil cell that is not a
+ *     finest-level leaf, a bounded loop that reached its cap) never trap: they set bits
+ *     of a per-octree error word that ot_last_error() reads after a stream sync.
+ *
+ * Geometry: one tree, the unit cube [0,1)^3.  Integer coordinates have 21 bits per axis
+ * (MAXLEVEL = 21), so a Morton key (x bit b -> key bit 3b, y -> 3b+1, z -> 3b+2) fits in
+ * 63 bits.  A leaf of level l at integer cell (i,j,k) covers [i,i+1)x[j,j+1)x[k,k+1)/2^l and
+ * is stored by its anchor key morton(i<<(21-l), j<<(21-l), k<<(21-l)) and its level.
+ * (The paper's Algorithm 1 uses p4est's 2-D MAXLEVEL = 30; 21 is the 3-D 64-bit value.)
+ */
+#ifndef OCTTRACK_H
+#define OCTTRACK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ot_octree ot_octree;
+typedef struct ot_batch ot_batch;
+
+typedef enum {
+    OT_OK = 0,
+    OT_ERR_ARG = -1,        /* invalid argument (null pointer, size, enum value)          */
+    OT_ERR_CUDA = -2,       /* a CUDA runtime call failed                                  */
+    OT_ERR_OOM = -3,        /* device allocation failed                                    */
+    OT_ERR_UNSORTED = -4,   /* leaves not strictly increasing / not aligned / not a tiling */
+    OT_ERR_UNBALANCED = -5, /* leaves violate the requested 2:1 balance                    */
+    OT_ERR_NOT_FOUND = -6,  /* reserved                                                    */
+    OT_ERR_STENCIL = -7,    /* reserved for callers that turn error bits into a status     */
+    OT_ERR_LIMIT = -8,      /* a size exceeds a documented limit                           */
+    OT_ERR_NO_INDEX = -9    /* OT_LEARNED requested before ot_index_train                  */
+} ot_status;
+
+/* interpolation / spreading kernels */
+enum { OT_TRILINEAR = 1, OT_PESKIN4 = 2, OT_ROMA3 = 3 };
+/* host-cell search */
+enum { OT_BINARY = 0, OT_LEARNED = 1 };
+/* spreading modes */
+enum { OT_SORTED = 0, OT_ATOMIC = 1 };
+/* learned-index root model */
+enum { OT_ROOT_LINEAR = 0, OT_ROOT_MLP = 1 };
+/* bits of the device error word */
+enum {
+    OT_DEV_OUTSIDE = 1u,     /* a point outside [0,1)^3 or NaN (host = -1)                   */
+    OT_DEV_STENCIL = 2u,     /* a delta-kernel stencil cell outside the domain or not a leaf
+                                of the finest level: its weight was dropped                */
+    OT_DEV_REFINED_CAP = 4u, /* a refined level-mate held more leaves than the averaging cap */
+    OT_DEV_WINDOW = 8u       /* a learned prediction missed; plain search answered instead  */
+};
+
+/* Limits. */
+#define OT_MAX_LEAVES 2000000000LL /* leaf indices are int32 */
+#define OT_MAX_SPHERES 4096
+#define OT_MAX_LEVEL 20            /* lmax; keys need 3*lmax <= 63 bits and one spare level  */
+#define OT_REFINED_CAP 4096        /* leaves averaged for one refined level-mate (trilinear) */
+
+/* A refinement sphere: cells whose closed box lies within `shell` of the sphere surface
+ * |p - c| = r are refined (Sec. 3.1 refinement; Sec. 3.3 auxiliary IBM forest). */
+typedef struct {
+    double c[3];
+    double r;
+    double shell;
+} ot_sphere;
+
+typedef struct {
+    int lmin, lmax;   /* 0 <= lmin <= lmax <= OT_MAX_LEVEL                                  */
+    int balance_full; /* 1: face+edge+corner 2:1 balance; 0: face-only balance               */
+} ot_build_params;
+
+/* ---------------------------------------------------------------------------------------
+ * Octree
+ * -------------------------------------------------------------------------------------*/
+
+/* Build the leaves on the device (Sec. 3.1: refine / balance; Sec. 3.3: refinement driven
+ * only by proximity to the IBM surfaces): start from the uniform level lmin, split a cell
+ * of level < lmax whenever the FP64 distance from its closed box to some sphere surface,
+ * max(0, d_near - r, r - d_far), is <= shell; then add the fewest splits that make any two
+ * adjacent leaves differ by at most one level.  Leaves come out Morton-sorted.
+ * h_spheres: n host records (0 <= n <= OT_MAX_SPHERES).  Synchronises the stream (sizes
+ * are read back).  *out receives a new octree; free it with ot_octree_destroy. */
+ot_status ot_octree_build(const ot_sphere* h_spheres, int n, const ot_build_params* params, void* stream,
+                          ot_octree** out);
+
+/* Adopt caller leaves (copied): d_keys strictly increasing anchor keys, d_levels their
+ * levels; they must tile the unit cube (OT_ERR_UNSORTED otherwise) and satisfy the 2:1
+ * balance named by balance_full (OT_ERR_UNBALANCED otherwise).  Synchronises the stream. */
+ot_status ot_octree_from_leaves(const uint64_t* d_keys, const uint8_t* d_levels, int64_t n, int balance_full,
+                                void* stream, ot_octree** out);
+
+/* Leaf count and level range. */
+ot_status ot_octree_info(const ot_octree* t, int64_t* n_leaves, int* lmin, int* lmax);
+
+/* Device pointers to the library-owned leaf arrays (valid until ot_octree_destroy). */
+ot_status ot_octree_leaves(const ot_octree* t, int64_t* n, const uint64_t** d_keys, const uint8_t** d_levels);
+
+/* Copy the leaves into caller buffers (d_keys: N uint64, d_levels: N uint8; either may be
+ * NULL), asynchronously on stream. */
+ot_status ot_octree_copy_leaves(const ot_octree* t, uint64_t* d_keys, uint8_t* d_levels, void* stream);
+
+/* Leaf centres, FP64, written as 3 planes of N (x..., y..., z...). */
+ot_status ot_octree_centres(const ot_octree* t, double* d_xyz, void* stream);
+
+ot_status ot_octree_destroy(ot_octree* t);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned index (not in the paper; a two-stage recursive model index after Kraska et al.,
+ * SIGMOD 2018): a root model maps a key to one of n_leaf_models linear models; each leaf
+ * model predicts the key's position in the leaf array and stores the maximum error of
+ * that prediction over the stored keys.  A query searches only the error window, verifies
+ * the answer and falls back to the plain binary search, so results are bit-identical to it.
+ * -------------------------------------------------------------------------------------*/
+
+typedef struct {
+    int root;          /* OT_ROOT_LINEAR or OT_ROOT_MLP (1 -> 32 ReLU -> 1)                    */
+    int n_leaf_models; /* 1 .. 1<<20; 4096 is the usual choice                               */
+    int epochs;        /* MLP root: training length; an epoch is min(N / batch, 512) Adam steps */
+    int batch;         /* MLP root: minibatch size                                           */
+    float lr;          /* MLP root: Adam step size                                           */
+    uint64_t seed;     /* MLP root: minibatch sampling                                       */
+} ot_index_params;
+
+/* Train on the device over the octree's keys; replaces a previous index.  Synchronises. */
+ot_status ot_index_train(ot_octree* t, const ot_index_params* params, void* stream);
+
+/* Index statistics (host values): mean and max window length over the leaf models,
+ * number of empty models, and learned-query fallbacks counted since the last reset. */
+typedef struct {
+    double mean_window;
+    int64_t max_window;
+    int64_t empty_models;
+    uint64_t fallbacks;
+    float final_loss; /* MLP root: last minibatch loss (0 for a linear root) */
+} ot_index_stats;
+ot_status ot_index_get_stats(const ot_octree* t, ot_index_stats* s, int reset_fallbacks);
+
+/* Root network hooks for gradient checks: loss and gradient of the MSE loss of params
+ * (97 floats: w1[32], b1[32], w2[32], b2) over n samples (d_x, d_t), on the device.
+ * d_grad: 97 floats; d_loss: 1 float. */
+ot_status ot_index_mlp_grad(const float* d_params, const float* d_x, const float* d_t, int64_t n, float* d_grad,
+                            float* d_loss, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Locate / interpolate / spread
+ * -------------------------------------------------------------------------------------*/
+
+/* Host-cell search (Algorithm 1, Sec. 3.2): d_host[i] = the leaf whose half-open box holds
+ * point i, i.e. the last leaf whose anchor key <= the point's key at MAXLEVEL, computed from
+ * floor(x 2^21) in FP64 so that points on a face go to the upper cell.  A point outside
+ * [0,1)^3 or NaN gets -1 and, when d_n_miss is not NULL, increments *d_n_miss.
+ * search: OT_BINARY or OT_LEARNED (OT_ERR_NO_INDEX without a trained index). */
+ot_status ot_locate(const ot_octree* t, const double* d_x, const double* d_y, const double* d_z, int64_t n,
+                    int search, int32_t* d_host, unsigned long long* d_n_miss, void* stream);
+
+/* Interpolation of a cell-centred field (float4 per leaf: x, y, z, unused) to n points.
+ *   OT_TRILINEAR (Sec. 2.3.2): the host leaf (level l) and its 7 level-mates, the cells
+ *     c + {0, s_d} per axis where s_d = sign of the offset from the host centre; a
+ *     level-mate inside a coarser leaf takes that leaf's value, a refined one the
+ *     volume-weighted mean of its leaves, one outside the cube the host's index on that axis.
+ *   OT_PESKIN4 / OT_ROMA3 (Sec. 2.2, Eq. ibm_interpolate): u(X) = sum over the 4^3 / 3^3
+ *     finest-level cells around X of phi(rx) phi(ry) phi(rz) u(cell); Peskin's 4-point or
+ *     the paper's 3-point function.  Cells outside the cube or not finest-level leaves are
+ *     dropped and flagged (OT_DEV_STENCIL).
+ * d_u: 3 planes of n floats.  d_host_in: host leaves from ot_locate, or NULL to locate
+ * here (search selects how); d_host_out (nullable) receives them.  For the delta kernels the
+ * host is the finest cell holding X when that cell is a leaf, else a plain search result. */
+ot_status ot_interpolate(const ot_octree* t, int kernel, const double* d_x, const double* d_y, const double* d_z,
+                         int64_t n, const int32_t* d_host_in, int search, const float* d_field, float* d_u,
+                         int32_t* d_host_out, void* stream);
+
+/* FP64 variant: d_field is N x 4 doubles, d_u 3 planes of n doubles; weights in FP64. */
+ot_status ot_interpolate_f64(const ot_octree* t, int kernel, const double* d_x, const double* d_y,
+                             const double* d_z, int64_t n, const int32_t* d_host_in, int search,
+                             const double* d_field, double* d_u, int32_t* d_host_out, void* stream);
+
+/* Workspace for OT_SORTED spreading of n markers with the given kernel. */
+ot_status ot_spread_workspace_size(const ot_octree* t, int kernel, int64_t n, size_t* bytes);
+
+/* Force spreading, the exact adjoint of the delta-kernel interpolation (Sec. 2.2, Eq. for
+ * F(x)): f(cell) += sum_k F_k phi phi phi dV_k / h^3, h = 2^-lmax, dV_k = h^3 when d_dV is
+ * NULL (the paper's literal form).  d_F: 3 planes of n floats; d_f: float4 per leaf,
+ * ACCUMULATED (the caller zeroes it), component w untouched.
+ *   OT_SORTED: pairs (leaf, marker, stencil slot) are radix-sorted by leaf (stable) and each
+ *     leaf sums its contributions in marker order: bit-identical run to run.
+ *     Needs d_workspace of ot_spread_workspace_size bytes (16-byte aligned).
+ *   OT_ATOMIC: float atomics; order varies run to run.  d_workspace may be NULL. */
+ot_status ot_spread(const ot_octree* t, int kernel, int mode, const double* d_x, const double* d_y,
+                    const double* d_z, const float* d_F, const float* d_dV, int64_t n, float* d_f,
+                    void* d_workspace, size_t ws_bytes, void* stream);
+
+/* FP64 variant: d_F 3 planes of n doubles, d_dV n doubles or NULL, d_f N x 4 doubles. */
+ot_status ot_spread_f64(const ot_octree* t, int kernel, int mode, const double* d_x, const double* d_y,
+                        const double* d_z, const double* d_F, const double* d_dV, int64_t n, double* d_f,
+                        void* d_workspace, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched launch: every group of points (IBM markers with a delta kernel, point particles
+ * with trilinear) located and interpolated by ONE persistent kernel, captured once in a
+ * CUDA graph and replayed.
+ * -------------------------------------------------------------------------------------*/
+
+typedef struct {
+    int kernel;           /* OT_TRILINEAR, OT_PESKIN4 or OT_ROMA3                          */
+    const double *d_x, *d_y, *d_z;
+    int64_t n;
+    float* d_u;           /* 3 planes of n                                                 */
+    int32_t* d_host;      /* nullable                                                      */
+} ot_group;
+
+/* Launch shape of the batched kernel (0 = library default). */
+typedef struct {
+    int block;       /* threads per block: 64 .. 1024, multiple of 32                       */
+    int tile;        /* points per work item fetched from the queue                         */
+    int blocks_per_sm;
+    int stage_log2;  /* plain search: log2 of the shared-memory sample of top-level keys     */
+} ot_launch;
+
+/* Create a batch over groups (copied) reading d_field (float4 per leaf).  search selects
+ * the host-cell search.  launch may be NULL.  Captures the graph on `stream`. */
+ot_status ot_batch_create(const ot_octree* t, const ot_group* groups, int n_groups, const float* d_field,
+                          int search, const ot_launch* launch, void* stream, ot_batch** out);
+ot_status ot_batch_run(ot_batch* b, void* stream);
+ot_status ot_batch_destroy(ot_batch* b);
+
+/* ---------------------------------------------------------------------------------------
+ * Point-particle advection (Sec. 2.3.2, Eq. PointParticle, gravity off): per particle
+ *   a = f_p (u - v)/tau, f_p = 1 + 0.15 (re_coef |u - v|)^0.687 (re_coef = 0: f_p = 1),
+ *   v += dt (3/2 a - 1/2 a_prev), x += dt (3/2 v_old - 1/2 v_prev); Euler when first != 0.
+ * d_x: 3 planes of n doubles (positions, FP64); d_v, d_a_prev, d_v_prev: 3 planes of n
+ * floats; d_u: 3 planes of n floats (interpolated fluid velocity).
+ * -------------------------------------------------------------------------------------*/
+ot_status ot_advect_ab2(double* d_x, float* d_v, float* d_a_prev, float* d_v_prev, const float* d_u, int64_t n,
+                        float tau, float re_coef, float dt, int first, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Diagnostics
+ * -------------------------------------------------------------------------------------*/
+
+/* Device error word of the octree (OT_DEV_* bits) accumulated since the last clear.
+ * Synchronises the stream.  clear != 0 zeroes it afterwards. */
+ot_status ot_last_error(const ot_octree* t, unsigned* bits, int clear, void* stream);
+
+/* Kernels this library has launched since load (a process-wide counter). */
+uint64_t ot_launch_count(void);
+
+const char* ot_status_string(ot_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCTTRACK_H */

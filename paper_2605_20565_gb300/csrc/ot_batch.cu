@@ -1,0 +1,189 @@
+// ot_batch.cu -- one persistent launch over every group of points (IBM markers with a delta
+// kernel, point particles with trilinear interpolation), replayed from a CUDA graph.
+//
+// Work is cut into tiles of 32 * tile points; warps take tiles from a global counter, the
+// expensive marker groups first (their tiles come first in the tile space), so uneven groups
+// balance across the SMs without a host round trip.  The counter is reset by a memset node
+// captured in the same graph.
+#include <algorithm>
+#include <vector>
+
+#include "ot_internal.h"
+#include "ot_points.cuh"
+
+struct ot_batch {
+    const ot_octree* tree = nullptr;
+    int n_groups = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned* d_counter = nullptr;
+    uint64_t* d_sample = nullptr;
+};
+
+namespace ot {
+
+constexpr int MAX_GROUPS = 16;
+
+struct GroupDev {
+    int kernel;
+    const double *x, *y, *z;
+    int64_t n;
+    float* u;
+    int32_t* host;
+    int64_t tile0; // first tile of the group
+};
+
+struct BatchArgs {
+    GroupDev g[MAX_GROUPS];
+    int ng;
+    int64_t ntiles;
+    int tile; // points per lane per tile
+};
+
+template <bool LEARNED>
+__global__ void __launch_bounds__(256) k_batch(TreeView t, RootModel rm, BatchArgs a, const float* __restrict__ field,
+                                               unsigned* __restrict__ counter) {
+    extern __shared__ uint64_t s_sample[];
+    const bool staged = !LEARNED && t.nsample > 1;
+    if (staged) load_sample(t, s_sample);
+    const uint64_t* ss = staged ? s_sample : nullptr;
+    const int lane = threadIdx.x & 31;
+    const int64_t tile_pts = 32 * (int64_t)a.tile;
+    for (;;) {
+        unsigned tl = 0;
+        if (lane == 0) tl = atomicAdd(counter, 1u);
+        tl = __shfl_sync(0xffffffffu, tl, 0);
+        if ((int64_t)tl >= a.ntiles) break;
+        int g = 0;
+        while (g + 1 < a.ng && (int64_t)tl >= a.g[g + 1].tile0) ++g;
+        const GroupDev& gr = a.g[g];
+        const int64_t base = ((int64_t)tl - gr.tile0) * tile_pts;
+        for (int j = 0; j < a.tile; ++j) {
+            const int64_t i = base + (int64_t)j * 32 + lane;
+            if (i >= gr.n) break;
+            float o[3];
+            int h;
+            const double x = gr.x[i], y = gr.y[i], z = gr.z[i];
+            if (gr.kernel == OT_TRILINEAR)
+                h = trilinear_point<float, LEARNED>(t, rm, ss, field, x, y, z, -1, o);
+            else if (gr.kernel == OT_PESKIN4)
+                h = delta_point<float, OT_PESKIN4, LEARNED>(t, rm, ss, field, x, y, z, gr.host != nullptr, o);
+            else
+                h = delta_point<float, OT_ROMA3, LEARNED>(t, rm, ss, field, x, y, z, gr.host != nullptr, o);
+            gr.u[i] = o[0];
+            gr.u[gr.n + i] = o[1];
+            gr.u[2 * gr.n + i] = o[2];
+            if (gr.host) gr.host[i] = h;
+        }
+    }
+}
+
+__global__ void k_batch_sample(const uint64_t* __restrict__ key, int nsample, int stride, uint64_t* __restrict__ out) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nsample; b += gridDim.x * blockDim.x)
+        out[b] = key[(int64_t)b * stride];
+}
+
+} // namespace ot
+
+using namespace ot;
+
+extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups, int n_groups, const float* d_field,
+                                     int search, const ot_launch* launch, void* stream, ot_batch** out) {
+    if (!t || !groups || !out || !d_field || n_groups < 1 || n_groups > MAX_GROUPS) return OT_ERR_ARG;
+    if (search != OT_BINARY && search != OT_LEARNED) return OT_ERR_ARG;
+    if (search == OT_LEARNED && !t->has_index) return OT_ERR_NO_INDEX;
+    *out = nullptr;
+    const int block = (launch && launch->block) ? launch->block : 256;
+    const int tile = (launch && launch->tile) ? launch->tile : 4;
+    const int stage = (launch && launch->stage_log2) ? launch->stage_log2 : t->stage_log2;
+    if (block < 64 || block > 256 || block % 32 || tile < 1 || tile > 64 || stage < 1 || stage > 14) return OT_ERR_ARG;
+    BatchArgs a{};
+    a.ng = n_groups;
+    a.tile = tile;
+    // delta-kernel groups first: the longest work is taken first
+    std::vector<int> order;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int g = 0; g < n_groups; ++g)
+            if ((groups[g].kernel != OT_TRILINEAR) == (pass == 0)) order.push_back(g);
+    int64_t tile0 = 0;
+    for (int k = 0; k < n_groups; ++k) {
+        const ot_group& gi = groups[order[k]];
+        if (gi.kernel != OT_TRILINEAR && gi.kernel != OT_PESKIN4 && gi.kernel != OT_ROMA3) return OT_ERR_ARG;
+        if (gi.n < 0 || (gi.n > 0 && (!gi.d_x || !gi.d_y || !gi.d_z || !gi.d_u))) return OT_ERR_ARG;
+        if (gi.kernel != OT_TRILINEAR && t->lmax < 1) return OT_ERR_ARG;
+        GroupDev& d = a.g[k];
+        d = GroupDev{gi.kernel, gi.d_x, gi.d_y, gi.d_z, gi.n, gi.d_u, gi.d_host, tile0};
+        tile0 += (gi.n + 32 * (int64_t)tile - 1) / (32 * (int64_t)tile);
+    }
+    a.ntiles = tile0;
+    if (a.ntiles >= (1LL << 32)) return OT_ERR_LIMIT;
+
+    ot_batch* b = new ot_batch();
+    b->tree = t;
+    b->n_groups = n_groups;
+    cudaStream_t cs = nullptr;
+    auto fail = [&](cudaError_t e) {
+        if (cs) cudaStreamDestroy(cs);
+        ot_batch_destroy(b);
+        return cuda_status(e);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned))) != cudaSuccess) return fail(e);
+    TreeView v = tree_view(t, search != OT_LEARNED);
+    if (search != OT_LEARNED) {
+        int64_t ns = std::min<int64_t>((int64_t)1 << stage, t->n);
+        int64_t stride = (t->n + ns - 1) / ns;
+        ns = (t->n + stride - 1) / stride;
+        if ((e = cudaMalloc(&b->d_sample, sizeof(uint64_t) * ns)) != cudaSuccess) return fail(e);
+        k_batch_sample<<<(unsigned)((ns + 255) / 256), 256, 0, (cudaStream_t)stream>>>(t->d_key, (int)ns, (int)stride,
+                                                                                      b->d_sample);
+        count_launch();
+        if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess) return fail(e);
+        v.sample = b->d_sample;
+        v.nsample = (int)ns;
+        v.stride = (int)stride;
+    }
+    const size_t smem = search != OT_LEARNED ? (size_t)v.nsample * sizeof(uint64_t) : 0;
+    void* kfn = search == OT_LEARNED ? (void*)k_batch<true> : (void*)k_batch<false>;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return fail(e);
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, block, smem)) != cudaSuccess) return fail(e);
+    if (launch && launch->blocks_per_sm > 0) per_sm = std::min(per_sm, launch->blocks_per_sm);
+    per_sm = std::max(per_sm, 1);
+    const unsigned grid = (unsigned)(num_sms() * per_sm);
+
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e);
+    cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), cs);
+    RootModel rm = t->root;
+    if (search == OT_LEARNED)
+        k_batch<true><<<grid, block, smem, cs>>>(v, rm, a, d_field, b->d_counter);
+    else
+        k_batch<false><<<grid, block, smem, cs>>>(v, rm, a, d_field, b->d_counter);
+    e = cudaStreamEndCapture(cs, &b->graph);
+    if (e != cudaSuccess) return fail(e);
+    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) return fail(e);
+    cudaStreamDestroy(cs);
+    *out = b;
+    return OT_OK;
+}
+
+extern "C" ot_status ot_batch_run(ot_batch* b, void* stream) {
+    if (!b || !b->exec) return OT_ERR_ARG;
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    count_launch();
+    return OT_OK;
+}
+
+extern "C" ot_status ot_batch_destroy(ot_batch* b) {
+    if (!b) return OT_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->d_counter) cudaFree(b->d_counter);
+    if (b->d_sample) cudaFree(b->d_sample);
+    delete b;
+    return OT_OK;
+}

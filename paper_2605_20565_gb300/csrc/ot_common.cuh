@@ -1,0 +1,249 @@
+// ot_common.cuh -- device building blocks shared by the library's kernels: Morton keys,
+// FP64 quantisation, host-cell search (plain and learned), delta functions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "octtrack.h"
+
+namespace ot {
+
+constexpr int MAXLEVEL = 21;
+constexpr int MLP_H = 32;
+constexpr int MLP_NPARAM = 3 * MLP_H + 1;
+
+// ------------------------------------------------------------------------------------------
+// Morton keys: x bit b -> key bit 3b, y -> 3b+1, z -> 3b+2 (the Z-order of p4est, Sec. 3.1).
+// ------------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t part1by2(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffULL;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffULL;
+    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+__host__ __device__ __forceinline__ uint32_t compact1by2(uint64_t x) {
+    x &= 0x1249249249249249ULL;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ULL;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00fULL;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffULL;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffULL;
+    x = (x ^ (x >> 32)) & 0x1fffffULL;
+    return (uint32_t)x;
+}
+__host__ __device__ __forceinline__ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+    return part1by2(x) | (part1by2(y) << 1) | (part1by2(z) << 2);
+}
+__host__ __device__ __forceinline__ void demorton3(uint64_t k, uint32_t& x, uint32_t& y, uint32_t& z) {
+    x = compact1by2(k);
+    y = compact1by2(k >> 1);
+    z = compact1by2(k >> 2);
+}
+// Number of MAXLEVEL keys covered by a leaf of level l: 8^(21-l).
+__host__ __device__ __forceinline__ uint64_t key_span(int l) { return 1ULL << (3 * (MAXLEVEL - l)); }
+
+// FP64 quantisation (Algorithm 1, get_cell_at at MAXLEVEL): q = floor(x 2^21) per axis.  The
+// scaling by a power of two is exact and the conversion truncates, so a point on a face
+// lands in the upper cell exactly as in an FP64 CPU evaluation.  False outside [0,1)^3 / NaN.
+__device__ __forceinline__ bool quantise(double x, double y, double z, uint32_t& qx, uint32_t& qy, uint32_t& qz) {
+    if (!(x >= 0.0 && x < 1.0 && y >= 0.0 && y < 1.0 && z >= 0.0 && z < 1.0)) return false;
+    qx = __double2uint_rz(x * 2097152.0);
+    qy = __double2uint_rz(y * 2097152.0);
+    qz = __double2uint_rz(z * 2097152.0);
+    return true;
+}
+
+// ------------------------------------------------------------------------------------------
+// Views passed by value to kernels.
+// ------------------------------------------------------------------------------------------
+struct __align__(32) LeafModel {
+    uint64_t base; // smallest key routed to the model (prediction input is key - base)
+    float slope;
+    float icpt; // relative to `first`
+    int err_lo; // window below the prediction
+    int err_hi; // window above the prediction
+    int first;  // index of the model's first key (prediction origin)
+    int count;  // keys routed here (0: empty model, queries fall back)
+};
+
+struct RootModel {
+    int kind;   // OT_ROOT_LINEAR / OT_ROOT_MLP
+    int n_models;
+    float a, b; // linear root: y = a + b x
+    float w1[MLP_H], b1[MLP_H], w2[MLP_H];
+    float b2;
+};
+
+struct TreeView {
+    const uint64_t* __restrict__ key;
+    const uint8_t* __restrict__ level;
+    int n;
+    int lmin, lmax;
+    // plain search: shared-memory sample of every stride-th key (nsample entries)
+    const uint64_t* __restrict__ sample;
+    int nsample;
+    int stride;
+    // learned search
+    const LeafModel* __restrict__ models;
+    unsigned* err;                      // device error word
+    unsigned long long* fallbacks;      // learned-query fallbacks
+};
+
+__device__ __forceinline__ uint64_t ldg_key(const uint64_t* p) { return __ldg(reinterpret_cast<const unsigned long long*>(p)); }
+
+// Last index in [lo, lo+len) whose key <= q, given key[lo] <= q (branch-free halving).
+__device__ __forceinline__ int search_range(const uint64_t* __restrict__ key, int lo, int len, uint64_t q) {
+    while (len > 1) {
+        int half = len >> 1;
+        uint64_t k = ldg_key(key + lo + half);
+        lo = (k <= q) ? lo + half : lo;
+        len -= half;
+    }
+    return lo;
+}
+
+// Last sample index whose key <= q, sample in shared memory (sample[0] = key[0] = 0 <= q).
+__device__ __forceinline__ int search_smem(const uint64_t* s, int len, uint64_t q) {
+    int lo = 0;
+    while (len > 1) {
+        int half = len >> 1;
+        lo = (s[lo + half] <= q) ? lo + half : lo;
+        len -= half;
+    }
+    return lo;
+}
+
+// Plain host search: the shared-memory sample selects a bucket of `stride` keys, a branch-free
+// binary search in global memory finishes.  s_sample may be null (then search [0, n)).
+__device__ __forceinline__ int search_plain(const TreeView& t, const uint64_t* s_sample, uint64_t q) {
+    if (s_sample == nullptr || t.nsample <= 1) return search_range(t.key, 0, t.n, q);
+    int b = search_smem(s_sample, t.nsample, q);
+    int lo = b * t.stride;
+    int len = min(t.stride, t.n - lo);
+    return search_range(t.key, lo, len, q);
+}
+
+// Root model: predicted fractional position y ~ i/N of key q.
+__device__ __forceinline__ float root_predict(const RootModel& r, uint64_t q) {
+    float x = __fmul_rn(__ull2float_rn(q), 0x1p-63f);
+    if (r.kind == OT_ROOT_LINEAR) return __fadd_rn(r.a, __fmul_rn(r.b, x));
+    float y = r.b2;
+#pragma unroll
+    for (int k = 0; k < MLP_H; ++k) {
+        float z = __fadd_rn(__fmul_rn(r.w1[k], x), r.b1[k]);
+        y = __fadd_rn(y, __fmul_rn(r.w2[k], fmaxf(z, 0.0f)));
+    }
+    return y;
+}
+__device__ __forceinline__ int root_route(const RootModel& r, uint64_t q) {
+    float y = root_predict(r, q) * (float)r.n_models;
+    y = fminf(fmaxf(y, 0.0f), (float)(r.n_models - 1));
+    return (int)y; // y >= 0: truncation is floor
+}
+// Leaf model prediction (integer), the same arithmetic at training and query time:
+// first + floor(slope (q - base) + icpt), clamped to [0, n).
+__device__ __forceinline__ int leaf_predict(const LeafModel& m, uint64_t q, int n) {
+    const float off = __ll2float_rn((long long)(q - m.base));
+    float p = __fadd_rn(__fmul_rn(m.slope, off), m.icpt);
+    p = fminf(fmaxf(p, -1.0e9f), 1.0e9f);
+    const int pc = m.first + (int)floorf(p);
+    return min(max(pc, 0), n - 1);
+}
+
+// Learned host search: predict, search the stored error window, verify, else plain search.
+__device__ __forceinline__ int search_learned(const TreeView& t, const RootModel& r, const uint64_t* s_sample,
+                                              uint64_t q) {
+    int j = root_route(r, q);
+    LeafModel m = t.models[j];
+    if (m.count > 0) {
+        int pc = leaf_predict(m, q, t.n);
+        int lo = max(pc - m.err_lo - 1, 0);
+        int hi = min(pc + m.err_hi + 1, t.n - 1);
+        if (ldg_key(t.key + lo) <= q) {
+            int a = search_range(t.key, lo, hi - lo + 1, q);
+            if (a < hi || a == t.n - 1 || ldg_key(t.key + a + 1) > q) return a;
+        }
+    }
+    atomicAdd(t.fallbacks, 1ULL);
+    atomicOr(t.err, (unsigned)OT_DEV_WINDOW);
+    return search_plain(t, s_sample, q);
+}
+
+template <bool LEARNED>
+__device__ __forceinline__ int search(const TreeView& t, const RootModel& r, const uint64_t* s_sample, uint64_t q) {
+    if (LEARNED) return search_learned(t, r, s_sample, q);
+    return search_plain(t, s_sample, q);
+}
+
+// Cooperative load of the plain-search sample into shared memory.
+__device__ __forceinline__ void load_sample(const TreeView& t, uint64_t* s) {
+    for (int i = threadIdx.x; i < t.nsample; i += blockDim.x) s[i] = ldg_key(t.sample + i);
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
+// Discrete delta functions (Sec. 2.2), argument in grid units.  Square-root arguments are
+// written in the factored forms 2 - (2a-1)^2, 1 - (2a-3)^2 (Peskin) and 1 - 3(1-a)^2 (Roma),
+// which equal the printed polynomials and lose less to cancellation in FP32.
+// ------------------------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T dsqrt(T v);
+template <> __device__ __forceinline__ float dsqrt<float>(float v) { return sqrtf(fmaxf(v, 0.0f)); }
+template <> __device__ __forceinline__ double dsqrt<double>(double v) { return sqrt(fmax(v, 0.0)); }
+
+template <typename T> __device__ __forceinline__ T phi_peskin4(T r) {
+    T a = r < T(0) ? -r : r;
+    if (a <= T(1)) {
+        T e = T(2) * a - T(1);
+        return (T(3) - T(2) * a + dsqrt<T>(T(2) - e * e)) * T(0.125);
+    }
+    if (a <= T(2)) {
+        T e = T(2) * a - T(3);
+        return (T(5) - T(2) * a - dsqrt<T>(T(1) - e * e)) * T(0.125);
+    }
+    return T(0);
+}
+template <typename T> __device__ __forceinline__ T phi_roma3(T r) {
+    T a = r < T(0) ? -r : r;
+    if (a <= T(0.5)) return (T(1) + dsqrt<T>(T(1) - T(3) * a * a)) * (T(1) / T(3));
+    if (a <= T(1.5)) {
+        T e = T(1) - a;
+        return (T(5) - T(3) * a - dsqrt<T>(T(1) - T(3) * e * e)) * (T(1) / T(6));
+    }
+    return T(0);
+}
+
+// Stencil of one axis for a point at fine coordinate s = X 2^lmax - 1/2 (cell c centred at s = c).
+template <int KERNEL> struct Stencil;
+template <> struct Stencil<OT_PESKIN4> {
+    static constexpr int W = 4;
+    __device__ static int first(double s) { return (int)floor(s) - 1; }
+    template <typename T> __device__ static T phi(T r) { return phi_peskin4<T>(r); }
+};
+template <> struct Stencil<OT_ROMA3> {
+    static constexpr int W = 3;
+    __device__ static int first(double s) { return (int)floor(s + 0.5) - 1; }
+    template <typename T> __device__ static T phi(T r) { return phi_roma3<T>(r); }
+};
+
+// Per-leaf field vectors.
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+    using type = float4;
+    __device__ static float4 load(const float* f, int i) { return __ldg(reinterpret_cast<const float4*>(f) + i); }
+};
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+template <> struct Vec4<double> {
+    using type = dbl4;
+    __device__ static dbl4 load(const double* f, int i) {
+        const double2* p = reinterpret_cast<const double2*>(f) + 2 * (size_t)i;
+        double2 a = __ldg(p), b = __ldg(p + 1);
+        return dbl4{a.x, a.y, b.x, b.y};
+    }
+};
+
+} // namespace ot

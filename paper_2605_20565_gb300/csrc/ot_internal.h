@@ -1,0 +1,95 @@
+// ot_internal.h -- library-private declarations shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "octtrack.h"
+#include "ot_common.cuh"
+
+struct ot_octree {
+    int device = 0;
+    int64_t n = 0;
+    int lmin = 0, lmax = 0;
+    uint64_t* d_key = nullptr;
+    uint8_t* d_level = nullptr;
+    // plain-search sample (every stride-th key)
+    uint64_t* d_sample = nullptr;
+    int nsample = 0;
+    int stride = 0;
+    int stage_log2 = 12;
+    // learned index
+    bool has_index = false;
+    ot::RootModel root{};
+    ot::LeafModel* d_models = nullptr;
+    int n_models = 0;
+    float final_loss = 0.0f;
+    // diagnostics: [0] error word (unsigned), [1..2] fallback counter (u64)
+    unsigned* d_err = nullptr;
+    unsigned long long* d_fallbacks = nullptr;
+};
+
+namespace ot {
+
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// status helpers
+ot_status cuda_status(cudaError_t e);
+#define OT_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return ot::cuda_status(e_); \
+    } while (0)
+
+int num_sms();
+
+TreeView tree_view(const ot_octree* t, bool with_sample = true);
+
+// primitives (ot_prims.cu) -------------------------------------------------------------------
+// Exclusive scan of n uint32 (in place allowed); returns the total in *d_total if non-null.
+// Temporary storage is allocated stream-ordered and released before return.
+ot_status scan_u32(const uint32_t* d_in, uint32_t* d_out, int64_t n, uint32_t* d_total, cudaStream_t s);
+// Stable LSD radix sort of n uint64 by bits [bit0, bit1) (8-bit digits).  d_tmp: n uint64
+// scratch.  Result in d_keys.  Temporaries (histograms) are stream-ordered allocations.
+ot_status radix_sort_u64(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bit0, int bit1, cudaStream_t s);
+// Histogram + offset workspace bytes for radix_sort_u64_ws.
+size_t radix_ws_bytes(int64_t n);
+// Same sort with caller-provided workspace (no allocation): ws of radix_ws_bytes(n) bytes.
+ot_status radix_sort_u64_ws(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bit0, int bit1, void* ws,
+                            cudaStream_t s);
+// Compaction: out[j] = in[i] for the i with flag[i] != 0, in order; *h_count on the host
+// (synchronises).  d_scan: n uint32 scratch.
+ot_status compact_u64(const uint64_t* d_in, const uint32_t* d_flag, uint32_t* d_scan, int64_t n, uint64_t* d_out,
+                      int64_t* h_count, cudaStream_t s);
+// Sorted input -> unique values in place; *h_count on the host (synchronises).
+ot_status unique_u64(uint64_t* d_keys, int64_t n, int64_t* h_count, cudaStream_t s);
+
+// builder (ot_build.cu) ------------------------------------------------------------------------
+ot_status build_tree(const ot_sphere* h_spheres, int n, const ot_build_params* p, cudaStream_t s, ot_octree* t);
+ot_status finish_tree(ot_octree* t, cudaStream_t s); // sample, error word
+ot_status validate_leaves(const uint64_t* d_key, const uint8_t* d_level, int64_t n, int full, cudaStream_t s,
+                          int* lmin, int* lmax);
+ot_status leaf_centres(const ot_octree* t, double* d_xyz, cudaStream_t s);
+
+// learned index (ot_learned.cu) ----------------------------------------------------------------
+ot_status train_index(ot_octree* t, const ot_index_params* p, cudaStream_t s);
+ot_status mlp_grad(const float* d_params, const float* d_x, const float* d_t, int64_t n, float* d_grad,
+                   float* d_loss, cudaStream_t s);
+
+// point kernels (ot_interp.cu) -------------------------------------------------------------------
+ot_status launch_locate(const ot_octree* t, const double* x, const double* y, const double* z, int64_t n, int search,
+                        int32_t* host, unsigned long long* n_miss, cudaStream_t s);
+template <typename T>
+ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const double* y, const double* z, int64_t n,
+                        const int32_t* host_in, int search, const T* field, T* u, int32_t* host_out, cudaStream_t s);
+
+// spreading (ot_spread.cu) ---------------------------------------------------------------------
+size_t spread_ws_bytes(const ot_octree* t, int kernel, int64_t n);
+template <typename T>
+ot_status launch_spread(const ot_octree* t, int kernel, int mode, const double* x, const double* y, const double* z,
+                        const T* F, const T* dV, int64_t n, T* f, void* ws, size_t ws_bytes, cudaStream_t s);
+
+} // namespace ot

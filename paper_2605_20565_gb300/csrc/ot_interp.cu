@@ -1,0 +1,168 @@
+// ot_interp.cu -- single-op kernels: locate, trilinear and delta-kernel interpolation.
+// Persistent grid-stride launches (a few blocks per SM); each block stages the plain-search
+// sample of top-level keys in shared memory once.
+#include <algorithm>
+
+#include "ot_internal.h"
+#include "ot_points.cuh"
+
+namespace ot {
+
+namespace {
+
+template <bool LEARNED>
+__global__ void __launch_bounds__(256) k_locate(TreeView t, RootModel rm, const double* __restrict__ x,
+                                                const double* __restrict__ y, const double* __restrict__ z, int64_t n,
+                                                int32_t* __restrict__ host, unsigned long long* n_miss) {
+    extern __shared__ uint64_t s_sample[];
+    const bool staged = t.nsample > 1;
+    if (staged) load_sample(t, s_sample);
+    const uint64_t* ss = staged ? s_sample : nullptr;
+    unsigned miss = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t qx, qy, qz;
+        int h = -1;
+        if (quantise(x[i], y[i], z[i], qx, qy, qz))
+            h = search<LEARNED>(t, rm, ss, morton3(qx, qy, qz));
+        else
+            ++miss;
+        host[i] = h;
+    }
+    if (miss) {
+        atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
+        if (n_miss) atomicAdd(n_miss, (unsigned long long)miss);
+    }
+}
+
+template <typename T, bool LEARNED>
+__global__ void __launch_bounds__(256) k_trilinear(TreeView t, RootModel rm, const double* __restrict__ x,
+                                                   const double* __restrict__ y, const double* __restrict__ z,
+                                                   int64_t n, const int32_t* __restrict__ host_in,
+                                                   const T* __restrict__ field, T* __restrict__ u,
+                                                   int32_t* __restrict__ host_out) {
+    extern __shared__ uint64_t s_sample[];
+    const bool staged = t.nsample > 1;
+    if (staged) load_sample(t, s_sample);
+    const uint64_t* ss = staged ? s_sample : nullptr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T o[3];
+        const int hin = host_in ? host_in[i] : -1;
+        int h;
+        if (host_in && (hin < 0 || hin >= t.n)) {
+            // no host (outside the cube) or an index that is not a leaf: no value
+            o[0] = o[1] = o[2] = qnan<T>();
+            if (hin >= t.n) atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
+            h = -1;
+        } else {
+            h = trilinear_point<T, LEARNED>(t, rm, ss, field, x[i], y[i], z[i], hin, o);
+        }
+        u[i] = o[0];
+        u[n + i] = o[1];
+        u[2 * n + i] = o[2];
+        if (host_out) host_out[i] = h;
+    }
+}
+
+template <typename T, int K, bool LEARNED>
+__global__ void __launch_bounds__(256) k_delta(TreeView t, RootModel rm, const double* __restrict__ x,
+                                               const double* __restrict__ y, const double* __restrict__ z, int64_t n,
+                                               const T* __restrict__ field, T* __restrict__ u,
+                                               int32_t* __restrict__ host_out) {
+    extern __shared__ uint64_t s_sample[];
+    const bool staged = t.nsample > 1;
+    if (staged) load_sample(t, s_sample);
+    const uint64_t* ss = staged ? s_sample : nullptr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T o[3];
+        const int h = delta_point<T, K, LEARNED>(t, rm, ss, field, x[i], y[i], z[i], host_out != nullptr, o);
+        u[i] = o[0];
+        u[n + i] = o[1];
+        u[2 * n + i] = o[2];
+        if (host_out) host_out[i] = h;
+    }
+}
+
+template <typename Kern>
+unsigned persistent_grid(Kern k, int block, size_t smem, int64_t n) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
+    per_sm = std::max(per_sm, 1);
+    int64_t need = (n + block - 1) / block;
+    int64_t g = std::min<int64_t>((int64_t)num_sms() * per_sm, need);
+    return (unsigned)std::max<int64_t>(g, 1);
+}
+
+template <typename Kern>
+ot_status prep_smem(Kern k, size_t smem) {
+    if (smem > 48 * 1024) OT_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return OT_OK;
+}
+
+} // namespace
+
+ot_status launch_locate(const ot_octree* t, const double* x, const double* y, const double* z, int64_t n, int search,
+                        int32_t* host, unsigned long long* n_miss, cudaStream_t s) {
+    if (n == 0) return OT_OK;
+    const bool learned = search == OT_LEARNED;
+    TreeView v = tree_view(t, !learned);
+    const size_t smem = (size_t)v.nsample * sizeof(uint64_t);
+    const int block = 256;
+    if (learned) {
+        auto k = k_locate<true>;
+        ot_status st = prep_smem(k, smem);
+        if (st != OT_OK) return st;
+        k<<<persistent_grid(k, block, smem, n), block, smem, s>>>(v, t->root, x, y, z, n, host, n_miss);
+    } else {
+        auto k = k_locate<false>;
+        ot_status st = prep_smem(k, smem);
+        if (st != OT_OK) return st;
+        k<<<persistent_grid(k, block, smem, n), block, smem, s>>>(v, t->root, x, y, z, n, host, n_miss);
+    }
+    count_launch();
+    OT_CUDA(cudaGetLastError());
+    return OT_OK;
+}
+
+template <typename T>
+ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const double* y, const double* z, int64_t n,
+                        const int32_t* host_in, int search, const T* field, T* u, int32_t* host_out, cudaStream_t s) {
+    if (n == 0) return OT_OK;
+    const bool learned = search == OT_LEARNED;
+    TreeView v = tree_view(t, !learned);
+    const size_t smem = (size_t)v.nsample * sizeof(uint64_t);
+    const int block = 256;
+    ot_status st = OT_OK;
+#define OT_LAUNCH(KERN, ...)                                                               \
+    do {                                                                                   \
+        auto k_ = KERN;                                                                    \
+        if ((st = prep_smem(k_, smem)) != OT_OK) return st;                                \
+        k_<<<persistent_grid(k_, block, smem, n), block, smem, s>>>(__VA_ARGS__);          \
+    } while (0)
+    if (kernel == OT_TRILINEAR) {
+        if (learned)
+            OT_LAUNCH((k_trilinear<T, true>), v, t->root, x, y, z, n, host_in, field, u, host_out);
+        else
+            OT_LAUNCH((k_trilinear<T, false>), v, t->root, x, y, z, n, host_in, field, u, host_out);
+    } else if (kernel == OT_PESKIN4) {
+        if (learned)
+            OT_LAUNCH((k_delta<T, OT_PESKIN4, true>), v, t->root, x, y, z, n, field, u, host_out);
+        else
+            OT_LAUNCH((k_delta<T, OT_PESKIN4, false>), v, t->root, x, y, z, n, field, u, host_out);
+    } else {
+        if (learned)
+            OT_LAUNCH((k_delta<T, OT_ROMA3, true>), v, t->root, x, y, z, n, field, u, host_out);
+        else
+            OT_LAUNCH((k_delta<T, OT_ROMA3, false>), v, t->root, x, y, z, n, field, u, host_out);
+    }
+#undef OT_LAUNCH
+    count_launch();
+    OT_CUDA(cudaGetLastError());
+    return OT_OK;
+}
+
+template ot_status launch_interp<float>(const ot_octree*, int, const double*, const double*, const double*, int64_t,
+                                        const int32_t*, int, const float*, float*, int32_t*, cudaStream_t);
+template ot_status launch_interp<double>(const ot_octree*, int, const double*, const double*, const double*, int64_t,
+                                         const int32_t*, int, const double*, double*, int32_t*, cudaStream_t);
+
+} // namespace ot

@@ -1,0 +1,417 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded
+inputs.  Host indices and octree leaves are compared bit for bit; FP32 values within 1e-5 of
+max|reference| (the tolerance stated for this path), FP64 values within 1e-12."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ot():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2605_20565_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    return torch
+
+
+def dev(a, dtype=None):
+    import torch
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def pts(a):
+    return [dev(np.ascontiguousarray(a[d], dtype=np.float64)) for d in range(3)]
+
+
+def leaves_np(ot, tree):
+    k, l = ot.ot_octree_copy_leaves(tree)
+    return k.cpu().numpy().view(np.uint64), l.cpu().numpy()
+
+
+def rel_err(a, ref):
+    scale = max(np.abs(ref).max(), 1e-300)
+    return float(np.abs(a - ref).max() / scale)
+
+
+@pytest.fixture(scope="module")
+def tiny(ot):
+    from paper_2605_20565_gb300 import synth
+    w = synth.tiny()
+    ko, lo = oracle.octree_build(w.spheres, w.lmin, w.lmax)
+    tree = ot.ot_octree_build(w.spheres, w.lmin, w.lmax)
+    return w, ko, lo, tree
+
+
+# ---------------------------------------------------------------------------------------
+# Octree construction
+# ---------------------------------------------------------------------------------------
+
+def test_tiny_octree_bit_exact(ot, tiny):
+    w, ko, lo, tree = tiny
+    k, l = leaves_np(ot, tree)
+    assert np.array_equal(k, ko) and np.array_equal(l, lo)
+    assert ot.ot_octree_info(tree) == (ko.size, w.lmin, w.lmax)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("full", [1, 0])
+def test_random_octrees_bit_exact(ot, seed, full):
+    rng = np.random.default_rng(1000 + seed)
+    lmin = int(rng.integers(0, 4))
+    lmax = int(rng.integers(lmin, 8))
+    ns = int(rng.integers(0, 6))
+    sph = np.column_stack([rng.uniform(0.0, 1.0, (ns, 3)), rng.uniform(0.0, 0.3, ns), rng.uniform(0.0, 0.1, ns)])
+    ko, lo = oracle.octree_build(sph, lmin, lmax, full)
+    tree = ot.ot_octree_build(sph, lmin, lmax, full)
+    k, l = leaves_np(ot, tree)
+    assert np.array_equal(k, ko) and np.array_equal(l, lo)
+
+
+def test_uniform_and_single_leaf_trees(ot):
+    for lev in (0, 1, 3):
+        ko, lo = oracle.octree_build(np.zeros((0, 5)), lev, lev)
+        tree = ot.ot_octree_build(np.zeros((0, 5)), lev, lev)
+        k, l = leaves_np(ot, tree)
+        assert np.array_equal(k, ko) and np.array_equal(l, lo)
+
+
+def test_from_leaves_validation(ot, tiny, torch_mod):
+    torch = torch_mod
+    w, ko, lo, tree = tiny
+    kt = dev(ko.view(np.int64))
+    lt = dev(lo)
+    t2 = ot.ot_octree_from_leaves(kt, lt)
+    assert ot.ot_octree_info(t2)[0] == ko.size
+    # unsorted
+    bad = ko.copy()
+    bad[[10, 11]] = bad[[11, 10]]
+    with pytest.raises(ot.OtError) as e:
+        ot.ot_octree_from_leaves(dev(bad.view(np.int64)), lt)
+    assert e.value.status == -4
+    # a gap (one leaf removed)
+    with pytest.raises(ot.OtError) as e:
+        ot.ot_octree_from_leaves(dev(np.delete(ko, 5).view(np.int64)), dev(np.delete(lo, 5)))
+    assert e.value.status == -4
+    # unbalanced: level-1 octants next to a block refined to level 3
+    keys, levels = [], []
+    for c in range(8):
+        if c == 0:
+            for g in range(64):
+                keys.append(g << (3 * 18))
+                levels.append(3)
+        else:
+            keys.append(c << (3 * 20))
+            levels.append(1)
+    with pytest.raises(ot.OtError) as e:
+        ot.ot_octree_from_leaves(dev(np.array(keys, np.uint64).view(np.int64)), dev(np.array(levels, np.uint8)))
+    assert e.value.status == -5
+    del torch
+
+
+# ---------------------------------------------------------------------------------------
+# Host-cell search
+# ---------------------------------------------------------------------------------------
+
+def special_points(ko, lo, rng, n_rand):
+    cen = oracle.leaf_centres(ko, lo)
+    h = 2.0 ** -lo.astype(np.float64)
+    anchors = cen - 0.5 * h[:, None]
+    P = np.concatenate([rng.uniform(0, 1, (n_rand, 3)), anchors, cen,
+                        np.array([[1.0, 0.5, 0.5], [-1e-300, 0.5, 0.5], [np.nan, 0.5, 0.5],
+                                  [np.nextafter(1.0, 0.0)] * 3, [0.0, 0.0, 0.0], [-0.0, 0.5, 0.5]])])
+    return P
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 33, 1007])
+def test_locate_binary_ragged(ot, tiny, n):
+    w, ko, lo, tree = tiny
+    rng = np.random.default_rng(n)
+    P = rng.uniform(0, 1, (n, 3))
+    x, y, z = pts(P.T) if n else [dev(np.zeros(0))] * 3
+    h = ot.ot_locate(tree, x, y, z)
+    ref = oracle.locate_ub(ko, lo, *P.T) if n else np.zeros(0, np.int32)
+    assert np.array_equal(h.cpu().numpy(), ref)
+
+
+def test_locate_special_points(ot, tiny, torch_mod):
+    torch = torch_mod
+    w, ko, lo, tree = tiny
+    P = special_points(ko, lo, np.random.default_rng(5), 3000)
+    ref = oracle.locate_ub(ko, lo, *P.T)
+    ref_alg1 = oracle.locate_alg1(ko, lo, w.lmin, w.lmax, *P.T)
+    assert np.array_equal(ref, ref_alg1)
+    miss = torch.zeros(1, dtype=torch.int64, device="cuda")
+    h = ot.ot_locate(tree, *pts(P.T), n_miss=miss)
+    assert np.array_equal(h.cpu().numpy(), ref)
+    assert int(miss.item()) == int((ref < 0).sum()) == 3
+    assert ot.ot_last_error(tree) & ot.OT_DEV_OUTSIDE
+
+
+@pytest.mark.parametrize("root", [0, 1])
+def test_learned_locate_bit_exact(ot, root):
+    from paper_2605_20565_gb300 import synth
+    w = synth.single_bubble(n_markers=2000, n_particles=200_000)
+    w.lmin, w.lmax = 4, 8
+    sph = w.spheres.copy()
+    sph[:, 4] = 0.1
+    ko, lo = oracle.octree_build(sph, 4, 8)
+    tree = ot.ot_octree_build(sph, 4, 8)
+    ot.ot_index_train(tree, root=root, n_leaf_models=1024, epochs=2, batch=8192, lr=1e-3, seed=7)
+    P = special_points(ko, lo, np.random.default_rng(9), 20000)
+    P = np.concatenate([P, w.particles.T])
+    x, y, z = pts(P.T)
+    hb = ot.ot_locate(tree, x, y, z, search=ot.OT_BINARY)
+    hl = ot.ot_locate(tree, x, y, z, search=ot.OT_LEARNED)
+    ref = oracle.locate_ub(ko, lo, *P.T)
+    assert np.array_equal(hb.cpu().numpy(), ref)
+    assert np.array_equal(hl.cpu().numpy(), ref)
+    # every stored key (the leaf anchors) is answered inside its window: no fallback
+    cen = oracle.leaf_centres(ko, lo)
+    anchors = cen - 0.5 * (2.0 ** -lo.astype(np.float64))[:, None]
+    ot.ot_index_get_stats(tree, reset=True)
+    ha = ot.ot_locate(tree, *pts(anchors.T), search=ot.OT_LEARNED)
+    assert np.array_equal(ha.cpu().numpy(), np.arange(ko.size, dtype=np.int32))
+    st = ot.ot_index_get_stats(tree)
+    assert st["fallbacks"] == 0
+    assert st["mean_window"] < ko.size / 8
+
+
+# ---------------------------------------------------------------------------------------
+# Interpolation
+# ---------------------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def tiny_fields(tiny):
+    from paper_2605_20565_gb300 import synth
+    w, ko, lo, tree = tiny
+    cen = oracle.leaf_centres(ko, lo)
+    return {"sin": synth.sin_field(cen), "linear": synth.linear_field(cen)}
+
+
+@pytest.mark.parametrize("fname", ["sin", "linear"])
+@pytest.mark.parametrize("search", [0, 1])
+def test_trilinear_f32(ot, tiny, tiny_fields, fname, search, torch_mod):
+    torch = torch_mod
+    w, ko, lo, tree = tiny
+    if search == 1:
+        ot.ot_index_train(tree, root=ot.OT_ROOT_LINEAR, n_leaf_models=128)
+    P = special_points(ko, lo, np.random.default_rng(3), 5000)[:-6]  # inside the cube
+    f32 = tiny_fields[fname].astype(np.float32)
+    field = dev(f32)
+    hout = torch.empty(P.shape[0], dtype=torch.int32, device="cuda")
+    u = ot.ot_interpolate(tree, ot.OT_TRILINEAR, *pts(P.T), field, search=search, host_out=hout)
+    href = oracle.locate_ub(ko, lo, *P.T)
+    ref = oracle.interp_trilinear(ko, lo, f32.astype(np.float64), *P.T, href)
+    assert np.array_equal(hout.cpu().numpy(), href)
+    assert rel_err(u.cpu().numpy(), ref) <= TOL32
+    # with given host indices
+    u2 = ot.ot_interpolate(tree, ot.OT_TRILINEAR, *pts(P.T), field, host_in=hout)
+    assert torch.equal(u, u2)
+
+
+def test_trilinear_f64_and_outside(ot, tiny, tiny_fields):
+    w, ko, lo, tree = tiny
+    P = special_points(ko, lo, np.random.default_rng(4), 5000)
+    field = tiny_fields["sin"]
+    u = ot.ot_interpolate_f64(tree, ot.OT_TRILINEAR, *pts(P.T), dev(field)).cpu().numpy()
+    href = oracle.locate_ub(ko, lo, *P.T)
+    ref = oracle.interp_trilinear(ko, lo, field, *P.T, href)
+    inside = href >= 0
+    assert np.all(np.isnan(u[:, ~inside]))
+    assert rel_err(u[:, inside], ref[:, inside]) <= TOL64
+
+
+@pytest.mark.parametrize("kernel", [2, 3])
+@pytest.mark.parametrize("search", [0, 1])
+def test_delta_interp(ot, tiny, tiny_fields, kernel, search, torch_mod):
+    torch = torch_mod
+    w, ko, lo, tree = tiny
+    if search == 1:
+        ot.ot_index_train(tree, root=ot.OT_ROOT_LINEAR, n_leaf_models=128)
+    X = w.markers
+    for fname in ("sin", "linear"):
+        f64 = tiny_fields[fname]
+        f32 = f64.astype(np.float32)
+        hout = torch.empty(X.shape[1], dtype=torch.int32, device="cuda")
+        u = ot.ot_interpolate(tree, kernel, *pts(X), dev(f32), search=search, host_out=hout)
+        ref, bad = oracle.interp_delta(ko, lo, w.lmax, kernel, f32.astype(np.float64), *X)
+        assert bad == 0
+        assert rel_err(u.cpu().numpy(), ref) <= TOL32
+        assert np.array_equal(hout.cpu().numpy(), oracle.locate_ub(ko, lo, *X))
+        u64 = ot.ot_interpolate_f64(tree, kernel, *pts(X), dev(f64), search=search)
+        ref64, _ = oracle.interp_delta(ko, lo, w.lmax, kernel, f64, *X)
+        assert rel_err(u64.cpu().numpy(), ref64) <= TOL64
+    assert ot.ot_last_error(tree) & (ot.OT_DEV_STENCIL | ot.OT_DEV_OUTSIDE) == 0
+
+
+def test_delta_stencil_errors_match_oracle(ot, tiny, tiny_fields):
+    w, ko, lo, tree = tiny
+    ot.ot_last_error(tree)
+    P = np.array([[0.01, 0.99, 0.5], [0.01, 0.5, 0.5], [0.5, 0.3005, 0.5], [0.5, 0.5, 0.5]]).T.copy()
+    f64 = tiny_fields["sin"]
+    u = ot.ot_interpolate_f64(tree, 2, *pts(P), dev(f64))
+    ref, bad = oracle.interp_delta(ko, lo, w.lmax, 2, f64, *P)
+    assert bad > 0
+    assert rel_err(u.cpu().numpy(), ref) <= TOL64
+    assert ot.ot_last_error(tree) & ot.OT_DEV_STENCIL
+
+
+# ---------------------------------------------------------------------------------------
+# Spreading
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kernel", [2, 3])
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("with_dv", [False, True])
+def test_spread(ot, tiny, kernel, mode, with_dv, torch_mod):
+    torch = torch_mod
+    w, ko, lo, tree = tiny
+    rng = np.random.default_rng(21)
+    X = w.markers
+    n = X.shape[1]
+    F = rng.normal(size=(3, n)).astype(np.float32)
+    h3 = 2.0 ** (-3 * w.lmax)
+    dV = (rng.uniform(0.5, 2.0, n) * h3).astype(np.float32) if with_dv else None
+    f = torch.zeros((ko.size, 4), dtype=torch.float32, device="cuda")
+    ot.ot_spread(tree, kernel, mode, *pts(X), dev(F), f, dV=dev(dV) if with_dv else None)
+    ref, bad = oracle.spread_delta(ko, lo, w.lmax, kernel, *X, F.astype(np.float64),
+                                   dV.astype(np.float64) if with_dv else None)
+    assert bad == 0
+    fn = f.cpu().numpy()
+    assert rel_err(fn[:, :3], ref[:, :3]) <= TOL32
+    assert np.all(fn[:, 3] == 0)
+    # f64
+    f64 = torch.zeros((ko.size, 4), dtype=torch.float64, device="cuda")
+    ot.ot_spread_f64(tree, kernel, mode, *pts(X), dev(F.astype(np.float64)), f64,
+                     dV=dev(dV.astype(np.float64)) if with_dv else None)
+    assert rel_err(f64.cpu().numpy()[:, :3], ref[:, :3]) <= TOL64
+
+
+def test_sorted_spread_is_deterministic_and_accumulates(ot, tiny, torch_mod):
+    torch = torch_mod
+    w, ko, lo, tree = tiny
+    rng = np.random.default_rng(22)
+    X = w.markers
+    F = dev(rng.normal(size=(3, X.shape[1])).astype(np.float32))
+    x, y, z = pts(X)
+    outs = []
+    for _ in range(10):
+        f = torch.zeros((ko.size, 4), dtype=torch.float32, device="cuda")
+        ot.ot_spread(tree, 2, ot.OT_SORTED, x, y, z, F, f)
+        outs.append(f)
+    for o in outs[1:]:
+        assert torch.equal(o.view(torch.int32), outs[0].view(torch.int32))
+    f = outs[0].clone()
+    ot.ot_spread(tree, 2, ot.OT_SORTED, x, y, z, F, f)
+    assert torch.equal(f, 2 * outs[0])
+    with pytest.raises(ot.OtError):
+        ot.ot_spread(tree, 2, ot.OT_SORTED, x, y, z, F, f,
+                     workspace=torch.empty(64, dtype=torch.uint8, device="cuda"))
+
+
+def test_adjoint_identity_on_device(ot, tiny, torch_mod):
+    """<I u, F>_L = <u, S F>_E with h^3 weights, both sides computed by the CUDA path (FP64)."""
+    torch = torch_mod
+    w, ko, lo, tree = tiny
+    rng = np.random.default_rng(23)
+    X = w.markers
+    n = X.shape[1]
+    F = rng.normal(size=(3, n))
+    uf = np.zeros((ko.size, 4))
+    uf[:, :3] = rng.normal(size=(ko.size, 3))
+    Iu = ot.ot_interpolate_f64(tree, 2, *pts(X), dev(uf)).cpu().numpy()
+    f = torch.zeros((ko.size, 4), dtype=torch.float64, device="cuda")
+    ot.ot_spread_f64(tree, 2, ot.OT_SORTED, *pts(X), dev(F), f)
+    h3 = 2.0 ** (-3 * w.lmax)
+    lhs = float((Iu * F).sum() * h3)
+    rhs = float((uf[:, :3] * f.cpu().numpy()[:, :3]).sum() * h3)
+    assert abs(lhs - rhs) <= 1e-11 * max(1.0, abs(lhs))
+
+
+# ---------------------------------------------------------------------------------------
+# Learned-index network gradient
+# ---------------------------------------------------------------------------------------
+
+def test_mlp_gradient_matches_oracle(ot, torch_mod):
+    torch = torch_mod
+    rng = np.random.default_rng(5)
+    prm = rng.normal(scale=0.5, size=97).astype(np.float32)
+    x = rng.uniform(0, 1, 4096).astype(np.float32)
+    t = np.sort(rng.uniform(0, 1, 4096)).astype(np.float32)
+    g, loss = ot.ot_index_mlp_grad(dev(prm), dev(x), dev(t))
+    lref, gref = oracle.mlp_loss_grad(prm.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss.item() - lref) <= 1e-4 * abs(lref)
+    assert np.abs(g.cpu().numpy() - gref).max() <= 1e-3 * np.abs(gref).max()
+    del torch
+
+
+# ---------------------------------------------------------------------------------------
+# Batched persistent launch
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("search", [0, 1])
+def test_batch_matches_single_ops(ot, tiny, tiny_fields, search, torch_mod):
+    torch = torch_mod
+    w, ko, lo, tree = tiny
+    ot.ot_index_train(tree, root=ot.OT_ROOT_MLP, n_leaf_models=256, epochs=2, batch=4096)
+    field = dev(tiny_fields["sin"].astype(np.float32))
+    X = w.markers
+    P = w.particles
+    mx, my, mz = pts(X)
+    px, py, pz = pts(P)
+    X3 = np.ascontiguousarray(X[:, :333])
+    gx, gy, gz = pts(X3)
+    um = torch.full((3, X.shape[1]), 7.0, device="cuda")
+    up = torch.full((3, P.shape[1]), 7.0, device="cuda")
+    ur = torch.full((3, X3.shape[1]), 7.0, device="cuda")
+    hp = torch.empty(P.shape[1], dtype=torch.int32, device="cuda")
+    b = ot.ot_batch_create(tree, [dict(kernel=2, x=mx, y=my, z=mz, u=um),
+                                  dict(kernel=1, x=px, y=py, z=pz, u=up, host=hp),
+                                  dict(kernel=3, x=gx, y=gy, z=gz, u=ur)], field, search=search,
+                           launch=dict(block=128, tile=2))
+    for _ in range(2):
+        ot.ot_batch_run(b)
+    torch.cuda.synchronize()
+    assert torch.equal(um, ot.ot_interpolate(tree, 2, mx, my, mz, field, search=search))
+    assert torch.equal(up, ot.ot_interpolate(tree, 1, px, py, pz, field, search=search))
+    assert torch.equal(ur, ot.ot_interpolate(tree, 3, gx, gy, gz, field, search=search))
+    assert np.array_equal(hp.cpu().numpy(), oracle.locate_ub(ko, lo, *P))
+
+
+# ---------------------------------------------------------------------------------------
+# Advection step
+# ---------------------------------------------------------------------------------------
+
+def test_advect_ab2_matches_oracle(ot, torch_mod):
+    torch = torch_mod
+    rng = np.random.default_rng(31)
+    n = 1000
+    x = rng.uniform(0.2, 0.8, (3, n))
+    v = rng.normal(scale=0.1, size=(3, n)).astype(np.float32)
+    u = rng.normal(scale=0.1, size=(3, n)).astype(np.float32)
+    st = {"x": x.copy(), "v": v.astype(np.float64), "a_prev": np.zeros((3, n)), "v_prev": np.zeros((3, n))}
+    dx, dv = dev(x), dev(v)
+    da, dvp = torch.zeros_like(dv), torch.zeros_like(dv)
+    for step in range(3):
+        oracle.advect_ab2(st, u.astype(np.float64), 0.05, 2.0, 1e-3, step == 0)
+        ot.ot_advect_ab2(dx, dv, da, dvp, dev(u), 0.05, 2.0, 1e-3, step == 0)
+    assert rel_err(dv.cpu().numpy(), st["v"]) <= TOL32
+    assert np.abs(dx.cpu().numpy() - st["x"]).max() <= 1e-9
