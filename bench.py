@@ -1,0 +1,449 @@
+#!/usr/bin/env python3
+"""Benchmark of the Lagrangian-Eulerian coupling step on the many-bubble workload.
+
+One step = one pass of the hot path over the whole point set:
+  * locate + interpolate every IBM marker (Peskin-4) and every point particle (trilinear) in
+    one persistent launch replayed from a CUDA graph (learned index by default);
+  * spread the marker forces back to the cells (deterministic sorted reduction).
+value = (markers + particles) / step time, summed over ranks (each rank runs its own
+independent copy of the workload: weak scaling, no data-path collective).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on the same
+workload instead (bounded samples, host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Lagrangian points located+interpolated/s on 1 GB300 (learned vs plain) at <=1e-5 rel err"
+BYTES_PER_POINT = 40   # position 24 B + u 12 B + host 4 B
+BYTES_PER_LEAF = 21    # key 8 B + level 1 B + field 12 B
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="many_bubbles",
+                   choices=["many_bubbles", "single_bubble", "learned_index", "tiny"])
+    p.add_argument("--search", default="learned", choices=["learned", "binary"])
+    p.add_argument("--spread", default="sorted", choices=["sorted", "atomic"])
+    p.add_argument("--scale", type=float, default=1.0, help="scale point counts (testing only)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--launch", default="", help="block,tile,blocks_per_sm,stage_log2")
+    return p.parse_args()
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(points_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank processes its own batch of points per step."""
+    return world * points_per_rank / (ms_per_step / 1e3)
+
+
+def make_workload(name: str, scale: float, rank: int):
+    from paper_2605_20565_gb300 import synth
+    if name == "many_bubbles":
+        w = synth.many_bubbles(n_markers=int(2_000_000 * scale), n_particles=int(50_000_000 * scale))
+    elif name == "single_bubble":
+        w = synth.single_bubble(n_markers=int(50_000 * scale), n_particles=int(10_000_000 * scale))
+    elif name == "learned_index":
+        w = synth.learned_index(n_particles=int(100_000_000 * scale), n_markers=0)
+    else:
+        w = synth.tiny()
+    if rank:  # independent particles per rank (same tree)
+        w.particles = synth._uniform_points(w.seed + 1000 * rank, 3, w.particles.shape[1])
+    return w
+
+
+def describe(w, n_leaves, search):
+    return {
+        "workload": w.name,
+        "bubbles": int(w.spheres.shape[0]),
+        "levels": [w.lmin, w.lmax],
+        "leaves": int(n_leaves),
+        "markers_peskin4": int(w.markers.shape[1]),
+        "particles_trilinear": int(w.particles.shape[1]),
+        "search": search,
+        "index": "MLP root 1-32-1 + 4096 leaf linear models" if search == "learned" else "binary (smem-staged top levels)",
+        "spread": "Peskin-4 sorted deterministic",
+        "l2": "inputs larger than L2 (tree+field ~0.7 GB, points 1.2 GB); no flush",
+    }
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------------------
+
+def oracle_setup(w):
+    import oracle
+    t0 = time.time()
+    ko, lo = oracle.octree_build(w.spheres, w.lmin, w.lmax)
+    cen = oracle.leaf_centres(ko, lo)
+    from paper_2605_20565_gb300 import synth
+    field = synth.fourier_field(w.modes, cen) if w.modes is not None else synth.sin_field(cen)
+    return ko, lo, field.astype(np.float32).astype(np.float64), time.time() - t0
+
+
+def oracle_step(w, ko, lo, field, npart, nmark):
+    """locate + interpolate npart particles and nmark markers, spread nmark markers."""
+    import oracle
+    P = w.particles[:, :npart]
+    X = w.markers[:, :nmark]
+    t0 = time.perf_counter()
+    host = oracle.locate_ub(ko, lo, *P)
+    up = oracle.interp_trilinear(ko, lo, field, *P, host)
+    um = None
+    if nmark:
+        um, _ = oracle.interp_delta(ko, lo, w.lmax, 2, field, *X)
+        oracle.spread_delta(ko, lo, w.lmax, 2, *X, w.forces[:, :nmark])
+    return time.perf_counter() - t0, host, up, um
+
+
+def size_cpu_sample(w, ko, lo, field, seconds):
+    """Points per oracle step so that one step takes about `seconds`."""
+    n_p0 = min(200_000, w.particles.shape[1])
+    frac = w.markers.shape[1] / max(1, w.n_points)
+    n_m0 = min(int(n_p0 * frac), w.markers.shape[1])
+    dt, *_ = oracle_step(w, ko, lo, field, n_p0, n_m0)
+    k = max(1.0, seconds / max(dt, 1e-3))
+    n_p = min(int(n_p0 * k), w.particles.shape[1])
+    n_m = min(int(n_m0 * k), w.markers.shape[1])
+    return n_p, n_m
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    w = make_workload(args.workload, args.scale, 0)
+    ko, lo, field, setup_s = oracle_setup(w)
+    n_p, n_m = size_cpu_sample(w, ko, lo, field, min(args.cpu_seconds, 20.0) / max(1, args.steps + args.warmup) * 4)
+    times = []
+    for s in range(args.warmup + args.steps):
+        dt, *_ = oracle_step(w, ko, lo, field, n_p, n_m)
+        if s >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * statistics.median(times)
+    value = (n_p + n_m) / (ms / 1e3)
+    cores = oracle.num_threads()
+    sample = (f"{n_p} particles (trilinear) + {n_m} markers (Peskin-4 interp + spread) of {w.name} "
+              f"per step; oracle octree build {setup_s:.1f} s untimed")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": describe(w, ko.size, "binary (CPU, FP64)"),
+           "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# GPU path
+# ---------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import paper_2605_20565_gb300 as ot
+    from paper_2605_20565_gb300 import _build, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    if rank == 0 or not os.path.exists(_build.LIB):
+        _build.build()
+    if dist:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    w = make_workload(args.workload, args.scale, rank)
+    search = ot.OT_LEARNED if args.search == "learned" else ot.OT_BINARY
+    t0 = time.time()
+    tree = ot.ot_octree_build(w.spheres, w.lmin, w.lmax)
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    n_leaves = ot.ot_octree_info(tree)[0]
+    t0 = time.time()
+    ot.ot_index_train(tree, root=ot.OT_ROOT_MLP, n_leaf_models=4096, epochs=4, batch=65536, lr=1e-3, seed=1)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    istats = ot.ot_index_get_stats(tree, reset=True)
+
+    cen = ot.ot_octree_centres(tree)
+    if w.modes is not None:
+        field64 = synth.fourier_field(w.modes, cen.T.contiguous())
+    else:
+        field64 = torch.as_tensor(synth.sin_field(cen.T.cpu().numpy()), device=dev)
+    field = field64.to(torch.float32).contiguous()
+    del cen, field64
+
+    def to_dev(a):
+        return [torch.as_tensor(np.ascontiguousarray(a[d]), device=dev) for d in range(3)]
+
+    mx, my, mz = to_dev(w.markers)
+    px, py, pz = to_dev(w.particles)
+    Fm = torch.as_tensor(np.ascontiguousarray(w.forces, dtype=np.float32), device=dev)
+    n_m, n_p = w.markers.shape[1], w.particles.shape[1]
+    npts = n_m + n_p
+    um = torch.empty((3, n_m), dtype=torch.float32, device=dev)
+    up = torch.empty((3, n_p), dtype=torch.float32, device=dev)
+    f = torch.zeros((n_leaves, 4), dtype=torch.float32, device=dev)
+    mode = ot.OT_SORTED if args.spread == "sorted" else ot.OT_ATOMIC
+    ws_bytes = ot.ot_spread_workspace_size(tree, ot.OT_PESKIN4, n_m) if mode == ot.OT_SORTED else 0
+    ws = torch.empty(max(1, ws_bytes), dtype=torch.uint8, device=dev)
+    launch = None
+    if args.launch:
+        b, t, s, st = [int(v) for v in args.launch.split(",")]
+        launch = dict(block=b, tile=t, blocks_per_sm=s, stage_log2=st)
+    groups = [dict(kernel=ot.OT_PESKIN4, x=mx, y=my, z=mz, u=um), dict(kernel=ot.OT_TRILINEAR, x=px, y=py, z=pz, u=up)]
+    batch = ot.ot_batch_create(tree, groups, field, search=search, launch=launch)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        ot.ot_batch_run(batch)
+        if ev:
+            ev[1].record(stream)
+        f.zero_()
+        ot.ot_spread(tree, ot.OT_PESKIN4, mode, mx, my, mz, Fm, f, workspace=ws)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    assert ot.ot_last_error(tree) & (ot.OT_DEV_STENCIL | ot.OT_DEV_OUTSIDE | ot.OT_DEV_REFINED_CAP) == 0
+
+    # timed region
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = Clocks(local) if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = ot.ot_launch_count()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = ot.ot_launch_count() - launches0
+    clk = clocks.stop() if clocks else None
+    total_ms = max_over_ranks(start.elapsed_time(stop), dist, dev)
+    ms_step = total_ms / args.steps
+    batch_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    spread_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    value = job_value(npts, world, ms_step)
+    fb = ot.ot_index_get_stats(tree, reset=True)["fallbacks"]
+
+    # plain binary search, same batch shape (learned vs plain)
+    plain = None
+    if search == ot.OT_LEARNED:
+        bplain = ot.ot_batch_create(tree, groups, field, search=ot.OT_BINARY, launch=launch)
+        for _ in range(3):
+            ot.ot_batch_run(bplain)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            ot.ot_batch_run(bplain)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_batch_ms = a.elapsed_time(b) / args.steps
+        plain = {"batch_ms": plain_batch_ms, "points_per_s_locate_interp": npts / (plain_batch_ms / 1e3),
+                 "step_points_per_s": npts / ((plain_batch_ms + spread_ms) / 1e3)}
+        del bplain
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hm = [torch.from_numpy(np.ascontiguousarray(w.markers[d])).pin_memory() for d in range(3)]
+        hp = [torch.from_numpy(np.ascontiguousarray(w.particles[d])).pin_memory() for d in range(3)]
+        hum = torch.empty((3, n_m), dtype=torch.float32).pin_memory()
+        hup = torch.empty((3, n_p), dtype=torch.float32).pin_memory()
+        hf = torch.empty((n_leaves, 4), dtype=torch.float32).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in hm + hp)
+        d2h = (hum.numel() + hup.numel() + hf.numel()) * 4
+
+        def e2e_step():
+            for d in range(3):
+                (mx, my, mz)[d].copy_(hm[d], non_blocking=True)
+                (px, py, pz)[d].copy_(hp[d], non_blocking=True)
+            step()
+            hum.copy_(um, non_blocking=True)
+            hup.copy_(up, non_blocking=True)
+            hf.copy_(f, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        k_e2e = max(3, min(args.steps, 10))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / k_e2e, dist, dev)
+        e2e = {"value": job_value(npts, world, e2e_ms), "unit": "points/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": k_e2e}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = measured_peaks()
+    alg_bytes = npts * BYTES_PER_POINT + n_leaves * BYTES_PER_LEAF
+    achieved = alg_bytes / (batch_ms / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "k_batch_traffic.json")
+    if os.path.exists(prof):
+        d = json.load(open(prof))
+        if d.get("workload") == w.name and d.get("search") == args.search and d.get("valid", False):
+            traffic = d.get("bytes_per_launch")
+    roof = {"bound": "hbm", "kernel": "k_batch (locate + interpolate, persistent, graph)", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(alg_bytes),
+            "bytes_rule": f"{BYTES_PER_POINT} B/point + {BYTES_PER_LEAF} B/leaf"}
+
+    cpu = None
+    parity = None
+    if not args.no_cpu_baseline:
+        import oracle
+        ko, lo, fref, setup_s = oracle_setup(w)
+        kg, lg = ot.ot_octree_copy_leaves(tree)
+        tree_exact = bool(np.array_equal(kg.cpu().numpy().view(np.uint64), ko) and
+                          np.array_equal(lg.cpu().numpy(), lo))
+        n_ps, n_ms = size_cpu_sample(w, ko, lo, fref, args.cpu_seconds)
+        dt, host_ref, up_ref, um_ref = oracle_step(w, ko, lo, fref, n_ps, n_ms)
+        cpu = {"value": (n_ps + n_ms) / dt, "unit": "points/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{n_ps} particles + {n_ms} markers of {w.name} (locate, interpolate, spread), "
+                         f"one step, {dt:.1f} s; oracle tree build {setup_s:.1f} s untimed"}
+        # sampled parity of the timed launch's outputs (same field values, FP32 inputs)
+        fscale = float(np.abs(fref[:, :3]).max())
+        hp_gpu = ot.ot_locate(tree, px[:n_ps], py[:n_ps], pz[:n_ps], search=search).cpu().numpy()
+        parity = {"octree_bit_exact": tree_exact,
+                  "hosts_bit_exact": bool(np.array_equal(hp_gpu, host_ref)),
+                  "particles_max_rel_err": float(np.abs(up[:, :n_ps].cpu().numpy() - up_ref).max() / fscale),
+                  "markers_max_rel_err": (float(np.abs(um[:, :n_ms].cpu().numpy() - um_ref).max() / fscale)
+                                          if n_ms else None),
+                  "sampled_points": n_ps + n_ms}
+
+    out = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": describe(w, n_leaves, args.search), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": int(launches), "clocks": clk,
+           "breakdown_ms": {"locate_interpolate": batch_ms, "spread": spread_ms, "step": ms_step},
+           "locate_interpolate_points_per_s": world * npts / (batch_ms / 1e3),
+           "plain": plain,
+           "learned_speedup_locate_interp": (plain["batch_ms"] / batch_ms) if plain else None,
+           "index": {"mean_window": istats["mean_window"], "max_window": istats["max_window"],
+                     "empty_models": istats["empty_models"], "fallbacks_timed": fb,
+                     "final_loss": istats["final_loss"], "train_s": train_s},
+           "setup_s": {"octree_build": build_s, "index_train": train_s},
+           "parity": parity}
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

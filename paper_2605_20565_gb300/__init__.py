@@ -313,16 +313,13 @@ def ot_spread_workspace_size(tree: Octree, kernel: int, n: int) -> int:
 def _spread(fn, dtype, tree, kernel, mode, x, y, z, F, f, dV, workspace, stream):
     torch = _torch()
     n, px, py, pz = _xyz(x, y, z)
-    ws_bytes = 0
-    if mode == OT_SORTED:
-        ws_bytes = ot_spread_workspace_size(tree, kernel, n)
-        if workspace is None:
-            workspace = torch.empty(max(1, (ws_bytes + 15) // 16), dtype=torch.float64, device="cuda").view(
-                torch.uint8)
-        elif workspace.numel() * workspace.element_size() < ws_bytes:
-            raise ValueError("workspace too small")
+    have = 0
+    if mode == OT_SORTED and workspace is None:
+        workspace = torch.empty(max(1, ot_spread_workspace_size(tree, kernel, n)), dtype=torch.uint8, device="cuda")
+    if workspace is not None:
+        have = workspace.numel() * workspace.element_size()  # the real size; the library checks it
     _check(fn(tree.handle, kernel, mode, px, py, pz, _dptr(F, dtype, "F"), _dptr(dV, dtype, "dV"), n,
-              _dptr(f, dtype, "f"), _dptr(workspace, None, "workspace"), ws_bytes, _stream(stream)))
+              _dptr(f, dtype, "f"), _dptr(workspace, None, "workspace"), have, _stream(stream)))
     return f
 
 

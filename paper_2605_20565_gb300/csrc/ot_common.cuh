@@ -186,7 +186,7 @@ __device__ __forceinline__ void load_sample(const TreeView& t, uint64_t* s) {
 
 // ------------------------------------------------------------------------------------------
 // Discrete delta functions (Sec. 2.2), argument in grid units.  Square-root arguments are
-// written in the factored forms 2 - (2a-1)^2, 1 - (2a-3)^2 (Peskin) and 1 - 3(1-a)^2 (Roma),
+// written in the factored forms 2 - (2a-1)^2, 2 - (2a-3)^2 (Peskin) and 1 - 3(1-a)^2 (Roma),
 // which equal the printed polynomials and lose less to cancellation in FP32.
 // ------------------------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ T dsqrt(T v);
@@ -201,7 +201,7 @@ template <typename T> __device__ __forceinline__ T phi_peskin4(T r) {
     }
     if (a <= T(2)) {
         T e = T(2) * a - T(3);
-        return (T(5) - T(2) * a - dsqrt<T>(T(1) - e * e)) * T(0.125);
+        return (T(5) - T(2) * a - dsqrt<T>(T(2) - e * e)) * T(0.125);
     }
     return T(0);
 }

@@ -246,6 +246,7 @@ def test_delta_interp(ot, tiny, tiny_fields, kernel, search, torch_mod):
     w, ko, lo, tree = tiny
     if search == 1:
         ot.ot_index_train(tree, root=ot.OT_ROOT_LINEAR, n_leaf_models=128)
+    ot.ot_last_error(tree)  # clear bits left by earlier tests
     X = w.markers
     for fname in ("sin", "linear"):
         f64 = tiny_fields[fname]
