@@ -60,20 +60,25 @@ __global__ void __launch_bounds__(256) k_batch(TreeView t, RootModel rm, BatchAr
         const int64_t base = ((int64_t)tl - gr.tile0) * tile_pts;
         for (int j = 0; j < a.tile; ++j) {
             const int64_t i = base + (int64_t)j * 32 + lane;
-            if (i >= gr.n) break;
+            const bool active = i < gr.n;
+            if (!__any_sync(0xffffffffu, active)) break;  // warp-uniform
             float o[3];
             int h;
-            const double x = gr.x[i], y = gr.y[i], z = gr.z[i];
+            const double x = active ? gr.x[i] : 0.0, y = active ? gr.y[i] : 0.0, z = active ? gr.z[i] : 0.0;
             if (gr.kernel == OT_TRILINEAR)
-                h = trilinear_point<float, LEARNED>(t, rm, ss, field, x, y, z, -1, o);
+                h = trilinear_warp<float, LEARNED>(t, rm, ss, field, active, x, y, z, -1, o);
+            else if (!active)
+                h = -1;
             else if (gr.kernel == OT_PESKIN4)
                 h = delta_point<float, OT_PESKIN4, LEARNED>(t, rm, ss, field, x, y, z, gr.host != nullptr, o);
             else
                 h = delta_point<float, OT_ROMA3, LEARNED>(t, rm, ss, field, x, y, z, gr.host != nullptr, o);
-            gr.u[i] = o[0];
-            gr.u[gr.n + i] = o[1];
-            gr.u[2 * gr.n + i] = o[2];
-            if (gr.host) gr.host[i] = h;
+            if (active) {
+                gr.u[i] = o[0];
+                gr.u[gr.n + i] = o[1];
+                gr.u[2 * gr.n + i] = o[2];
+                if (gr.host) gr.host[i] = h;
+            }
         }
     }
 }

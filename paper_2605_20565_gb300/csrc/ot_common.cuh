@@ -45,16 +45,62 @@ __host__ __device__ __forceinline__ void demorton3(uint64_t k, uint32_t& x, uint
 // Number of MAXLEVEL keys covered by a leaf of level l: 8^(21-l).
 __host__ __device__ __forceinline__ uint64_t key_span(int l) { return 1ULL << (3 * (MAXLEVEL - l)); }
 
-// FP64 quantisation (Algorithm 1, get_cell_at at MAXLEVEL): q = floor(x 2^21) per axis.  The
-// scaling by a power of two is exact and the conversion truncates, so a point on a face
-// lands in the upper cell exactly as in an FP64 CPU evaluation.  False outside [0,1)^3 / NaN.
-__device__ __forceinline__ bool quantise(double x, double y, double z, uint32_t& qx, uint32_t& qy, uint32_t& qz) {
-    if (!(x >= 0.0 && x < 1.0 && y >= 0.0 && y < 1.0 && z >= 0.0 && z < 1.0)) return false;
-    qx = __double2uint_rz(x * 2097152.0);
-    qy = __double2uint_rz(y * 2097152.0);
-    qz = __double2uint_rz(z * 2097152.0);
+// ------------------------------------------------------------------------------------------
+// Exact fixed-point coordinates, integer operations only.
+// X = floor(x 2^53) is read off the IEEE-754 bits of x: every cell index and in-cell fraction
+// the path needs is a shift of X, so the integer cell of a point (Algorithm 1, get_cell_at:
+// floor(x 2^level)) is exactly the FP64 floor, faces go to the upper cell, and no FP64
+// arithmetic (a slow pipe on this GPU) is spent on it.
+// ------------------------------------------------------------------------------------------
+// False for x outside [0,1) or NaN; -0.0 counts as 0 (it compares equal to 0).
+__device__ __forceinline__ bool fixpoint(double x, uint64_t& X) {
+    const uint64_t u = (uint64_t)__double_as_longlong(x);
+    X = 0;
+    if (u == 0x8000000000000000ULL) return true;  // -0.0
+    if (u >> 63) return false;                      // negative
+    const int e = (int)(u >> 52);                   // biased exponent
+    if (e >= 1023) return false;                    // >= 1, inf, NaN
+    if (e == 0) return true;                        // +0, subnormal: floor(x 2^53) = 0
+    const uint64_t m = (u & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+    const int sh = 1022 - e;                        // x 2^53 = m 2^(e - 1022)
+    X = sh >= 64 ? 0 : (m >> sh);
     return true;
 }
+__device__ __forceinline__ bool fixpoint3(double x, double y, double z, uint64_t X[3]) {
+    const bool a = fixpoint(x, X[0]), b = fixpoint(y, X[1]), c = fixpoint(z, X[2]);
+    return a && b && c;
+}
+// floor(x 2^l), l <= 21.
+__device__ __forceinline__ uint32_t fix_cell(uint64_t X, int l) { return (uint32_t)(X >> (53 - l)); }
+// The top 24 bits of the fraction of x 2^l.
+__device__ __forceinline__ uint32_t fix_frac24(uint64_t X, int l) { return (uint32_t)(X >> (29 - l)) & 0xFFFFFFu; }
+// Offset from the centre of the level-l cell, frac(x 2^l) - 1/2: exact in FP64 from all bits,
+// from the top 24 fraction bits in FP32 (itself exact: 24 significant bits).
+template <typename T> __device__ __forceinline__ T fix_offset(uint64_t X, int l);
+template <> __device__ __forceinline__ float fix_offset<float>(uint64_t X, int l) {
+    return __fmaf_rn((float)fix_frac24(X, l), 0x1p-24f, -0.5f);
+}
+template <> __device__ __forceinline__ double fix_offset<double>(uint64_t X, int l) {
+    const uint64_t f = X & ((1ULL << (53 - l)) - 1ULL);
+    return ldexp((double)f, l - 53) - 0.5;
+}
+// Whether the point lies in the upper half of its level-l cell (offset >= 0): one bit of X.
+__device__ __forceinline__ bool fix_upper_half(uint64_t X, int l) { return (X >> (52 - l)) & 1ULL; }
+
+// Unsigned 64-bit integer -> float, rounding toward zero, built from the bits (no 64-bit
+// conversion instruction).  Used identically at index training and query time.
+__device__ __forceinline__ float u64_to_float_rz(uint64_t v) {
+    if (v == 0) return 0.0f;
+    const int lz = __clzll((long long)v);
+    const int e = 63 - lz;                                   // position of the leading one
+    const uint32_t mant = (uint32_t)((v << lz) >> 40) & 0x7FFFFFu;  // 23 bits after it
+    return __int_as_float(((e + 127) << 23) | (int)mant);
+}
+__device__ __forceinline__ float i64_to_float_rz(int64_t v) {
+    return v < 0 ? -u64_to_float_rz(0ULL - (uint64_t)v) : u64_to_float_rz((uint64_t)v);
+}
+// 2^-k as float for 0 <= k < 126.
+__device__ __forceinline__ float exp2_neg(int k) { return __int_as_float((127 - k) << 23); }
 
 // ------------------------------------------------------------------------------------------
 // Views passed by value to kernels.
@@ -126,14 +172,17 @@ __device__ __forceinline__ int search_plain(const TreeView& t, const uint64_t* s
     return search_range(t.key, lo, len, q);
 }
 
+// Input of the root model: key 2^-63 in FP32 (rounded toward zero).
+__device__ __forceinline__ float key_to_x(uint64_t q) { return u64_to_float_rz(q) * 0x1p-63f; }
+
 // Root model: predicted fractional position y ~ i/N of key q.
 __device__ __forceinline__ float root_predict(const RootModel& r, uint64_t q) {
-    float x = __fmul_rn(__ull2float_rn(q), 0x1p-63f);
+    const float x = key_to_x(q);
     if (r.kind == OT_ROOT_LINEAR) return __fadd_rn(r.a, __fmul_rn(r.b, x));
     float y = r.b2;
 #pragma unroll
     for (int k = 0; k < MLP_H; ++k) {
-        float z = __fadd_rn(__fmul_rn(r.w1[k], x), r.b1[k]);
+        const float z = __fadd_rn(__fmul_rn(r.w1[k], x), r.b1[k]);
         y = __fadd_rn(y, __fmul_rn(r.w2[k], fmaxf(z, 0.0f)));
     }
     return y;
@@ -144,11 +193,13 @@ __device__ __forceinline__ int root_route(const RootModel& r, uint64_t q) {
     return (int)y; // y >= 0: truncation is floor
 }
 // Leaf model prediction (integer), the same arithmetic at training and query time:
-// first + floor(slope (q - base) + icpt), clamped to [0, n).
+// first + floor(slope (q - base) + icpt), clamped to the model's own index range widened by
+// one on each side (the answer for a key routed here lies there unless routing is not
+// monotone, which the search verifies), then to [0, n).
 __device__ __forceinline__ int leaf_predict(const LeafModel& m, uint64_t q, int n) {
-    const float off = __ll2float_rn((long long)(q - m.base));
+    const float off = i64_to_float_rz((int64_t)(q - m.base));
     float p = __fadd_rn(__fmul_rn(m.slope, off), m.icpt);
-    p = fminf(fmaxf(p, -1.0e9f), 1.0e9f);
+    p = fminf(fmaxf(p, -1.0f), (float)m.count);
     const int pc = m.first + (int)floorf(p);
     return min(max(pc, 0), n - 1);
 }
@@ -215,16 +266,22 @@ template <typename T> __device__ __forceinline__ T phi_roma3(T r) {
     return T(0);
 }
 
-// Stencil of one axis for a point at fine coordinate s = X 2^lmax - 1/2 (cell c centred at s = c).
+// Stencil of one axis on the finest level.  With the point's finest cell c, the upper-half bit
+// hi and the offset t = frac - 1/2 from the cell centre (cell j is centred at s = j when
+// s = X 2^lmax - 1/2):
+//   Peskin-4: cells floor(s) - 1 .. floor(s) + 2, floor(s) = c - 1 + hi; r_a = (2 - hi - a) + t;
+//   Roma-3:   cells c - 1 .. c + 1 (nearest centre and its neighbours); r_a = (1 - a) + t.
 template <int KERNEL> struct Stencil;
 template <> struct Stencil<OT_PESKIN4> {
     static constexpr int W = 4;
-    __device__ static int first(double s) { return (int)floor(s) - 1; }
+    __device__ static int first(int c, int hi) { return c - 2 + hi; }
+    template <typename T> __device__ static T r(int a, int hi, T t) { return (T)(2 - hi - a) + t; }
     template <typename T> __device__ static T phi(T r) { return phi_peskin4<T>(r); }
 };
 template <> struct Stencil<OT_ROMA3> {
     static constexpr int W = 3;
-    __device__ static int first(double s) { return (int)floor(s + 0.5) - 1; }
+    __device__ static int first(int c, int hi) { (void)hi; return c - 1; }
+    template <typename T> __device__ static T r(int a, int hi, T t) { (void)hi; return (T)(1 - a) + t; }
     template <typename T> __device__ static T phi(T r) { return phi_roma3<T>(r); }
 };
 

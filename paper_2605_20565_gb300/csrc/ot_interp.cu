@@ -20,10 +20,11 @@ __global__ void __launch_bounds__(256) k_locate(TreeView t, RootModel rm, const 
     const uint64_t* ss = staged ? s_sample : nullptr;
     unsigned miss = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t qx, qy, qz;
+        uint64_t X[3];
         int h = -1;
-        if (quantise(x[i], y[i], z[i], qx, qy, qz))
-            h = search<LEARNED>(t, rm, ss, morton3(qx, qy, qz));
+        if (fixpoint3(x[i], y[i], z[i], X))
+            h = search<LEARNED>(t, rm, ss,
+                                morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32)));
         else
             ++miss;
         host[i] = h;
@@ -44,22 +45,33 @@ __global__ void __launch_bounds__(256) k_trilinear(TreeView t, RootModel rm, con
     const bool staged = t.nsample > 1;
     if (staged) load_sample(t, s_sample);
     const uint64_t* ss = staged ? s_sample : nullptr;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    // warp-aligned iteration: every lane of a warp runs the same trip count (the trilinear
+    // routine is warp-cooperative)
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp0 * 32; base < n; base += nwarps * 32) {
+        const int64_t i = base + lane;
+        const bool inr = i < n;
         T o[3];
-        const int hin = host_in ? host_in[i] : -1;
-        int h;
-        if (host_in && (hin < 0 || hin >= t.n)) {
-            // no host (outside the cube) or an index that is not a leaf: no value
-            o[0] = o[1] = o[2] = qnan<T>();
-            if (hin >= t.n) atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
-            h = -1;
-        } else {
-            h = trilinear_point<T, LEARNED>(t, rm, ss, field, x[i], y[i], z[i], hin, o);
+        int hin = -1;
+        bool active = inr;
+        if (inr && host_in) {
+            hin = host_in[i];
+            if (hin < 0 || hin >= t.n) {
+                // no host (outside the cube) or an index that is not a leaf: no value
+                if (hin >= t.n) atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
+                active = false;
+            }
         }
-        u[i] = o[0];
-        u[n + i] = o[1];
-        u[2 * n + i] = o[2];
-        if (host_out) host_out[i] = h;
+        const int h = trilinear_warp<T, LEARNED>(t, rm, ss, field, active, inr ? x[i] : 0.0, inr ? y[i] : 0.0,
+                                                 inr ? z[i] : 0.0, hin, o);
+        if (inr) {
+            u[i] = o[0];
+            u[n + i] = o[1];
+            u[2 * n + i] = o[2];
+            if (host_out) host_out[i] = h;
+        }
     }
 }
 

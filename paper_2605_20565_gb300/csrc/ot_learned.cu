@@ -20,8 +20,6 @@ namespace {
 #define GSTRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-__device__ __forceinline__ float key_to_x(uint64_t k) { return __fmul_rn(__ull2float_rn(k), 0x1p-63f); }
-
 // Block sum of `v` (doubles), result valid in thread 0.  Fixed reduction order.
 template <int NT>
 __device__ double block_sum_d(double v, double* s) {

@@ -1,11 +1,13 @@
-// ot_points.cuh -- per-point device routines: host search, trilinear interpolation with
-// level-mates, delta-kernel interpolation and stencil enumeration.  Used by the single-op
-// kernels, the persistent batched kernel and the spreading kernels.
+// ot_points.cuh -- per-point device routines: trilinear interpolation with level-mates,
+// delta-kernel interpolation and stencil enumeration, all on exact fixed-point coordinates.
+// Used by the single-op kernels, the persistent batched kernel and the spreading kernels.
 #pragma once
 
 #include "ot_common.cuh"
 
 namespace ot {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
 
 __device__ __forceinline__ int floordiv2(int v) { return v >> 1; } // arithmetic shift: floor
 
@@ -13,40 +15,83 @@ template <typename T> __device__ __forceinline__ T qnan();
 template <> __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
 template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
 
-// Trilinear interpolation at one point (Sec. 2.3.2) with the level-mate rule:
-//   host leaf of level l, cell c; t_d = x_d 2^l - (c_d + 1/2); s_d = sign(t_d) (+1 at 0);
-//   level-mates c + {0, s_d}; weights prod (1 - |t_d|) or |t_d|;
-//   level-mate value: leaf of level l -> its value; inside a coarser leaf -> that leaf's value;
-//   refined -> volume-weighted mean of its leaves; outside the cube -> host index on that axis.
-// Returns the host leaf (-1 outside the cube; out = NaN).
-template <typename T, bool LEARNED>
-__device__ __forceinline__ int trilinear_point(const TreeView& t, const RootModel& rm, const uint64_t* s_sample,
-                                               const T* __restrict__ field, double x, double y, double z, int host_in,
-                                               T out[3]) {
-    using V = Vec4<T>;
-    uint32_t q[3];
-    if (!quantise(x, y, z, q[0], q[1], q[2])) {
-        out[0] = out[1] = out[2] = qnan<T>();
-        atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
-        return -1;
-    }
-    const int h = host_in >= 0 ? host_in : search<LEARNED>(t, rm, s_sample, morton3(q[0], q[1], q[2]));
-    const int l = t.level[h];
-    const int sh = MAXLEVEL - l;
-    const int ncell = 1 << l;
-    const double p[3] = {x, y, z};
-    const double sc = (double)ncell;
-    int c[3], sg[3];
-    T at[3];
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        c[d] = (int)(q[d] >> sh);
-        const double td = p[d] * sc - ((double)c[d] + 0.5);
-        sg[d] = td >= 0.0 ? 1 : -1;
-        at[d] = (T)fabs(td);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+// Volume-weighted sum over the leaves [a, ...) whose keys are below `end`, weight 8^-(level-l):
+// the value of a refined level-mate of level l (the coalescence average of Sec. 2.1.1).  The
+// whole warp works on one range at a time, 32 consecutive leaves per step; every lane gets the
+// sum.  Must be reached by all 32 lanes together.  Bounded by OT_REFINED_CAP leaves.
+template <typename T>
+__device__ __forceinline__ void warp_range_mean(const TreeView& t, const T* __restrict__ field, int a, uint64_t end,
+                                                int l, T& s0, T& s1, T& s2, bool& capped) {
+    using V = Vec4<T>;
+    const int lane = threadIdx.x & 31;
+    T p0 = T(0), p1 = T(0), p2 = T(0);
+    int b = a + lane;
+    bool done = false;
+    for (int it = 0; it < OT_REFINED_CAP / 32; ++it) {
+        bool in = false;
+        if (b < t.n) in = ldg_key(t.key + b) < end;
+        if (in) {
+            const T vol = (T)exp2_neg(3 * ((int)t.level[b] - l));
+            const auto f = V::load(field, b);
+            p0 += vol * f.x;
+            p1 += vol * f.y;
+            p2 += vol * f.z;
+        }
+        if (__ballot_sync(FULL_MASK, in) != FULL_MASK) {  // sorted keys: the range ended here
+            done = true;
+            break;
+        }
+        b += 32;
     }
-    T acc0 = T(0), acc1 = T(0), acc2 = T(0);
+    if (!done) capped = true;
+    s0 = warp_sum(p0);
+    s1 = warp_sum(p1);
+    s2 = warp_sum(p2);
+}
+
+// Trilinear interpolation at one point per lane (Sec. 2.3.2) with the level-mate rule:
+//   host leaf of level l, cell c; t_d = offset from the cell centre; s_d = +1 if t_d >= 0;
+//   level-mates c + {0, s_d}; weights prod (1 - |t_d|) or |t_d|;
+//   level-mate value: leaf of level l -> its value; inside a coarser leaf -> that leaf's
+//   value; refined -> volume-weighted mean of its leaves; outside the cube -> the host's
+//   index on that axis.
+// All 32 lanes of the warp must call this together; lanes with active == false idle.
+// Returns the host leaf (-1 when inactive or outside the cube, out = NaN).
+template <typename T, bool LEARNED>
+__device__ __forceinline__ int trilinear_warp(const TreeView& t, const RootModel& rm, const uint64_t* s_sample,
+                                              const T* __restrict__ field, bool active, double x, double y, double z,
+                                              int host_in, T out[3]) {
+    using V = Vec4<T>;
+    const int lane = threadIdx.x & 31;
+    uint64_t X[3] = {0, 0, 0};
+    bool ok = active && fixpoint3(x, y, z, X);
+    if (active && !ok) atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
+    int h = -1, l = 0, c[3] = {0, 0, 0}, sg[3] = {1, 1, 1}, ncell = 1;
+    T at[3] = {T(0), T(0), T(0)};
+    if (ok) {
+        h = host_in >= 0 ? host_in
+                         : search<LEARNED>(t, rm, s_sample,
+                                           morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32)));
+        l = t.level[h];
+        ncell = 1 << l;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            c[d] = (int)fix_cell(X[d], l);
+            sg[d] = fix_upper_half(X[d], l) ? 1 : -1;
+            const T td = fix_offset<T>(X[d], l);
+            at[d] = td < T(0) ? -td : td;
+        }
+    }
+    const int sh = MAXLEVEL - l;
     const uint64_t span = key_span(l);
+    T acc0 = T(0), acc1 = T(0), acc2 = T(0);
+    bool capped = false;
 #pragma unroll 1
     for (int corner = 0; corner < 8; ++corner) {
         int m[3];
@@ -61,37 +106,41 @@ __device__ __forceinline__ int trilinear_point(const TreeView& t, const RootMode
             self = self && (v == c[d]);
             w *= off ? at[d] : T(1) - at[d];
         }
-        T v0, v1, v2;
-        if (self) {
-            auto f = V::load(field, h);
-            v0 = f.x, v1 = f.y, v2 = f.z;
-        } else {
-            const uint64_t anchor =
-                morton3((uint32_t)m[0] << sh, (uint32_t)m[1] << sh, (uint32_t)m[2] << sh);
-            const int a = search<LEARNED>(t, rm, s_sample, anchor);
-            const int la = t.level[a];
-            if (la <= l) {
-                auto f = V::load(field, a);
-                v0 = f.x, v1 = f.y, v2 = f.z;
-            } else {
-                // refined: leaves with keys in [anchor, anchor + span), weight 8^-(level - l)
-                v0 = v1 = v2 = T(0);
-                const uint64_t end = anchor + span;
-                int b = a, it = 0;
-                for (; b < t.n && it < OT_REFINED_CAP; ++b, ++it) {
-                    if (ldg_key(t.key + b) >= end) break;
-                    const T vol = (T)ldexp(1.0, -3 * ((int)t.level[b] - l));
-                    auto f = V::load(field, b);
-                    v0 += vol * f.x;
-                    v1 += vol * f.y;
-                    v2 += vol * f.z;
-                }
-                if (it >= OT_REFINED_CAP) atomicOr(t.err, (unsigned)OT_DEV_REFINED_CAP);
+        T v0 = T(0), v1 = T(0), v2 = T(0);
+        bool refined = false;
+        int a = h;
+        uint64_t end = 0;
+        if (ok) {
+            if (!self) {
+                const uint64_t anchor = morton3((uint32_t)m[0] << sh, (uint32_t)m[1] << sh, (uint32_t)m[2] << sh);
+                a = search<LEARNED>(t, rm, s_sample, anchor);
+                refined = (int)t.level[a] > l;
+                end = anchor + span;
             }
+            if (!refined) {
+                const auto f = V::load(field, a);
+                v0 = f.x, v1 = f.y, v2 = f.z;
+            }
+        }
+        unsigned pend = __ballot_sync(FULL_MASK, refined);
+        while (pend) {
+            const int owner = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int ao = __shfl_sync(FULL_MASK, a, owner);
+            const uint64_t eo = __shfl_sync(FULL_MASK, end, owner);
+            const int lo_ = __shfl_sync(FULL_MASK, l, owner);
+            T r0, r1, r2;
+            warp_range_mean<T>(t, field, ao, eo, lo_, r0, r1, r2, capped);
+            if (lane == owner) v0 = r0, v1 = r1, v2 = r2;
         }
         acc0 += w * v0;
         acc1 += w * v1;
         acc2 += w * v2;
+    }
+    if (capped) atomicOr(t.err, (unsigned)OT_DEV_REFINED_CAP);
+    if (!ok) {
+        out[0] = out[1] = out[2] = qnan<T>();
+        return -1;
     }
     out[0] = acc0;
     out[1] = acc1;
@@ -99,17 +148,40 @@ __device__ __forceinline__ int trilinear_point(const TreeView& t, const RootMode
     return h;
 }
 
-// Delta-kernel stencil around one point on the finest level.  For every parent block (2x2x2
-// cells of level lmax) that overlaps the stencil, one search finds its first child; a parent
-// whose first child is a leaf of level lmax has all 8 children as consecutive leaves.  The
-// visitor gets (leaf, weight index ax, ay, az) for each valid stencil cell.  Returns false
-// when some stencil cell was outside the cube or not a finest-level leaf.
+// Stencil origin and per-axis weights of a point with fixed-point coordinates X on the
+// finest level lmax (Sec. 2.2: W(x) = prod phi(x_d/dx)/dx).
+template <int K, typename T>
+__device__ __forceinline__ void stencil_weights(int lmax, const uint64_t X[3], int i0[3], T w[3][Stencil<K>::W]) {
+    constexpr int W = Stencil<K>::W;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int c = (int)fix_cell(X[d], lmax);
+        const int hi = fix_upper_half(X[d], lmax) ? 1 : 0;
+        const T t = fix_offset<T>(X[d], lmax);
+        i0[d] = Stencil<K>::first(c, hi);
+#pragma unroll
+        for (int a = 0; a < W; ++a) w[d][a] = Stencil<K>::template phi<T>(Stencil<K>::template r<T>(a, hi, t));
+    }
+}
+
+// One axis weight of stencil slot a (used when a pair is reduced on its own).
+template <int K, typename T>
+__device__ __forceinline__ T stencil_weight_1d(int lmax, uint64_t X, int a) {
+    const int hi = fix_upper_half(X, lmax) ? 1 : 0;
+    return Stencil<K>::template phi<T>(Stencil<K>::template r<T>(a, hi, fix_offset<T>(X, lmax)));
+}
+
+// Delta-kernel stencil on the finest level.  For every parent block (2x2x2 cells of level
+// lmax) overlapping the stencil, one search finds its first child; a parent whose first child
+// is a leaf of level lmax has all 8 children as consecutive leaves.  The visitor gets
+// (leaf, ax, ay, az) for each valid stencil cell.  Returns false when some stencil cell was
+// outside the cube or not a finest-level leaf (its weight is dropped).
 template <int K, bool LEARNED, typename Visit>
 __device__ __forceinline__ bool visit_stencil(const TreeView& t, const RootModel& rm, const uint64_t* s_sample,
                                               const int i0[3], Visit&& visit) {
     constexpr int W = Stencil<K>::W;
-    const int lp = t.lmax - 1;          // parent level
-    const int np_cells = 1 << lp;       // parents per axis
+    const int lp = t.lmax - 1;     // parent level
+    const int np_cells = 1 << lp;  // parents per axis
     const int shp = MAXLEVEL - lp;
     int p0[3], pn[3];
 #pragma unroll
@@ -125,7 +197,7 @@ __device__ __forceinline__ bool visit_stencil(const TreeView& t, const RootModel
                 const bool inside = P[0] >= 0 && P[1] >= 0 && P[2] >= 0 && P[0] < np_cells && P[1] < np_cells &&
                                     P[2] < np_cells;
                 int a0 = -1;
-                if (inside && t.lmax > 0) {
+                if (inside) {
                     const uint64_t anchor =
                         morton3((uint32_t)P[0] << shp, (uint32_t)P[1] << shp, (uint32_t)P[2] << shp);
                     const int a = search<LEARNED>(t, rm, s_sample, anchor);
@@ -147,21 +219,6 @@ __device__ __forceinline__ bool visit_stencil(const TreeView& t, const RootModel
     return ok_all;
 }
 
-// Stencil origin and per-axis weights of a point at X (finest spacing 2^-lmax).
-template <int K, typename T>
-__device__ __forceinline__ void stencil_weights(int lmax, double x, double y, double z, int i0[3],
-                                                T w[3][Stencil<K>::W]) {
-    constexpr int W = Stencil<K>::W;
-    const double sc = ldexp(1.0, lmax);
-    const double s[3] = {x * sc - 0.5, y * sc - 0.5, z * sc - 0.5};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        i0[d] = Stencil<K>::first(s[d]);
-#pragma unroll
-        for (int a = 0; a < W; ++a) w[d][a] = Stencil<K>::template phi<T>((T)(s[d] - (double)(i0[d] + a)));
-    }
-}
-
 // Delta-kernel interpolation at one marker (Sec. 2.2, Eq. ibm_interpolate).  Returns the host
 // leaf (-1 outside the cube).
 template <typename T, int K, bool LEARNED>
@@ -170,30 +227,32 @@ __device__ __forceinline__ int delta_point(const TreeView& t, const RootModel& r
                                            T out[3]) {
     using V = Vec4<T>;
     constexpr int W = Stencil<K>::W;
-    uint32_t q[3];
-    if (!quantise(x, y, z, q[0], q[1], q[2])) {
+    uint64_t X[3];
+    if (!fixpoint3(x, y, z, X)) {
         out[0] = out[1] = out[2] = qnan<T>();
         atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
         return -1;
     }
     int i0[3];
     T w[3][W];
-    stencil_weights<K, T>(t.lmax, x, y, z, i0, w);
-    // host cell of level lmax: floor(X 2^lmax), one of the stencil cells
-    const int sh = MAXLEVEL - t.lmax;
-    const int hc[3] = {(int)(q[0] >> sh) - i0[0], (int)(q[1] >> sh) - i0[1], (int)(q[2] >> sh) - i0[2]};
+    stencil_weights<K, T>(t.lmax, X, i0, w);
+    // host: the finest cell holding X, one of the stencil cells
+    const int hc[3] = {(int)fix_cell(X[0], t.lmax) - i0[0], (int)fix_cell(X[1], t.lmax) - i0[1],
+                       (int)fix_cell(X[2], t.lmax) - i0[2]};
     int host = -1;
     T a0 = T(0), a1 = T(0), a2 = T(0);
     const bool ok = visit_stencil<K, LEARNED>(t, rm, s_sample, i0, [&](int leaf, int ax, int ay, int az) {
         const T wt = w[0][ax] * w[1][ay] * w[2][az];
-        auto f = V::load(field, leaf);
+        const auto f = V::load(field, leaf);
         a0 += wt * f.x;
         a1 += wt * f.y;
         a2 += wt * f.z;
         if (ax == hc[0] && ay == hc[1] && az == hc[2]) host = leaf;
     });
     if (!ok) atomicOr(t.err, (unsigned)OT_DEV_STENCIL);
-    if (want_host && host < 0) host = search_plain(t, s_sample, morton3(q[0], q[1], q[2]));
+    if (want_host && host < 0)
+        host = search_plain(t, s_sample,
+                            morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32)));
     out[0] = a0;
     out[1] = a1;
     out[2] = a2;

@@ -43,14 +43,14 @@ __global__ void __launch_bounds__(256) k_spread_atomic(TreeView t, RootModel rm,
     const uint64_t* ss = staged ? s_sample : nullptr;
     constexpr int W = Stencil<K>::W;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t q[3];
-        if (!quantise(x[k], y[k], z[k], q[0], q[1], q[2])) {
+        uint64_t X[3];
+        if (!fixpoint3(x[k], y[k], z[k], X)) {
             atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
             continue;
         }
         int i0[3];
         T w[3][W];
-        stencil_weights<K, T>(t.lmax, x[k], y[k], z[k], i0, w);
+        stencil_weights<K, T>(t.lmax, X, i0, w);
         const T vol = marker_volume(dV, k, t.lmax);
         const T F0 = F[k] * vol, F1 = F[n + k] * vol, F2 = F[2 * n + k] * vol;
         const bool ok = visit_stencil<K, false>(t, rm, ss, i0, [&](int leaf, int ax, int ay, int az) {
@@ -74,15 +74,14 @@ __global__ void __launch_bounds__(256) k_spread_emit(TreeView t, RootModel rm, c
         uint64_t* out = pairs + k * W3;
         const uint64_t id0 = (uint64_t)k * W3;
         for (int sl = 0; sl < W3; ++sl) out[sl] = (INVALID_HI << 32) | (id0 + sl);
-        uint32_t q[3];
-        if (!quantise(x[k], y[k], z[k], q[0], q[1], q[2])) {
+        uint64_t X[3];
+        if (!fixpoint3(x[k], y[k], z[k], X)) {
             atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
             continue;
         }
-        const double sc = ldexp(1.0, t.lmax);
-        const double s[3] = {x[k] * sc - 0.5, y[k] * sc - 0.5, z[k] * sc - 0.5};
         int i0[3];
-        for (int d = 0; d < 3; ++d) i0[d] = Stencil<K>::first(s[d]);
+        for (int d = 0; d < 3; ++d)
+            i0[d] = Stencil<K>::first((int)fix_cell(X[d], t.lmax), fix_upper_half(X[d], t.lmax) ? 1 : 0);
         const bool ok = visit_stencil<K, false>(t, rm, ss, i0, [&](int leaf, int ax, int ay, int az) {
             const int sl = ax + W * (ay + W * az);
             out[sl] = ((uint64_t)(uint32_t)leaf << 32) | (id0 + sl);
@@ -98,7 +97,6 @@ __global__ void __launch_bounds__(256) k_spread_reduce(const uint64_t* __restric
                                                        const double* __restrict__ z, const T* __restrict__ F,
                                                        const T* __restrict__ dV, int64_t n, T* __restrict__ f) {
     constexpr int W = Stencil<K>::W, W3 = W * W * W;
-    const double sc = ldexp(1.0, lmax);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npairs;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t pv = pairs[i];
@@ -113,14 +111,11 @@ __global__ void __launch_bounds__(256) k_spread_reduce(const uint64_t* __restric
             const int64_t k = id / W3;
             const int sl = (int)(id - (uint32_t)(k * W3));
             const int slot[3] = {sl % W, (sl / W) % W, sl / (W * W)};
-            const double p[3] = {x[k], y[k], z[k]};
+            uint64_t X[3];
+            fixpoint3(x[k], y[k], z[k], X);  // inside: the pair was emitted
             T wt = T(1);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const double s = p[d] * sc - 0.5;
-                const int i0 = Stencil<K>::first(s);
-                wt *= Stencil<K>::template phi<T>((T)(s - (double)(i0 + slot[d])));
-            }
+            for (int d = 0; d < 3; ++d) wt *= stencil_weight_1d<K, T>(lmax, X[d], slot[d]);
             const T vol = marker_volume(dV, k, lmax);
             a0 += F[k] * vol * wt;
             a1 += F[n + k] * vol * wt;
