@@ -212,6 +212,26 @@ ot_status ot_spread_f64(const ot_octree* t, int kernel, int mode, const double* 
                         const double* d_z, const double* d_F, const double* d_dV, int64_t n, double* d_f,
                         void* d_workspace, size_t ws_bytes, void* stream);
 
+/* Size of the library's static device scratch used by ot_spread_noalloc: 64 MiB on every GPU
+ * that loads the library, held until the process exits. */
+#define OT_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* Sorted force spreading that allocates nothing (no counterpart in the paper: it exists for
+ * callers that cannot call cudaMalloc, e.g. a solver whose memory pool already owns the
+ * device, or code that must not risk an allocation's synchronisation or failure mid-step).
+ * Same result as ot_spread(kernel, OT_SORTED, ...) for FP32: d_f is accumulated, d_dV may be
+ * NULL.  The scratch is a fixed library array of OT_NOALLOC_SCRATCH_BYTES per device; it
+ * holds about 1088 bytes per marker for OT_PESKIN4 (about 61,000 markers) and 459 bytes per
+ * marker for OT_ROMA3 (about 146,000); larger n returns OT_ERR_LIMIT and launches nothing.
+ * The first call on a device (with that device current) looks up the scratch address; make
+ * that first call before any stream capture.  All calls share the one array: calls whose
+ * work overlaps on the GPU (different streams, or different threads without ordering) race
+ * and give wrong results; order them on one stream.  The array keeps the last call's
+ * contents; nothing in it needs clearing between calls. */
+ot_status ot_spread_noalloc(const ot_octree* t, int kernel, const double* d_x, const double* d_y,
+                            const double* d_z, const float* d_F, const float* d_dV, int64_t n, float* d_f,
+                            void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * Batched launch: every group of points (IBM markers with a delta kernel, point particles
  * with trilinear) located and interpolated by ONE persistent kernel, captured once in a

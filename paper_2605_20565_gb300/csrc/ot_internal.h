@@ -67,6 +67,12 @@ ot_status compact_u64(const uint64_t* d_in, const uint32_t* d_flag, uint32_t* d_
 // Sorted input -> unique values in place; *h_count on the host (synchronises).
 ot_status unique_u64(uint64_t* d_keys, int64_t n, int64_t* h_count, cudaStream_t s);
 
+// Allocation-free scan / radix sort: temporaries in caller scratch.
+ot_status scan_u32_noalloc(const uint32_t* d_in, uint32_t* d_out, int64_t n, uint32_t* tmp, cudaStream_t s);
+size_t radix_noalloc_bytes(int64_t n);
+ot_status radix_sort_u64_noalloc(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bit0, int bit1, void* ws,
+                                 cudaStream_t s);
+
 // builder (ot_build.cu) ------------------------------------------------------------------------
 ot_status build_tree(const ot_sphere* h_spheres, int n, const ot_build_params* p, cudaStream_t s, ot_octree* t);
 ot_status finish_tree(ot_octree* t, cudaStream_t s); // sample, error word
@@ -91,5 +97,10 @@ size_t spread_ws_bytes(const ot_octree* t, int kernel, int64_t n);
 template <typename T>
 ot_status launch_spread(const ot_octree* t, int kernel, int mode, const double* x, const double* y, const double* z,
                         const T* F, const T* dV, int64_t n, T* f, void* ws, size_t ws_bytes, cudaStream_t s);
+// Sorted spreading with every temporary in `scratch` (spread_noalloc_bytes(kernel, n) bytes).
+size_t spread_noalloc_bytes(int kernel, int64_t n);
+ot_status launch_spread_sorted_noalloc(const ot_octree* t, int kernel, const double* x, const double* y,
+                                       const double* z, const float* F, const float* dV, int64_t n, float* f,
+                                       void* scratch, cudaStream_t s);
 
 } // namespace ot

@@ -287,3 +287,72 @@ ot_status unique_u64(uint64_t* d_keys, int64_t n, int64_t* h_count, cudaStream_t
 }
 
 } // namespace ot
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free variants: every temporary lives in caller-provided scratch.
+// ------------------------------------------------------------------------------------------
+namespace ot {
+
+int64_t scan_noalloc_elems(int64_t n) {
+    int64_t total = 0;
+    int64_t m = n;
+    while (m > SCAN_TILE) {
+        const int64_t nt = (m + SCAN_TILE - 1) / SCAN_TILE;
+        total += nt;
+        m = nt;
+    }
+    return total + 1;
+}
+
+// Exclusive scan with the tile totals of every level in tmp (scan_noalloc_elems(n) uint32).
+ot_status scan_u32_noalloc(const uint32_t* d_in, uint32_t* d_out, int64_t n, uint32_t* tmp, cudaStream_t s) {
+    if (n <= 0) return OT_OK;
+    const int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nt == 1) {
+        k_scan_tiles<<<1, SCAN_T, 0, s>>>(d_in, d_out, n, nullptr);
+        count_launch();
+    } else {
+        uint32_t* tiles = tmp;
+        k_scan_tiles<<<(unsigned)nt, SCAN_T, 0, s>>>(d_in, d_out, n, tiles);
+        count_launch();
+        ot_status st = scan_u32_noalloc(tiles, tiles, nt, tmp + nt, s);
+        if (st != OT_OK) return st;
+        k_scan_add<<<(unsigned)nt, 256, 0, s>>>(d_out, n, tiles);
+        count_launch();
+    }
+    OT_CUDA(cudaGetLastError());
+    return OT_OK;
+}
+
+size_t radix_noalloc_bytes(int64_t n) {
+    int64_t nt = (n + RTILE - 1) / RTILE;
+    if (nt < 1) nt = 1;
+    return (size_t)(2 * 256 * nt + scan_noalloc_elems(256 * nt)) * sizeof(uint32_t) + 256;
+}
+
+ot_status radix_sort_u64_noalloc(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bit0, int bit1, void* ws,
+                                 cudaStream_t s) {
+    if (n <= 1 || bit1 <= bit0) return OT_OK;
+    const int nt = (int)((n + RTILE - 1) / RTILE);
+    uint32_t* hist = static_cast<uint32_t*>(ws);
+    uint32_t* offs = hist + 256 * (int64_t)nt;
+    uint32_t* stmp = offs + 256 * (int64_t)nt;
+    uint64_t* src = d_keys;
+    uint64_t* dst = d_tmp;
+    for (int sh = bit0; sh < bit1; sh += 8) {
+        const int nb = std::min(8, bit1 - sh);
+        const uint32_t mask = (1u << nb) - 1u;
+        k_radix_hist<<<nt, RT, 0, s>>>(src, n, sh, mask, hist, nt);
+        count_launch();
+        ot_status st = scan_u32_noalloc(hist, offs, (int64_t)256 * nt, stmp, s);
+        if (st != OT_OK) return st;
+        k_radix_scatter<<<nt, RT, 0, s>>>(src, dst, n, sh, mask, offs, nt);
+        count_launch();
+        std::swap(src, dst);
+    }
+    if (src != d_keys) OT_CUDA(cudaMemcpyAsync(d_keys, src, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+    OT_CUDA(cudaGetLastError());
+    return OT_OK;
+}
+
+} // namespace ot

@@ -216,3 +216,49 @@ template ot_status launch_spread<double>(const ot_octree*, int, int, const doubl
                                          const double*, const double*, int64_t, double*, void*, size_t, cudaStream_t);
 
 } // namespace ot
+
+// ------------------------------------------------------------------------------------------
+// Sorted spreading with caller scratch only (no allocation of any kind).
+// ------------------------------------------------------------------------------------------
+namespace ot {
+
+size_t spread_noalloc_bytes(int kernel, int64_t n) {
+    const int64_t np = n * stencil_cells(kernel);
+    return (size_t)np * 16 + radix_noalloc_bytes(np) + 256;
+}
+
+namespace {
+template <int K>
+ot_status sorted_noalloc(const ot_octree* t, const double* x, const double* y, const double* z, const float* F,
+                         const float* dV, int64_t n, float* f, void* scratch, cudaStream_t s) {
+    constexpr int W3 = Stencil<K>::W * Stencil<K>::W * Stencil<K>::W;
+    const int64_t np = n * W3;
+    uint64_t* pairs = static_cast<uint64_t*>(scratch);
+    uint64_t* tmp = pairs + np;
+    void* rws = tmp + np;
+    TreeView v = tree_view(t, true);
+    const size_t smem = (size_t)v.nsample * sizeof(uint64_t);
+    ot_status st;
+    auto ke = k_spread_emit<K>;
+    if ((st = prep(ke, smem)) != OT_OK) return st;
+    ke<<<grid_for(ke, 256, smem, n), 256, smem, s>>>(v, t->root, x, y, z, n, pairs);
+    count_launch();
+    OT_CUDA(cudaGetLastError());
+    if ((st = radix_sort_u64_noalloc(pairs, tmp, np, 32, 32 + leaf_bits(t->n), rws, s)) != OT_OK) return st;
+    auto kr = k_spread_reduce<float, K>;
+    kr<<<grid_for(kr, 256, 0, np), 256, 0, s>>>(pairs, np, t->lmax, x, y, z, F, dV, n, f);
+    count_launch();
+    OT_CUDA(cudaGetLastError());
+    return OT_OK;
+}
+} // namespace
+
+ot_status launch_spread_sorted_noalloc(const ot_octree* t, int kernel, const double* x, const double* y,
+                                       const double* z, const float* F, const float* dV, int64_t n, float* f,
+                                       void* scratch, cudaStream_t s) {
+    if (n == 0) return OT_OK;
+    if (kernel == OT_PESKIN4) return sorted_noalloc<OT_PESKIN4>(t, x, y, z, F, dV, n, f, scratch, s);
+    return sorted_noalloc<OT_ROMA3>(t, x, y, z, F, dV, n, f, scratch, s);
+}
+
+} // namespace ot
