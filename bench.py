@@ -28,6 +28,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+INDEX_DESC = {"mlp3": "learned: MLP root 1-32-1 -> 4096 linear mid models -> 262144 linear leaf models",
+              "mlp2": "learned: MLP root 1-32-1 -> 4096 linear leaf models",
+              "linear2": "learned: linear root -> 4096 linear leaf models"}
 METRIC = "Lagrangian points located+interpolated/s on 1 GB300 (learned vs plain) at <=1e-5 rel err"
 BYTES_PER_POINT = 40   # position 24 B + u 12 B + host 4 B
 BYTES_PER_LEAF = 21    # key 8 B + level 1 B + field 12 B
@@ -42,7 +45,11 @@ def parse():
     p.add_argument("--workload", default="many_bubbles",
                    choices=["many_bubbles", "single_bubble", "learned_index", "tiny"])
     p.add_argument("--search", default="learned", choices=["learned", "binary"])
+    p.add_argument("--index", default="mlp3", choices=["mlp3", "mlp2", "linear2"],
+                   help="mlp3: MLP root -> 4096 mid -> 2^18 leaf models; mlp2: MLP root -> 4096 leaf models")
     p.add_argument("--spread", default="sorted", choices=["sorted", "atomic"])
+    p.add_argument("--n-mid", type=int, default=None, help="override the mid model count of mlp3")
+    p.add_argument("--n-leaf", type=int, default=None, help="override the leaf model count")
     p.add_argument("--scale", type=float, default=1.0, help="scale point counts (testing only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -90,7 +97,7 @@ def describe(w, n_leaves, search):
         "markers_peskin4": int(w.markers.shape[1]),
         "particles_trilinear": int(w.particles.shape[1]),
         "search": search,
-        "index": "MLP root 1-32-1 + 4096 leaf linear models" if search == "learned" else "binary (smem-staged top levels)",
+        "index": search,
         "spread": "Peskin-4 sorted deterministic",
         "l2": "inputs larger than L2 (tree+field ~0.7 GB, points 1.2 GB); no flush",
     }
@@ -252,7 +259,14 @@ def run_ours(args):
     build_s = time.time() - t0
     n_leaves = ot.ot_octree_info(tree)[0]
     t0 = time.time()
-    ot.ot_index_train(tree, root=ot.OT_ROOT_MLP, n_leaf_models=4096, epochs=4, batch=65536, lr=1e-3, seed=1)
+    root = ot.OT_ROOT_LINEAR if args.index == "linear2" else ot.OT_ROOT_MLP
+    n_leaf, n_mid = (1 << 18, 4096) if args.index == "mlp3" else (4096, 0)
+    if args.n_leaf:
+        n_leaf = args.n_leaf
+    if args.n_mid is not None and args.index == "mlp3":
+        n_mid = args.n_mid
+    ot.ot_index_train(tree, root=root, n_leaf_models=n_leaf, n_mid_models=n_mid, epochs=4, batch=65536, lr=1e-3,
+                      seed=1)
     torch.cuda.synchronize()
     train_s = time.time() - t0
     istats = ot.ot_index_get_stats(tree, reset=True)
@@ -310,11 +324,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches0 = ot.ot_launch_count()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     start.record(stream)
     for k in range(args.steps):
         step(evs[k])
     stop.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     barrier()
     launches = ot.ot_launch_count() - launches0
     clk = clocks.stop() if clocks else None
@@ -342,6 +358,24 @@ def run_ours(args):
         plain = {"batch_ms": plain_batch_ms, "points_per_s_locate_interp": npts / (plain_batch_ms / 1e3),
                  "step_points_per_s": npts / ((plain_batch_ms + spread_ms) / 1e3)}
         del bplain
+
+    # per-group timing (markers only, particles only), learned and plain
+    groups_t = {}
+    for gname, gsel in (("markers", groups[:1]), ("particles", groups[1:])):
+        for sname, sv in (("learned", ot.OT_LEARNED), ("binary", ot.OT_BINARY)):
+            if sv == ot.OT_LEARNED and search != ot.OT_LEARNED:
+                continue
+            bb = ot.ot_batch_create(tree, gsel, field, search=sv, launch=launch)
+            for _ in range(2):
+                ot.ot_batch_run(bb)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(5):
+                ot.ot_batch_run(bb)
+            b.record(stream)
+            torch.cuda.synchronize()
+            groups_t[f"{gname}_{sname}_ms"] = a.elapsed_time(b) / 5
+            del bb
 
     # end to end through the public API with host buffers
     e2e = None
@@ -421,13 +455,14 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": describe(w, n_leaves, args.search), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+           "config": describe(w, n_leaves, INDEX_DESC[args.index] if args.search == "learned" else "binary"),
+           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": int(launches), "clocks": clk,
            "breakdown_ms": {"locate_interpolate": batch_ms, "spread": spread_ms, "step": ms_step},
            "locate_interpolate_points_per_s": world * npts / (batch_ms / 1e3),
-           "plain": plain,
+           "plain": plain, "groups_ms": groups_t,
            "learned_speedup_locate_interp": (plain["batch_ms"] / batch_ms) if plain else None,
-           "index": {"mean_window": istats["mean_window"], "max_window": istats["max_window"],
+           "index": {"n_mid": n_mid, "n_leaf": n_leaf, "mean_window": istats["mean_window"], "max_window": istats["max_window"],
                      "empty_models": istats["empty_models"], "fallbacks_timed": fb,
                      "final_loss": istats["final_loss"], "train_s": train_s},
            "setup_s": {"octree_build": build_s, "index_train": train_s},

@@ -132,7 +132,10 @@ ot_status ot_octree_destroy(ot_octree* t);
 
 typedef struct {
     int root;          /* OT_ROOT_LINEAR or OT_ROOT_MLP (1 -> 32 ReLU -> 1)                    */
-    int n_leaf_models; /* 1 .. 1<<20; 4096 is the usual choice                               */
+    int n_leaf_models; /* 1 .. 1<<22; 4096 for the two-stage index                           */
+    int n_mid_models;  /* 0: two-stage (root -> leaf models).  > 0: three-stage: the root picks
+                          one of n_mid_models linear models, whose position estimate picks the
+                          leaf model (integer scaling, monotone within a mid model)            */
     int epochs;        /* MLP root: training length; an epoch is min(N / batch, 512) Adam steps */
     int batch;         /* MLP root: minibatch size                                           */
     float lr;          /* MLP root: Adam step size                                           */

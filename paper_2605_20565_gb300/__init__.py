@@ -56,8 +56,8 @@ class _BuildParams(C.Structure):
 
 
 class _IndexParams(C.Structure):
-    _fields_ = [("root", C.c_int), ("n_leaf_models", C.c_int), ("epochs", C.c_int), ("batch", C.c_int),
-                ("lr", C.c_float), ("seed", C.c_uint64)]
+    _fields_ = [("root", C.c_int), ("n_leaf_models", C.c_int), ("n_mid_models", C.c_int), ("epochs", C.c_int),
+                ("batch", C.c_int), ("lr", C.c_float), ("seed", C.c_uint64)]
 
 
 class _IndexStats(C.Structure):
@@ -234,8 +234,8 @@ def ot_octree_destroy(tree: Octree):
 # --- learned index ------------------------------------------------------------------------
 
 def ot_index_train(tree: Octree, root: int = OT_ROOT_MLP, n_leaf_models: int = 4096, epochs: int = 4,
-                   batch: int = 65536, lr: float = 1e-3, seed: int = 0, stream=None):
-    prm = _IndexParams(root, n_leaf_models, epochs, batch, lr, seed)
+                   batch: int = 65536, lr: float = 1e-3, seed: int = 0, n_mid_models: int = 0, stream=None):
+    prm = _IndexParams(root, n_leaf_models, n_mid_models, epochs, batch, lr, seed)
     _check(_L().ot_index_train(tree.handle, C.byref(prm), _stream(stream)))
 
 

@@ -183,6 +183,7 @@ ot_status ot_octree_destroy(ot_octree* t) {
     if (t->d_level) cudaFree(t->d_level);
     if (t->d_sample) cudaFree(t->d_sample);
     if (t->d_models) cudaFree(t->d_models);
+    if (t->d_mids) cudaFree(t->d_mids);
     if (t->d_err) cudaFree(t->d_err);
     delete t;
     return OT_OK;
@@ -191,7 +192,8 @@ ot_status ot_octree_destroy(ot_octree* t) {
 ot_status ot_index_train(ot_octree* t, const ot_index_params* p, void* stream) {
     if (!t || !p) return OT_ERR_ARG;
     if (p->root != OT_ROOT_LINEAR && p->root != OT_ROOT_MLP) return OT_ERR_ARG;
-    if (p->n_leaf_models < 1 || p->n_leaf_models > (1 << 20)) return OT_ERR_ARG;
+    if (p->n_leaf_models < 1 || p->n_leaf_models > (1 << 22)) return OT_ERR_ARG;
+    if (p->n_mid_models < 0 || p->n_mid_models > (1 << 20)) return OT_ERR_ARG;
     if (p->root == OT_ROOT_MLP && (p->epochs < 0 || p->batch < 1 || !(p->lr >= 0.0f))) return OT_ERR_ARG;
     return train_index(t, p, (cudaStream_t)stream);
 }
@@ -204,7 +206,7 @@ ot_status ot_index_get_stats(const ot_octree* t, ot_index_stats* s, int reset) {
     double sum = 0.0;
     int64_t mx = 0, empty = 0, used = 0;
     for (const LeafModel& x : m) {
-        if (x.count == 0) {
+        if (x.count == 0 || x.err_lo < 0) {  // no stored key routed here (filled model)
             ++empty;
             continue;
         }

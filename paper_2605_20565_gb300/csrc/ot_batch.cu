@@ -44,7 +44,7 @@ template <bool LEARNED>
 __global__ void __launch_bounds__(256) k_batch(TreeView t, RootModel rm, BatchArgs a, const float* __restrict__ field,
                                                unsigned* __restrict__ counter) {
     extern __shared__ uint64_t s_sample[];
-    const bool staged = !LEARNED && t.nsample > 1;
+    const bool staged = t.nsample > 1;  // plain search, and the learned fallback
     if (staged) load_sample(t, s_sample);
     const uint64_t* ss = staged ? s_sample : nullptr;
     const int lane = threadIdx.x & 31;
@@ -134,8 +134,8 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     };
     cudaError_t e;
     if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned))) != cudaSuccess) return fail(e);
-    TreeView v = tree_view(t, search != OT_LEARNED);
-    if (search != OT_LEARNED) {
+    TreeView v = tree_view(t, true);
+    {
         int64_t ns = std::min<int64_t>((int64_t)1 << stage, t->n);
         int64_t stride = (t->n + ns - 1) / ns;
         ns = (t->n + stride - 1) / stride;
@@ -148,7 +148,7 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
         v.nsample = (int)ns;
         v.stride = (int)stride;
     }
-    const size_t smem = search != OT_LEARNED ? (size_t)v.nsample * sizeof(uint64_t) : 0;
+    const size_t smem = (size_t)v.nsample * sizeof(uint64_t);
     void* kfn = search == OT_LEARNED ? (void*)k_batch<true> : (void*)k_batch<false>;
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -163,10 +163,10 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e);
     cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), cs);
     RootModel rm = t->root;
-    if (search == OT_LEARNED)
-        k_batch<true><<<grid, block, smem, cs>>>(v, rm, a, d_field, b->d_counter);
-    else
-        k_batch<false><<<grid, block, smem, cs>>>(v, rm, a, d_field, b->d_counter);
+    {
+        void* args[] = {&v, &rm, &a, (void*)&d_field, &b->d_counter};
+        cudaLaunchKernel(kfn, dim3(grid), dim3(block), args, smem, cs);
+    }
     e = cudaStreamEndCapture(cs, &b->graph);
     if (e != cudaSuccess) return fail(e);
     if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) return fail(e);

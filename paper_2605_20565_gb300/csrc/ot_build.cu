@@ -508,6 +508,8 @@ TreeView tree_view(const ot_octree* t, bool with_sample) {
     v.nsample = with_sample ? t->nsample : 0;
     v.stride = t->stride;
     v.models = t->d_models;
+    v.mids = t->d_mids;
+    v.n_leaf = t->n_models;
     v.err = t->d_err;
     v.fallbacks = t->d_fallbacks;
     return v;

@@ -112,7 +112,7 @@ struct __align__(32) LeafModel {
     int err_lo; // window below the prediction
     int err_hi; // window above the prediction
     int first;  // index of the model's first key (prediction origin)
-    int count;  // keys routed here (0: empty model, queries fall back)
+    int count;  // keys routed here; a model no key routed to is filled (err_lo = -1, below)
 };
 
 struct RootModel {
@@ -132,8 +132,10 @@ struct TreeView {
     const uint64_t* __restrict__ sample;
     int nsample;
     int stride;
-    // learned search
+    // learned search: root -> (optional mid models) -> leaf models
     const LeafModel* __restrict__ models;
+    const LeafModel* __restrict__ mids;  // null for a two-stage index
+    int n_leaf;                          // leaf models
     unsigned* err;                      // device error word
     unsigned long long* fallbacks;      // learned-query fallbacks
 };
@@ -204,19 +206,30 @@ __device__ __forceinline__ int leaf_predict(const LeafModel& m, uint64_t q, int 
     return min(max(pc, 0), n - 1);
 }
 
-// Learned host search: predict, search the stored error window, verify, else plain search.
+// Leaf model serving key q: the root's choice, or, with a middle stage, the mid model's
+// position estimate scaled to the leaf count (integer, monotone within a mid model).
+__device__ __forceinline__ int route_leaf(const RootModel& r, const LeafModel* mids, int n_leaf, int n, uint64_t q) {
+    const int j = root_route(r, q);
+    if (!mids) return j;
+    const int pc = leaf_predict(mids[j], q, n);
+    return (int)(((int64_t)pc * n_leaf) / n);
+}
+
+// Learned host search: the models give a window [pc - err_lo - 1, pc + err_hi + 1]; it is
+// searched by halving and the answer a is verified by key[a] <= q < key[a+1]; a window that missed
+// is answered by the plain search (counted as a fallback).
 __device__ __forceinline__ int search_learned(const TreeView& t, const RootModel& r, const uint64_t* s_sample,
                                               uint64_t q) {
-    int j = root_route(r, q);
-    LeafModel m = t.models[j];
+    const int j = route_leaf(r, t.mids, t.n_leaf, t.n, q);
+    const LeafModel m = t.models[j];
     if (m.count > 0) {
-        int pc = leaf_predict(m, q, t.n);
-        int lo = max(pc - m.err_lo - 1, 0);
-        int hi = min(pc + m.err_hi + 1, t.n - 1);
-        if (ldg_key(t.key + lo) <= q) {
-            int a = search_range(t.key, lo, hi - lo + 1, q);
-            if (a < hi || a == t.n - 1 || ldg_key(t.key + a + 1) > q) return a;
-        }
+        const int pc = leaf_predict(m, q, t.n);
+        const int lo = max(pc - m.err_lo - 1, 0);
+        const int hi = min(pc + m.err_hi + 1, t.n - 1);
+        const int a = search_range(t.key, lo, hi - lo + 1, q);
+        const uint64_t a0 = ldg_key(t.key + a);
+        const uint64_t a1 = a + 1 < t.n ? ldg_key(t.key + a + 1) : ~0ULL;
+        if (a0 <= q && q < a1) return a;
     }
     atomicAdd(t.fallbacks, 1ULL);
     atomicOr(t.err, (unsigned)OT_DEV_WINDOW);

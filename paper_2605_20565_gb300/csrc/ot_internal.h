@@ -23,8 +23,10 @@ struct ot_octree {
     // learned index
     bool has_index = false;
     ot::RootModel root{};
-    ot::LeafModel* d_models = nullptr;
+    ot::LeafModel* d_models = nullptr;  // leaf models
     int n_models = 0;
+    ot::LeafModel* d_mids = nullptr;    // middle stage (null: two-stage index)
+    int n_mids = 0;
     float final_loss = 0.0f;
     // diagnostics: [0] error word (unsigned), [1..2] fallback counter (u64)
     unsigned* d_err = nullptr;

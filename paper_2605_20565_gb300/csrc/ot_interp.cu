@@ -116,7 +116,7 @@ ot_status launch_locate(const ot_octree* t, const double* x, const double* y, co
                         int32_t* host, unsigned long long* n_miss, cudaStream_t s) {
     if (n == 0) return OT_OK;
     const bool learned = search == OT_LEARNED;
-    TreeView v = tree_view(t, !learned);
+    TreeView v = tree_view(t, true);  // the sample serves plain searches and learned fallbacks
     const size_t smem = (size_t)v.nsample * sizeof(uint64_t);
     const int block = 256;
     if (learned) {
@@ -140,7 +140,7 @@ ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const d
                         const int32_t* host_in, int search, const T* field, T* u, int32_t* host_out, cudaStream_t s) {
     if (n == 0) return OT_OK;
     const bool learned = search == OT_LEARNED;
-    TreeView v = tree_view(t, !learned);
+    TreeView v = tree_view(t, true);  // the sample serves plain searches and learned fallbacks
     const size_t smem = (size_t)v.nsample * sizeof(uint64_t);
     const int block = 256;
     ot_status st = OT_OK;

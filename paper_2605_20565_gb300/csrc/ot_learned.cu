@@ -62,6 +62,30 @@ __global__ void k_lin_sums(const uint64_t* __restrict__ key, int64_t n, double* 
     }
 }
 
+// A model that no stored key was routed to: under monotone routing every query that reaches it
+// lies between the last key of the previous non-empty model and the first key of the next
+// one, so its answer is the index just before the next model's first key.  The model
+// predicts that index with the window [pc, pc + 1] (err_lo = -1 marks it as filled); a query
+// that breaks the premise fails verification and falls back.
+__global__ void k_fill_empty(const LeafModel* __restrict__ fitted, LeafModel* __restrict__ models, int nm,
+                             int nkeys) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nm; j += gridDim.x * blockDim.x) {
+        if (fitted[j].count > 0) continue;
+        int k = j + 1;
+        while (k < nm && fitted[k].count <= 0) ++k;
+        const int first_next = k < nm ? fitted[k].first : nkeys;
+        LeafModel m{};
+        m.base = 0;
+        m.slope = 0.0f;
+        m.icpt = 0.0f;
+        m.first = max(first_next - 1, 0);
+        m.count = 1;
+        m.err_lo = -1;
+        m.err_hi = 0;
+        models[j] = m;
+    }
+}
+
 __global__ void k_lin_finish(const double* __restrict__ part, int nb, int64_t n, double* __restrict__ means, int pass) {
     if (threadIdx.x != 0) return;
     double a = 0, b = 0;
@@ -215,26 +239,34 @@ __global__ void k_knot_cdf(const uint64_t* __restrict__ key, int64_t n, float* _
 }
 
 // ----- leaf models -------------------------------------------------------------------------
-__global__ void k_route(const uint64_t* __restrict__ key, int64_t n, RootModel rm, uint64_t* __restrict__ pairs) {
-    GSTRIDE(i, n) pairs[i] = ((uint64_t)(uint32_t)root_route(rm, key[i]) << 32) | (uint64_t)i;
+// (model, index) pairs of every stored key, routed exactly as a query would be.
+__global__ void k_route(const uint64_t* __restrict__ key, int64_t n, RootModel rm, const LeafModel* __restrict__ mids,
+                        int n_leaf, uint64_t* __restrict__ pairs) {
+    GSTRIDE(i, n) {
+        const int j = route_leaf(rm, mids, n_leaf, (int)n, key[i]);
+        pairs[i] = ((uint64_t)(uint32_t)j << 32) | (uint64_t)i;
+    }
 }
 
-__global__ void k_model_bounds(const uint64_t* __restrict__ pairs, int64_t n, int* __restrict__ start) {
+// Run [start, end) of every model in the sorted pairs (untouched for empty models).
+__global__ void k_model_bounds(const uint64_t* __restrict__ pairs, int64_t n, int* __restrict__ start,
+                               int* __restrict__ end) {
     GSTRIDE(i, n) {
         const int m = (int)(pairs[i] >> 32);
         if (i == 0 || (int)(pairs[i - 1] >> 32) != m) start[m] = (int)i;
+        if (i == n - 1 || (int)(pairs[i + 1] >> 32) != m) end[m] = (int)i + 1;
     }
 }
 
 // One block per model: FP64 least squares (two passes), then the error window with the query's
 // float arithmetic.  start/cnt: run of the model in the sorted pairs.
 __global__ void __launch_bounds__(LT) k_fit_models(const uint64_t* __restrict__ key, const uint64_t* __restrict__ pairs,
-                                                   const int* __restrict__ start, const int* __restrict__ cnt, int nkeys,
+                                                   const int* __restrict__ start, const int* __restrict__ end, int nkeys,
                                                    LeafModel* __restrict__ models) {
     __shared__ double s[LT];
     __shared__ int s_i[2 * LT];
     const int m = blockIdx.x;
-    const int c = cnt[m];
+    const int c = start[m] >= 0 ? end[m] - start[m] : 0;
     LeafModel md{};
     if (c == 0) {
         if (threadIdx.x == 0) {
@@ -296,23 +328,6 @@ __global__ void __launch_bounds__(LT) k_fit_models(const uint64_t* __restrict__ 
         md.err_lo = s_i[0];
         md.err_hi = s_i[LT];
         models[m] = md;
-    }
-}
-
-__global__ void k_counts_from_start(const int* __restrict__ start, int nm, int64_t n, int* __restrict__ cnt) {
-    // start[m] = -1 for empty models; count = next non-empty start - start
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += gridDim.x * blockDim.x) {
-        if (start[m] < 0) {
-            cnt[m] = 0;
-            continue;
-        }
-        int nx = (int)n;
-        for (int k = m + 1; k < nm; ++k)
-            if (start[k] >= 0) {
-                nx = start[k];
-                break;
-            }
-        cnt[m] = nx - start[m];
     }
 }
 
@@ -415,36 +430,59 @@ ot_status train_index(ot_octree* t, const ot_index_params* prm, cudaStream_t s) 
         }
         rm.b2 = p[3 * MLP_H];
     }
-    // leaf models: route, stable sort by model, per-model fit and error window
-    uint64_t *pairs = nullptr, *tmp = nullptr;
-    int *start = nullptr, *cnt = nullptr;
-    OT_CUDA(cudaMallocAsync(&pairs, sizeof(uint64_t) * n, s));
-    OT_CUDA(cudaMallocAsync(&tmp, sizeof(uint64_t) * n, s));
-    OT_CUDA(cudaMallocAsync(&start, sizeof(int) * M, s));
-    OT_CUDA(cudaMallocAsync(&cnt, sizeof(int) * M, s));
-    k_route<<<g1(n, 256), 256, 0, s>>>(t->d_key, n, rm, pairs);
-    count_launch();
-    int bits = 1;
-    while ((1 << bits) < M) ++bits;
-    ot_status st = radix_sort_u64(pairs, tmp, n, 32, 32 + bits, s);
-    if (st != OT_OK) return st;
-    OT_CUDA(cudaMemsetAsync(start, 0xff, sizeof(int) * M, s));
-    k_model_bounds<<<g1(n, 256), 256, 0, s>>>(pairs, n, start);
-    k_counts_from_start<<<g1(M, 256), 256, 0, s>>>(start, M, n, cnt);
-    count_launch(2);
+    const bool three = prm->n_mid_models > 0;
+    rm.n_models = three ? prm->n_mid_models : M;
+    // models of one stage: route every key as a query would be, stable-sort the (model, index)
+    // pairs by model, fit each model's line and error window
+    auto fit_stage = [&](const LeafModel* mids, int n_route, LeafModel* out) -> ot_status {
+        uint64_t *pairs = nullptr, *tmp = nullptr;
+        int *start = nullptr, *end = nullptr;
+        OT_CUDA(cudaMallocAsync(&pairs, sizeof(uint64_t) * n, s));
+        OT_CUDA(cudaMallocAsync(&tmp, sizeof(uint64_t) * n, s));
+        OT_CUDA(cudaMallocAsync(&start, sizeof(int) * n_route, s));
+        OT_CUDA(cudaMallocAsync(&end, sizeof(int) * n_route, s));
+        k_route<<<g1(n, 256), 256, 0, s>>>(t->d_key, n, rm, mids, M, pairs);
+        count_launch();
+        int bits = 1;
+        while ((1 << bits) < n_route) ++bits;
+        ot_status st = radix_sort_u64(pairs, tmp, n, 32, 32 + bits, s);
+        if (st != OT_OK) return st;
+        OT_CUDA(cudaMemsetAsync(start, 0xff, sizeof(int) * n_route, s));
+        OT_CUDA(cudaMemsetAsync(end, 0xff, sizeof(int) * n_route, s));
+        k_model_bounds<<<g1(n, 256), 256, 0, s>>>(pairs, n, start, end);
+        k_fit_models<<<n_route, LT, 0, s>>>(t->d_key, pairs, start, end, (int)n, out);
+        count_launch(2);
+        // empty models are filled from a copy of the fitted ones (no reader sees a half-filled model)
+        LeafModel* fitted = nullptr;
+        OT_CUDA(cudaMallocAsync(&fitted, sizeof(LeafModel) * n_route, s));
+        OT_CUDA(cudaMemcpyAsync(fitted, out, sizeof(LeafModel) * n_route, cudaMemcpyDeviceToDevice, s));
+        k_fill_empty<<<g1(n_route, 256), 256, 0, s>>>(fitted, out, n_route, (int)n);
+        count_launch();
+        cudaFreeAsync(fitted, s);
+        OT_CUDA(cudaGetLastError());
+        cudaFreeAsync(pairs, s);
+        cudaFreeAsync(tmp, s);
+        cudaFreeAsync(start, s);
+        cudaFreeAsync(end, s);
+        return OT_OK;
+    };
     if (t->d_models) cudaFree(t->d_models);
-    t->d_models = nullptr;
+    if (t->d_mids) cudaFree(t->d_mids);
+    t->d_models = t->d_mids = nullptr;
+    t->has_index = false;
     OT_CUDA(cudaMalloc(&t->d_models, sizeof(LeafModel) * M));
-    k_fit_models<<<M, LT, 0, s>>>(t->d_key, pairs, start, cnt, (int)n, t->d_models);
-    count_launch();
-    OT_CUDA(cudaGetLastError());
-    cudaFreeAsync(pairs, s);
-    cudaFreeAsync(tmp, s);
-    cudaFreeAsync(start, s);
-    cudaFreeAsync(cnt, s);
+    ot_status st;
+    if (three) {
+        OT_CUDA(cudaMalloc(&t->d_mids, sizeof(LeafModel) * prm->n_mid_models));
+        if ((st = fit_stage(nullptr, prm->n_mid_models, t->d_mids)) != OT_OK) return st;
+        if ((st = fit_stage(t->d_mids, M, t->d_models)) != OT_OK) return st;
+    } else {
+        if ((st = fit_stage(nullptr, M, t->d_models)) != OT_OK) return st;
+    }
     OT_CUDA(cudaStreamSynchronize(s));
     t->root = rm;
     t->n_models = M;
+    t->n_mids = three ? prm->n_mid_models : 0;
     t->has_index = true;
     t->final_loss = final_loss;
     return OT_OK;

@@ -90,12 +90,17 @@ __device__ __forceinline__ int trilinear_warp(const TreeView& t, const RootModel
     }
     const int sh = MAXLEVEL - l;
     const uint64_t span = key_span(l);
-    T acc0 = T(0), acc1 = T(0), acc2 = T(0);
-    bool capped = false;
-#pragma unroll 1
+    // level-mates: anchors, weights; a sibling of the host cell is usually h + (difference of
+    // child numbers), which one key comparison proves (keys are unique); the rest are searched
+    // together in lockstep
+    uint64_t anc[8];
+    T w[8];
+    int a[8];
+    unsigned need = 0, self_mask = 0;
+#pragma unroll
     for (int corner = 0; corner < 8; ++corner) {
         int m[3];
-        T w = T(1);
+        T wc = T(1);
         bool self = true;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -104,38 +109,76 @@ __device__ __forceinline__ int trilinear_warp(const TreeView& t, const RootModel
             if (v < 0 || v >= ncell) v = c[d];
             m[d] = v;
             self = self && (v == c[d]);
-            w *= off ? at[d] : T(1) - at[d];
+            wc *= off ? at[d] : T(1) - at[d];
         }
-        T v0 = T(0), v1 = T(0), v2 = T(0);
-        bool refined = false;
-        int a = h;
-        uint64_t end = 0;
-        if (ok) {
-            if (!self) {
-                const uint64_t anchor = morton3((uint32_t)m[0] << sh, (uint32_t)m[1] << sh, (uint32_t)m[2] << sh);
-                a = search<LEARNED>(t, rm, s_sample, anchor);
-                refined = (int)t.level[a] > l;
-                end = anchor + span;
+        w[corner] = wc;
+        anc[corner] = morton3((uint32_t)m[0] << sh, (uint32_t)m[1] << sh, (uint32_t)m[2] << sh);
+        a[corner] = h;
+        if (self) self_mask |= 1u << corner;
+        if (ok && !self) {
+            bool hit = false;
+            if ((m[0] >> 1) == (c[0] >> 1) && (m[1] >> 1) == (c[1] >> 1) && (m[2] >> 1) == (c[2] >> 1)) {
+                const int gi = h + ((m[0] & 1) | ((m[1] & 1) << 1) | ((m[2] & 1) << 2)) -
+                               ((c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2));
+                if (gi >= 0 && gi < t.n && ldg_key(t.key + gi) == anc[corner]) {
+                    a[corner] = gi;
+                    hit = true;
+                }
             }
-            if (!refined) {
-                const auto f = V::load(field, a);
-                v0 = f.x, v1 = f.y, v2 = f.z;
-            }
+            if (!hit) need |= 1u << corner;
         }
-        unsigned pend = __ballot_sync(FULL_MASK, refined);
+    }
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner)
+        if ((need >> corner) & 1u) a[corner] = search<LEARNED>(t, rm, s_sample, anc[corner]);
+    // values: leaves of level <= l directly; refined level-mates afterwards, warp-cooperatively
+    T acc0 = T(0), acc1 = T(0), acc2 = T(0);
+    unsigned rmask = 0;
+    int lv[8];
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) lv[corner] = ok ? (int)t.level[a[corner]] : 0;
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+        if (!ok) continue;
+        if (!((self_mask >> corner) & 1u) && lv[corner] > l) {
+            rmask |= 1u << corner;
+        } else {
+            const auto f = V::load(field, a[corner]);
+            acc0 += w[corner] * f.x;
+            acc1 += w[corner] * f.y;
+            acc2 += w[corner] * f.z;
+        }
+    }
+    bool capped = false;
+    while (__any_sync(FULL_MASK, rmask != 0)) {
+        // each lane's next refined level-mate
+        const int k = rmask ? __ffs(rmask) - 1 : 0;
+        int ak = 0;
+        uint64_t ek = 0;
+        T wk = T(0);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+            if (kk == k) {
+                ak = a[kk];
+                ek = anc[kk] + span;
+                wk = w[kk];
+            }
+        unsigned pend = __ballot_sync(FULL_MASK, rmask != 0);
         while (pend) {
             const int owner = __ffs(pend) - 1;
             pend &= pend - 1;
-            const int ao = __shfl_sync(FULL_MASK, a, owner);
-            const uint64_t eo = __shfl_sync(FULL_MASK, end, owner);
+            const int ao = __shfl_sync(FULL_MASK, ak, owner);
+            const uint64_t eo = __shfl_sync(FULL_MASK, ek, owner);
             const int lo_ = __shfl_sync(FULL_MASK, l, owner);
             T r0, r1, r2;
             warp_range_mean<T>(t, field, ao, eo, lo_, r0, r1, r2, capped);
-            if (lane == owner) v0 = r0, v1 = r1, v2 = r2;
+            if (lane == owner) {
+                acc0 += wk * r0;
+                acc1 += wk * r1;
+                acc2 += wk * r2;
+            }
         }
-        acc0 += w * v0;
-        acc1 += w * v1;
-        acc2 += w * v2;
+        if (rmask) rmask &= rmask - 1;
     }
     if (capped) atomicOr(t.err, (unsigned)OT_DEV_REFINED_CAP);
     if (!ok) {
@@ -190,6 +233,7 @@ __device__ __forceinline__ bool visit_stencil(const TreeView& t, const RootModel
         pn[d] = floordiv2(i0[d] + W - 1) - p0[d] + 1;
     }
     bool ok_all = true;
+    int prevP[3] = {-1, -1, -1}, prev_a0 = -1;  // last parent found with its 8 finest leaves
     for (int bz = 0; bz < pn[2]; ++bz)
         for (int by = 0; by < pn[1]; ++by)
             for (int bx = 0; bx < pn[0]; ++bx) {
@@ -200,8 +244,19 @@ __device__ __forceinline__ bool visit_stencil(const TreeView& t, const RootModel
                 if (inside) {
                     const uint64_t anchor =
                         morton3((uint32_t)P[0] << shp, (uint32_t)P[1] << shp, (uint32_t)P[2] << shp);
-                    const int a = search<LEARNED>(t, rm, s_sample, anchor);
-                    if (ldg_key(t.key + a) == anchor && t.level[a] == t.lmax) a0 = a;
+                    int a = -1;
+                    if (prev_a0 >= 0 && (P[0] >> 1) == (prevP[0] >> 1) && (P[1] >> 1) == (prevP[1] >> 1) &&
+                        (P[2] >> 1) == (prevP[2] >> 1)) {
+                        const int g = prev_a0 + 8 * (((P[0] & 1) | ((P[1] & 1) << 1) | ((P[2] & 1) << 2)) -
+                                                     ((prevP[0] & 1) | ((prevP[1] & 1) << 1) | ((prevP[2] & 1) << 2)));
+                        if (g >= 0 && g < t.n && ldg_key(t.key + g) == anchor) a = g;
+                    }
+                    if (a < 0) a = search<LEARNED>(t, rm, s_sample, anchor);
+                    if (ldg_key(t.key + a) == anchor && t.level[a] == t.lmax) {
+                        a0 = a;
+                        prevP[0] = P[0], prevP[1] = P[1], prevP[2] = P[2];
+                        prev_a0 = a;
+                    }
                 }
 #pragma unroll
                 for (int ch = 0; ch < 8; ++ch) {

@@ -165,8 +165,8 @@ def test_locate_special_points(ot, tiny, torch_mod):
     assert ot.ot_last_error(tree) & ot.OT_DEV_OUTSIDE
 
 
-@pytest.mark.parametrize("root", [0, 1])
-def test_learned_locate_bit_exact(ot, root):
+@pytest.mark.parametrize("root,mid", [(0, 0), (1, 0), (1, 64)])
+def test_learned_locate_bit_exact(ot, root, mid):
     from paper_2605_20565_gb300 import synth
     w = synth.single_bubble(n_markers=2000, n_particles=200_000)
     w.lmin, w.lmax = 4, 8
@@ -174,7 +174,8 @@ def test_learned_locate_bit_exact(ot, root):
     sph[:, 4] = 0.1
     ko, lo = oracle.octree_build(sph, 4, 8)
     tree = ot.ot_octree_build(sph, 4, 8)
-    ot.ot_index_train(tree, root=root, n_leaf_models=1024, epochs=2, batch=8192, lr=1e-3, seed=7)
+    ot.ot_index_train(tree, root=root, n_leaf_models=1024 if not mid else 8192, n_mid_models=mid, epochs=2,
+                      batch=8192, lr=1e-3, seed=7)
     P = special_points(ko, lo, np.random.default_rng(9), 20000)
     P = np.concatenate([P, w.particles.T])
     x, y, z = pts(P.T)
