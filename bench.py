@@ -54,7 +54,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--launch", default="", help="block,tile,blocks_per_sm,stage_log2")
+    p.add_argument("--launch", default="", help="block,tile,blocks_per_sm")
+    p.add_argument("--map-level", type=int, default=None, help="level of the level map (default min(lmax, 7))")
     return p.parse_args()
 
 
@@ -99,6 +100,7 @@ def describe(w, n_leaves, search):
         "search": search,
         "index": search,
         "spread": "Peskin-4 sorted deterministic",
+        "level_map": "top levels staged as a dense level map (default level min(lmax, 7))",
         "l2": "inputs larger than L2 (tree+field ~0.7 GB, points 1.2 GB); no flush",
     }
 
@@ -258,6 +260,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     build_s = time.time() - t0
     n_leaves = ot.ot_octree_info(tree)[0]
+    if args.map_level is not None:
+        ot.ot_octree_set_map_level(tree, args.map_level)
     t0 = time.time()
     root = ot.OT_ROOT_LINEAR if args.index == "linear2" else ot.OT_ROOT_MLP
     n_leaf, n_mid = (1 << 18, 4096) if args.index == "mlp3" else (4096, 0)
@@ -295,8 +299,8 @@ def run_ours(args):
     ws = torch.empty(max(1, ws_bytes), dtype=torch.uint8, device=dev)
     launch = None
     if args.launch:
-        b, t, s, st = [int(v) for v in args.launch.split(",")]
-        launch = dict(block=b, tile=t, blocks_per_sm=s, stage_log2=st)
+        b, t, s = [int(v) for v in args.launch.split(",")]
+        launch = dict(block=b, tile=t, blocks_per_sm=s)
     groups = [dict(kernel=ot.OT_PESKIN4, x=mx, y=my, z=mz, u=um), dict(kernel=ot.OT_TRILINEAR, x=px, y=py, z=pz, u=up)]
     batch = ot.ot_batch_create(tree, groups, field, search=search, launch=launch)
     stream = torch.cuda.current_stream()

@@ -117,6 +117,13 @@ ot_status ot_octree_leaves(const ot_octree* t, int64_t* n, const uint64_t** d_ke
  * NULL), asynchronously on stream. */
 ot_status ot_octree_copy_leaves(const ot_octree* t, uint64_t* d_keys, uint8_t* d_levels, void* stream);
 
+/* Level of the level map that every host search starts from (0 .. 8, capped at lmax): for
+ * each cell of that level the map holds the leaf at the cell's anchor, so a point in a cell
+ * covered by one leaf is located with one table read, and any other point is searched only
+ * among its cell's leaves.  8^level * 4 bytes of device memory.  Octrees are created with
+ * min(lmax, 7).  Synchronises the stream. */
+ot_status ot_octree_set_map_level(ot_octree* t, int level, void* stream);
+
 /* Leaf centres, FP64, written as 3 planes of N (x..., y..., z...). */
 ot_status ot_octree_centres(const ot_octree* t, double* d_xyz, void* stream);
 
@@ -202,8 +209,9 @@ ot_status ot_spread_workspace_size(const ot_octree* t, int kernel, int64_t n, si
  * F(x)): f(cell) += sum_k F_k phi phi phi dV_k / h^3, h = 2^-lmax, dV_k = h^3 when d_dV is
  * NULL (the paper's literal form).  d_F: 3 planes of n floats; d_f: float4 per leaf,
  * ACCUMULATED (the caller zeroes it), component w untouched.
- *   OT_SORTED: pairs (leaf, marker, stencil slot) are radix-sorted by leaf (stable) and each
- *     leaf sums its contributions in marker order: bit-identical run to run.
+ *   OT_SORTED: one pair per (marker, overlapping 2x2x2 block of finest cells) is radix-sorted
+ *     by block (stable); each block sums its 8 cells' contributions in marker order:
+ *     bit-identical run to run and for any launch shape.
  *     Needs d_workspace of ot_spread_workspace_size bytes (16-byte aligned).
  *   OT_ATOMIC: float atomics; order varies run to run.  d_workspace may be NULL. */
 ot_status ot_spread(const ot_octree* t, int kernel, int mode, const double* d_x, const double* d_y,
@@ -224,8 +232,8 @@ ot_status ot_spread_f64(const ot_octree* t, int kernel, int mode, const double* 
  * device, or code that must not risk an allocation's synchronisation or failure mid-step).
  * Same result as ot_spread(kernel, OT_SORTED, ...) for FP32: d_f is accumulated, d_dV may be
  * NULL.  The scratch is a fixed library array of OT_NOALLOC_SCRATCH_BYTES per device; it
- * holds about 1088 bytes per marker for OT_PESKIN4 (about 61,000 markers) and 459 bytes per
- * marker for OT_ROMA3 (about 146,000); larger n returns OT_ERR_LIMIT and launches nothing.
+ * holds about 459 bytes per marker for OT_PESKIN4 (at most 146,202 markers) and 136 bytes per
+ * marker for OT_ROMA3 (at most 493,432); larger n returns OT_ERR_LIMIT and launches nothing.
  * The first call on a device (with that device current) looks up the scratch address; make
  * that first call before any stream capture.  All calls share the one array: calls whose
  * work overlaps on the GPU (different streams, or different threads without ordering) race
@@ -254,7 +262,6 @@ typedef struct {
     int block;       /* threads per block: 64 .. 1024, multiple of 32                       */
     int tile;        /* points per work item fetched from the queue                         */
     int blocks_per_sm;
-    int stage_log2;  /* plain search: log2 of the shared-memory sample of top-level keys     */
 } ot_launch;
 
 /* Create a batch over groups (copied) reading d_field (float4 per leaf).  search selects

@@ -19,7 +19,7 @@ __all__ = [
     "OT_TRILINEAR", "OT_PESKIN4", "OT_ROMA3", "OT_BINARY", "OT_LEARNED", "OT_SORTED", "OT_ATOMIC",
     "OT_ROOT_LINEAR", "OT_ROOT_MLP", "OT_DEV_OUTSIDE", "OT_DEV_STENCIL", "OT_DEV_REFINED_CAP", "OT_DEV_WINDOW",
     "OtError", "Octree", "Batch", "library_path", "ot_octree_build", "ot_octree_from_leaves", "ot_octree_info",
-    "ot_octree_copy_leaves", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats",
+    "ot_octree_copy_leaves", "ot_octree_set_map_level", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats",
     "ot_index_mlp_grad", "ot_locate", "ot_interpolate", "ot_interpolate_f64", "ot_spread_workspace_size",
     "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
     "ot_last_error", "ot_launch_count",
@@ -71,7 +71,7 @@ class _Group(C.Structure):
 
 
 class _Launch(C.Structure):
-    _fields_ = [("block", C.c_int), ("tile", C.c_int), ("blocks_per_sm", C.c_int), ("stage_log2", C.c_int)]
+    _fields_ = [("block", C.c_int), ("tile", C.c_int), ("blocks_per_sm", C.c_int)]
 
 
 def _L():
@@ -92,6 +92,7 @@ def _L():
                 "ot_octree_leaves": (st, [P, P, P, P]),
                 "ot_octree_copy_leaves": (st, [P, P, P, P]),
                 "ot_octree_centres": (st, [P, P, P]),
+                "ot_octree_set_map_level": (st, [P, i32, P]),
                 "ot_octree_destroy": (st, [P]),
                 "ot_index_train": (st, [P, P, P]),
                 "ot_index_get_stats": (st, [P, P, i32]),
@@ -214,6 +215,10 @@ def ot_octree_copy_leaves(tree: Octree, stream=None):
     lev = torch.empty(n, dtype=torch.uint8, device="cuda")
     _check(_L().ot_octree_copy_leaves(tree.handle, _dptr(keys), _dptr(lev), _stream(stream)))
     return keys, lev
+
+
+def ot_octree_set_map_level(tree: Octree, level: int, stream=None):
+    _check(_L().ot_octree_set_map_level(tree.handle, level, _stream(stream)))
 
 
 def ot_octree_centres(tree: Octree, out=None, stream=None):
@@ -352,8 +357,7 @@ def ot_batch_create(tree: Octree, groups, field, search: int = OT_BINARY, launch
         keep.append(g)
     lp = None
     if launch:
-        lp = _Launch(launch.get("block", 0), launch.get("tile", 0), launch.get("blocks_per_sm", 0),
-                     launch.get("stage_log2", 0))
+        lp = _Launch(launch.get("block", 0), launch.get("tile", 0), launch.get("blocks_per_sm", 0))
     h = C.c_void_p()
     _check(_L().ot_batch_create(tree.handle, arr, len(groups), _dptr(field, torch.float32, "field"), search,
                                 C.byref(lp) if lp is not None else None, _stream(stream), C.byref(h)))

@@ -172,6 +172,11 @@ ot_status ot_octree_copy_leaves(const ot_octree* t, uint64_t* d_keys, uint8_t* d
     return OT_OK;
 }
 
+ot_status ot_octree_set_map_level(ot_octree* t, int level, void* stream) {
+    if (!t || level < 0 || level > 8) return OT_ERR_ARG;
+    return finish_tree(t, (cudaStream_t)stream, level);
+}
+
 ot_status ot_octree_centres(const ot_octree* t, double* d_xyz, void* stream) {
     if (!t || !d_xyz) return OT_ERR_ARG;
     return leaf_centres(t, d_xyz, (cudaStream_t)stream);
@@ -181,9 +186,10 @@ ot_status ot_octree_destroy(ot_octree* t) {
     if (!t) return OT_OK;
     if (t->d_key) cudaFree(t->d_key);
     if (t->d_level) cudaFree(t->d_level);
-    if (t->d_sample) cudaFree(t->d_sample);
+    if (t->d_lmap) cudaFree(t->d_lmap);
     if (t->d_models) cudaFree(t->d_models);
     if (t->d_mids) cudaFree(t->d_mids);
+    if (t->d_root) cudaFree(t->d_root);
     if (t->d_err) cudaFree(t->d_err);
     delete t;
     return OT_OK;

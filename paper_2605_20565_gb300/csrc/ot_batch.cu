@@ -1,7 +1,8 @@
 // ot_batch.cu -- one persistent launch over every group of points (IBM markers with a delta
 // kernel, point particles with trilinear interpolation), replayed from a CUDA graph.
 //
-// Work is cut into tiles of 32 * tile points; warps take tiles from a global counter, the
+// A graph replay first recomputes the prefix of the volume-weighted field (refined trilinear
+// level-mates read it), then runs the batch kernel.  Work is cut into tiles of 32 * tile points; warps take tiles from a global counter, the
 // expensive marker groups first (their tiles come first in the tile space), so uneven groups
 // balance across the SMs without a host round trip.  The counter is reset by a memset node
 // captured in the same graph.
@@ -17,7 +18,8 @@ struct ot_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned* d_counter = nullptr;
-    uint64_t* d_sample = nullptr;
+    void* d_prefix = nullptr;  // volume-weighted field prefix, recomputed at every replay
+    int kernels = 1;           // kernels in one replay of the graph
 };
 
 namespace ot {
@@ -41,12 +43,8 @@ struct BatchArgs {
 };
 
 template <bool LEARNED>
-__global__ void __launch_bounds__(256) k_batch(TreeView t, RootModel rm, BatchArgs a, const float* __restrict__ field,
-                                               unsigned* __restrict__ counter) {
-    extern __shared__ uint64_t s_sample[];
-    const bool staged = t.nsample > 1;  // plain search, and the learned fallback
-    if (staged) load_sample(t, s_sample);
-    const uint64_t* ss = staged ? s_sample : nullptr;
+__global__ void __launch_bounds__(256) k_batch(TreeView t, BatchArgs a, const float* __restrict__ field,
+                                               const double4* __restrict__ P, unsigned* __restrict__ counter) {
     const int lane = threadIdx.x & 31;
     const int64_t tile_pts = 32 * (int64_t)a.tile;
     for (;;) {
@@ -66,13 +64,13 @@ __global__ void __launch_bounds__(256) k_batch(TreeView t, RootModel rm, BatchAr
             int h;
             const double x = active ? gr.x[i] : 0.0, y = active ? gr.y[i] : 0.0, z = active ? gr.z[i] : 0.0;
             if (gr.kernel == OT_TRILINEAR)
-                h = trilinear_warp<float, LEARNED>(t, rm, ss, field, active, x, y, z, -1, o);
+                h = trilinear_point<float, LEARNED>(t, field, P, active, x, y, z, -1, o);
             else if (!active)
                 h = -1;
             else if (gr.kernel == OT_PESKIN4)
-                h = delta_point<float, OT_PESKIN4, LEARNED>(t, rm, ss, field, x, y, z, gr.host != nullptr, o);
+                h = delta_point<float, OT_PESKIN4, LEARNED>(t, field, x, y, z, gr.host != nullptr, o);
             else
-                h = delta_point<float, OT_ROMA3, LEARNED>(t, rm, ss, field, x, y, z, gr.host != nullptr, o);
+                h = delta_point<float, OT_ROMA3, LEARNED>(t, field, x, y, z, gr.host != nullptr, o);
             if (active) {
                 gr.u[i] = o[0];
                 gr.u[gr.n + i] = o[1];
@@ -83,10 +81,6 @@ __global__ void __launch_bounds__(256) k_batch(TreeView t, RootModel rm, BatchAr
     }
 }
 
-__global__ void k_batch_sample(const uint64_t* __restrict__ key, int nsample, int stride, uint64_t* __restrict__ out) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nsample; b += gridDim.x * blockDim.x)
-        out[b] = key[(int64_t)b * stride];
-}
 
 } // namespace ot
 
@@ -100,8 +94,7 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     *out = nullptr;
     const int block = (launch && launch->block) ? launch->block : 256;
     const int tile = (launch && launch->tile) ? launch->tile : 4;
-    const int stage = (launch && launch->stage_log2) ? launch->stage_log2 : t->stage_log2;
-    if (block < 64 || block > 256 || block % 32 || tile < 1 || tile > 64 || stage < 1 || stage > 14) return OT_ERR_ARG;
+    if (block < 64 || block > 256 || block % 32 || tile < 1 || tile > 64) return OT_ERR_ARG;
     BatchArgs a{};
     a.ng = n_groups;
     a.tile = tile;
@@ -134,21 +127,12 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     };
     cudaError_t e;
     if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned))) != cudaSuccess) return fail(e);
-    TreeView v = tree_view(t, true);
-    {
-        int64_t ns = std::min<int64_t>((int64_t)1 << stage, t->n);
-        int64_t stride = (t->n + ns - 1) / ns;
-        ns = (t->n + stride - 1) / stride;
-        if ((e = cudaMalloc(&b->d_sample, sizeof(uint64_t) * ns)) != cudaSuccess) return fail(e);
-        k_batch_sample<<<(unsigned)((ns + 255) / 256), 256, 0, (cudaStream_t)stream>>>(t->d_key, (int)ns, (int)stride,
-                                                                                      b->d_sample);
-        count_launch();
-        if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess) return fail(e);
-        v.sample = b->d_sample;
-        v.nsample = (int)ns;
-        v.stride = (int)stride;
-    }
-    const size_t smem = (size_t)v.nsample * sizeof(uint64_t);
+    bool has_tri = false;
+    for (int k = 0; k < n_groups; ++k) has_tri = has_tri || groups[k].kernel == OT_TRILINEAR;
+    if (has_tri && (e = cudaMalloc(&b->d_prefix, prefix_bytes(t->n))) != cudaSuccess) return fail(e);
+    b->kernels = has_tri ? 4 : 1;
+    TreeView v = tree_view(t);
+    const size_t smem = 0;
     void* kfn = search == OT_LEARNED ? (void*)k_batch<true> : (void*)k_batch<false>;
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -162,9 +146,15 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e);
     cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), cs);
-    RootModel rm = t->root;
+    if (has_tri && launch_prefix<float>(t, d_field, b->d_prefix, cs) != OT_OK) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(cs, &g);
+        if (g) cudaGraphDestroy(g);
+        return fail(cudaErrorUnknown);
+    }
+    const double4* P = static_cast<const double4*>(b->d_prefix);
     {
-        void* args[] = {&v, &rm, &a, (void*)&d_field, &b->d_counter};
+        void* args[] = {&v, &a, (void*)&d_field, (void*)&P, &b->d_counter};
         cudaLaunchKernel(kfn, dim3(grid), dim3(block), args, smem, cs);
     }
     e = cudaStreamEndCapture(cs, &b->graph);
@@ -179,7 +169,7 @@ extern "C" ot_status ot_batch_run(ot_batch* b, void* stream) {
     if (!b || !b->exec) return OT_ERR_ARG;
     cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_status(e);
-    count_launch();
+    count_launch((uint64_t)b->kernels);
     return OT_OK;
 }
 
@@ -188,7 +178,7 @@ extern "C" ot_status ot_batch_destroy(ot_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->d_counter) cudaFree(b->d_counter);
-    if (b->d_sample) cudaFree(b->d_sample);
+    if (b->d_prefix) cudaFree(b->d_prefix);
     delete b;
     return OT_OK;
 }

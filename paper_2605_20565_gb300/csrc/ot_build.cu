@@ -1,4 +1,4 @@
-// ot_build.cu -- octree construction on the device, leaf validation, centres, search sample.
+// ot_build.cu -- octree construction on the device, leaf validation, centres, level map.
 //
 // Construction (Sec. 3.1 refinement + 2:1 balance, Sec. 3.3 surface-driven auxiliary forest)
 // works on per-level sorted key arrays R[l] of the REFINED cells of level l (3l-bit keys):
@@ -463,8 +463,9 @@ __global__ void k_centres(const uint64_t* __restrict__ key, const uint8_t* __res
     }
 }
 
-__global__ void k_sample(const uint64_t* __restrict__ key, int nsample, int stride, uint64_t* __restrict__ out) {
-    GRID_STRIDE(b, (int64_t)nsample) out[b] = key[b * (int64_t)stride];
+// lmap[c] = the leaf holding the anchor of level-L cell c: the last key <= its anchor.
+__global__ void k_lmap(const uint64_t* __restrict__ key, int n, int L, int64_t ncell, uint32_t* __restrict__ out) {
+    GRID_STRIDE(c, ncell) out[c] = (uint32_t)search_range(key, 0, n, (uint64_t)c << (3 * (MAXLEVEL - L)));
 }
 
 } // namespace
@@ -476,17 +477,15 @@ ot_status leaf_centres(const ot_octree* t, double* d_xyz, cudaStream_t s) {
     return OT_OK;
 }
 
-ot_status finish_tree(ot_octree* t, cudaStream_t s) {
-    const int64_t cap = (int64_t)1 << t->stage_log2;
-    int64_t ns = std::min<int64_t>(cap, t->n);
-    int64_t stride = (t->n + ns - 1) / ns;
-    ns = (t->n + stride - 1) / stride;
-    if (t->d_sample) cudaFree(t->d_sample);
-    OT_CUDA(cudaMalloc(&t->d_sample, sizeof(uint64_t) * ns));
-    k_sample<<<grid1d(ns, 256), 256, 0, s>>>(t->d_key, (int)ns, (int)stride, t->d_sample);
+ot_status finish_tree(ot_octree* t, cudaStream_t s, int map_level) {
+    const int L = map_level >= 0 ? std::min(map_level, t->lmax) : std::min(t->lmax, 7);
+    const int64_t ncell = (int64_t)1 << (3 * L);
+    if (t->d_lmap) cudaFree(t->d_lmap);
+    t->d_lmap = nullptr;
+    OT_CUDA(cudaMalloc(&t->d_lmap, sizeof(uint32_t) * ncell));
+    k_lmap<<<grid1d(ncell, 256), 256, 0, s>>>(t->d_key, (int)t->n, L, ncell, t->d_lmap);
     count_launch();
-    t->nsample = (int)ns;
-    t->stride = (int)stride;
+    t->lmap_level = L;
     if (!t->d_err) {
         OT_CUDA(cudaMalloc(&t->d_err, 64));
         OT_CUDA(cudaMemsetAsync(t->d_err, 0, 64, s));
@@ -497,16 +496,16 @@ ot_status finish_tree(ot_octree* t, cudaStream_t s) {
     return OT_OK;
 }
 
-TreeView tree_view(const ot_octree* t, bool with_sample) {
+TreeView tree_view(const ot_octree* t) {
     TreeView v{};
     v.key = t->d_key;
     v.level = t->d_level;
     v.n = (int)t->n;
     v.lmin = t->lmin;
     v.lmax = t->lmax;
-    v.sample = with_sample ? t->d_sample : nullptr;
-    v.nsample = with_sample ? t->nsample : 0;
-    v.stride = t->stride;
+    v.lmap = t->d_lmap;
+    v.lmap_level = t->lmap_level;
+    v.root = t->d_root;
     v.models = t->d_models;
     v.mids = t->d_mids;
     v.n_leaf = t->n_models;

@@ -128,11 +128,12 @@ struct TreeView {
     const uint8_t* __restrict__ level;
     int n;
     int lmin, lmax;
-    // plain search: shared-memory sample of every stride-th key (nsample entries)
-    const uint64_t* __restrict__ sample;
-    int nsample;
-    int stride;
+    // level map: lmap[c] = the leaf holding the anchor of cell c of level lmap_level (the
+    // top levels of the tree, staged as a dense table)
+    const uint32_t* __restrict__ lmap;
+    int lmap_level;
     // learned search: root -> (optional mid models) -> leaf models
+    const RootModel* __restrict__ root;  // device copy
     const LeafModel* __restrict__ models;
     const LeafModel* __restrict__ mids;  // null for a two-stage index
     int n_leaf;                          // leaf models
@@ -153,25 +154,25 @@ __device__ __forceinline__ int search_range(const uint64_t* __restrict__ key, in
     return lo;
 }
 
-// Last sample index whose key <= q, sample in shared memory (sample[0] = key[0] = 0 <= q).
-__device__ __forceinline__ int search_smem(const uint64_t* s, int len, uint64_t q) {
-    int lo = 0;
-    while (len > 1) {
-        int half = len >> 1;
-        lo = (s[lo + half] <= q) ? lo + half : lo;
-        len -= half;
-    }
-    return lo;
+// Cell of the level map holding key q, and the leaf range [a, e) of that cell: a is the leaf
+// holding the cell's anchor; when that leaf's level is <= the map level it covers the whole
+// cell (then it is the answer for every key in the cell).
+__device__ __forceinline__ void map_range(const TreeView& t, uint64_t q, int& a, int& e, bool& covered) {
+    const uint32_t c = (uint32_t)(q >> (3 * (MAXLEVEL - t.lmap_level)));
+    a = (int)t.lmap[c];
+    covered = (int)t.level[a] <= t.lmap_level;
+    e = (c + 1 < (1u << (3 * t.lmap_level))) ? (int)t.lmap[c + 1] : t.n;
 }
 
-// Plain host search: the shared-memory sample selects a bucket of `stride` keys, a branch-free
-// binary search in global memory finishes.  s_sample may be null (then search [0, n)).
-__device__ __forceinline__ int search_plain(const TreeView& t, const uint64_t* s_sample, uint64_t q) {
-    if (s_sample == nullptr || t.nsample <= 1) return search_range(t.key, 0, t.n, q);
-    int b = search_smem(s_sample, t.nsample, q);
-    int lo = b * t.stride;
-    int len = min(t.stride, t.n - lo);
-    return search_range(t.key, lo, len, q);
+// Plain host search (Algorithm 1's answer, upper bound - 1): the level map gives the leaf
+// directly for a cell covered by one leaf, else the cell's range of leaves, which a
+// branch-free binary search finishes (key[a] <= q: a holds the cell's anchor).
+__device__ __forceinline__ int search_plain(const TreeView& t, uint64_t q) {
+    int a, e;
+    bool covered;
+    map_range(t, q, a, e, covered);
+    if (covered) return a;
+    return search_range(t.key, a, e - a, q);
 }
 
 // Input of the root model: key 2^-63 in FP32 (rounded toward zero).
@@ -215,38 +216,49 @@ __device__ __forceinline__ int route_leaf(const RootModel& r, const LeafModel* m
     return (int)(((int64_t)pc * n_leaf) / n);
 }
 
-// Learned host search: the models give a window [pc - err_lo - 1, pc + err_hi + 1]; it is
-// searched by halving and the answer a is verified by key[a] <= q < key[a+1]; a window that missed
-// is answered by the plain search (counted as a fallback).
-__device__ __forceinline__ int search_learned(const TreeView& t, const RootModel& r, const uint64_t* s_sample,
-                                              uint64_t q) {
-    const int j = route_leaf(r, t.mids, t.n_leaf, t.n, q);
-    const LeafModel m = t.models[j];
+// Learned search inside a level-map cell [ca, ce) that one leaf does not cover: the models give
+// a window [pc - err_lo - 1, pc + err_hi + 1], clamped to the cell, searched by halving; the
+// answer a is verified by key[a] <= q < key[a+1], and a window that missed is answered by a
+// binary search of the cell (counted as a fallback).  Out of line: one copy serves every call
+// site, and the root network stays in device memory.
+static __device__ __noinline__ int learned_in_cell(const uint64_t* __restrict__ key, const RootModel* __restrict__ root,
+                                            const LeafModel* __restrict__ mids, const LeafModel* __restrict__ models,
+                                            int n, int n_leaf, int ca, int ce, uint64_t q,
+                                            unsigned long long* fallbacks, unsigned* err) {
+    const int j = route_leaf(*root, mids, n_leaf, n, q);
+    const LeafModel m = models[j];
     if (m.count > 0) {
-        const int pc = leaf_predict(m, q, t.n);
-        const int lo = max(pc - m.err_lo - 1, 0);
-        const int hi = min(pc + m.err_hi + 1, t.n - 1);
-        const int a = search_range(t.key, lo, hi - lo + 1, q);
-        const uint64_t a0 = ldg_key(t.key + a);
-        const uint64_t a1 = a + 1 < t.n ? ldg_key(t.key + a + 1) : ~0ULL;
-        if (a0 <= q && q < a1) return a;
+        const int pc = leaf_predict(m, q, n);
+        const int lo = max(pc - m.err_lo - 1, ca);
+        const int hi = min(pc + m.err_hi + 1, ce - 1);
+        if (lo <= hi) {
+            const int a = search_range(key, lo, hi - lo + 1, q);
+            const uint64_t a0 = ldg_key(key + a);
+            const uint64_t a1 = a + 1 < n ? ldg_key(key + a + 1) : ~0ULL;
+            if (a0 <= q && q < a1) return a;
+        }
     }
-    atomicAdd(t.fallbacks, 1ULL);
-    atomicOr(t.err, (unsigned)OT_DEV_WINDOW);
-    return search_plain(t, s_sample, q);
+    atomicAdd(fallbacks, 1ULL);
+    atomicOr(err, (unsigned)OT_DEV_WINDOW);
+    return search_range(key, ca, ce - ca, q);
+}
+
+// Learned host search: the level map first (a covered cell answers directly), the models
+// inside an uncovered cell.
+__device__ __forceinline__ int search_learned(const TreeView& t, uint64_t q) {
+    int ca, ce;
+    bool covered;
+    map_range(t, q, ca, ce, covered);
+    if (covered) return ca;
+    return learned_in_cell(t.key, t.root, t.mids, t.models, t.n, t.n_leaf, ca, ce, q, t.fallbacks, t.err);
 }
 
 template <bool LEARNED>
-__device__ __forceinline__ int search(const TreeView& t, const RootModel& r, const uint64_t* s_sample, uint64_t q) {
-    if (LEARNED) return search_learned(t, r, s_sample, q);
-    return search_plain(t, s_sample, q);
+__device__ __forceinline__ int search(const TreeView& t, uint64_t q) {
+    if (LEARNED) return search_learned(t, q);
+    return search_plain(t, q);
 }
 
-// Cooperative load of the plain-search sample into shared memory.
-__device__ __forceinline__ void load_sample(const TreeView& t, uint64_t* s) {
-    for (int i = threadIdx.x; i < t.nsample; i += blockDim.x) s[i] = ldg_key(t.sample + i);
-    __syncthreads();
-}
 
 // ------------------------------------------------------------------------------------------
 // Discrete delta functions (Sec. 2.2), argument in grid units.  Square-root arguments are

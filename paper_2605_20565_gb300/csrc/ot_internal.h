@@ -15,14 +15,13 @@ struct ot_octree {
     int lmin = 0, lmax = 0;
     uint64_t* d_key = nullptr;
     uint8_t* d_level = nullptr;
-    // plain-search sample (every stride-th key)
-    uint64_t* d_sample = nullptr;
-    int nsample = 0;
-    int stride = 0;
-    int stage_log2 = 12;
+    // level map: the leaf holding the anchor of every cell of level lmap_level
+    uint32_t* d_lmap = nullptr;
+    int lmap_level = 0;
     // learned index
     bool has_index = false;
     ot::RootModel root{};
+    ot::RootModel* d_root = nullptr;  // device copy read by the queries
     ot::LeafModel* d_models = nullptr;  // leaf models
     int n_models = 0;
     ot::LeafModel* d_mids = nullptr;    // middle stage (null: two-stage index)
@@ -48,7 +47,7 @@ ot_status cuda_status(cudaError_t e);
 
 int num_sms();
 
-TreeView tree_view(const ot_octree* t, bool with_sample = true);
+TreeView tree_view(const ot_octree* t);
 
 // primitives (ot_prims.cu) -------------------------------------------------------------------
 // Exclusive scan of n uint32 (in place allowed); returns the total in *d_total if non-null.
@@ -77,7 +76,8 @@ ot_status radix_sort_u64_noalloc(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, i
 
 // builder (ot_build.cu) ------------------------------------------------------------------------
 ot_status build_tree(const ot_sphere* h_spheres, int n, const ot_build_params* p, cudaStream_t s, ot_octree* t);
-ot_status finish_tree(ot_octree* t, cudaStream_t s); // sample, error word
+// Level map (level < 0: min(lmax, 7)) and the error word.
+ot_status finish_tree(ot_octree* t, cudaStream_t s, int map_level = -1);
 ot_status validate_leaves(const uint64_t* d_key, const uint8_t* d_level, int64_t n, int full, cudaStream_t s,
                           int* lmin, int* lmax);
 ot_status leaf_centres(const ot_octree* t, double* d_xyz, cudaStream_t s);
@@ -93,6 +93,11 @@ ot_status launch_locate(const ot_octree* t, const double* x, const double* y, co
 template <typename T>
 ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const double* y, const double* z, int64_t n,
                         const int32_t* host_in, int search, const T* field, T* u, int32_t* host_out, cudaStream_t s);
+
+// volume-weighted field prefix (ot_prefix.cu) --------------------------------------------------
+// P (n + 1 double4 entries, P[i] = sum_{j<i} f_j 8^-level_j) and tile sums in ws.
+size_t prefix_bytes(int64_t n);
+template <typename T> ot_status launch_prefix(const ot_octree* t, const T* field, void* ws, cudaStream_t s);
 
 // spreading (ot_spread.cu) ---------------------------------------------------------------------
 size_t spread_ws_bytes(const ot_octree* t, int kernel, int64_t n);

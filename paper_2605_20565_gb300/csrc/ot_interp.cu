@@ -1,6 +1,5 @@
 // ot_interp.cu -- single-op kernels: locate, trilinear and delta-kernel interpolation.
-// Persistent grid-stride launches (a few blocks per SM); each block stages the plain-search
-// sample of top-level keys in shared memory once.
+// Persistent grid-stride launches (a few blocks per SM).
 #include <algorithm>
 
 #include "ot_internal.h"
@@ -11,19 +10,15 @@ namespace ot {
 namespace {
 
 template <bool LEARNED>
-__global__ void __launch_bounds__(256) k_locate(TreeView t, RootModel rm, const double* __restrict__ x,
+__global__ void __launch_bounds__(256) k_locate(TreeView t, const double* __restrict__ x,
                                                 const double* __restrict__ y, const double* __restrict__ z, int64_t n,
                                                 int32_t* __restrict__ host, unsigned long long* n_miss) {
-    extern __shared__ uint64_t s_sample[];
-    const bool staged = t.nsample > 1;
-    if (staged) load_sample(t, s_sample);
-    const uint64_t* ss = staged ? s_sample : nullptr;
     unsigned miss = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         uint64_t X[3];
         int h = -1;
         if (fixpoint3(x[i], y[i], z[i], X))
-            h = search<LEARNED>(t, rm, ss,
+            h = search<LEARNED>(t,
                                 morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32)));
         else
             ++miss;
@@ -36,15 +31,11 @@ __global__ void __launch_bounds__(256) k_locate(TreeView t, RootModel rm, const 
 }
 
 template <typename T, bool LEARNED>
-__global__ void __launch_bounds__(256) k_trilinear(TreeView t, RootModel rm, const double* __restrict__ x,
+__global__ void __launch_bounds__(256) k_trilinear(TreeView t, const double* __restrict__ x,
                                                    const double* __restrict__ y, const double* __restrict__ z,
                                                    int64_t n, const int32_t* __restrict__ host_in,
-                                                   const T* __restrict__ field, T* __restrict__ u,
-                                                   int32_t* __restrict__ host_out) {
-    extern __shared__ uint64_t s_sample[];
-    const bool staged = t.nsample > 1;
-    if (staged) load_sample(t, s_sample);
-    const uint64_t* ss = staged ? s_sample : nullptr;
+                                                   const T* __restrict__ field, const double4* __restrict__ P,
+                                                   T* __restrict__ u, int32_t* __restrict__ host_out) {
     // warp-aligned iteration: every lane of a warp runs the same trip count (the trilinear
     // routine is warp-cooperative)
     const int lane = threadIdx.x & 31;
@@ -64,8 +55,8 @@ __global__ void __launch_bounds__(256) k_trilinear(TreeView t, RootModel rm, con
                 active = false;
             }
         }
-        const int h = trilinear_warp<T, LEARNED>(t, rm, ss, field, active, inr ? x[i] : 0.0, inr ? y[i] : 0.0,
-                                                 inr ? z[i] : 0.0, hin, o);
+        const int h = trilinear_point<T, LEARNED>(t, field, P, active, inr ? x[i] : 0.0, inr ? y[i] : 0.0,
+                                                  inr ? z[i] : 0.0, hin, o);
         if (inr) {
             u[i] = o[0];
             u[n + i] = o[1];
@@ -76,17 +67,13 @@ __global__ void __launch_bounds__(256) k_trilinear(TreeView t, RootModel rm, con
 }
 
 template <typename T, int K, bool LEARNED>
-__global__ void __launch_bounds__(256) k_delta(TreeView t, RootModel rm, const double* __restrict__ x,
+__global__ void __launch_bounds__(256) k_delta(TreeView t, const double* __restrict__ x,
                                                const double* __restrict__ y, const double* __restrict__ z, int64_t n,
                                                const T* __restrict__ field, T* __restrict__ u,
                                                int32_t* __restrict__ host_out) {
-    extern __shared__ uint64_t s_sample[];
-    const bool staged = t.nsample > 1;
-    if (staged) load_sample(t, s_sample);
-    const uint64_t* ss = staged ? s_sample : nullptr;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         T o[3];
-        const int h = delta_point<T, K, LEARNED>(t, rm, ss, field, x[i], y[i], z[i], host_out != nullptr, o);
+        const int h = delta_point<T, K, LEARNED>(t, field, x[i], y[i], z[i], host_out != nullptr, o);
         u[i] = o[0];
         u[n + i] = o[1];
         u[2 * n + i] = o[2];
@@ -116,19 +103,19 @@ ot_status launch_locate(const ot_octree* t, const double* x, const double* y, co
                         int32_t* host, unsigned long long* n_miss, cudaStream_t s) {
     if (n == 0) return OT_OK;
     const bool learned = search == OT_LEARNED;
-    TreeView v = tree_view(t, true);  // the sample serves plain searches and learned fallbacks
-    const size_t smem = (size_t)v.nsample * sizeof(uint64_t);
+    TreeView v = tree_view(t);
+    const size_t smem = 0;
     const int block = 256;
     if (learned) {
         auto k = k_locate<true>;
         ot_status st = prep_smem(k, smem);
         if (st != OT_OK) return st;
-        k<<<persistent_grid(k, block, smem, n), block, smem, s>>>(v, t->root, x, y, z, n, host, n_miss);
+        k<<<persistent_grid(k, block, smem, n), block, smem, s>>>(v, x, y, z, n, host, n_miss);
     } else {
         auto k = k_locate<false>;
         ot_status st = prep_smem(k, smem);
         if (st != OT_OK) return st;
-        k<<<persistent_grid(k, block, smem, n), block, smem, s>>>(v, t->root, x, y, z, n, host, n_miss);
+        k<<<persistent_grid(k, block, smem, n), block, smem, s>>>(v, x, y, z, n, host, n_miss);
     }
     count_launch();
     OT_CUDA(cudaGetLastError());
@@ -140,8 +127,8 @@ ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const d
                         const int32_t* host_in, int search, const T* field, T* u, int32_t* host_out, cudaStream_t s) {
     if (n == 0) return OT_OK;
     const bool learned = search == OT_LEARNED;
-    TreeView v = tree_view(t, true);  // the sample serves plain searches and learned fallbacks
-    const size_t smem = (size_t)v.nsample * sizeof(uint64_t);
+    TreeView v = tree_view(t);
+    const size_t smem = 0;
     const int block = 256;
     ot_status st = OT_OK;
 #define OT_LAUNCH(KERN, ...)                                                               \
@@ -151,20 +138,29 @@ ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const d
         k_<<<persistent_grid(k_, block, smem, n), block, smem, s>>>(__VA_ARGS__);          \
     } while (0)
     if (kernel == OT_TRILINEAR) {
+        // prefix of the volume-weighted field (refined level-mates), stream-ordered scratch
+        void* pws = nullptr;
+        OT_CUDA(cudaMallocAsync(&pws, prefix_bytes(t->n), s));
+        if ((st = launch_prefix<T>(t, field, pws, s)) != OT_OK) {
+            cudaFreeAsync(pws, s);
+            return st;
+        }
+        const double4* P = static_cast<const double4*>(pws);
         if (learned)
-            OT_LAUNCH((k_trilinear<T, true>), v, t->root, x, y, z, n, host_in, field, u, host_out);
+            OT_LAUNCH((k_trilinear<T, true>), v, x, y, z, n, host_in, field, P, u, host_out);
         else
-            OT_LAUNCH((k_trilinear<T, false>), v, t->root, x, y, z, n, host_in, field, u, host_out);
+            OT_LAUNCH((k_trilinear<T, false>), v, x, y, z, n, host_in, field, P, u, host_out);
+        cudaFreeAsync(pws, s);
     } else if (kernel == OT_PESKIN4) {
         if (learned)
-            OT_LAUNCH((k_delta<T, OT_PESKIN4, true>), v, t->root, x, y, z, n, field, u, host_out);
+            OT_LAUNCH((k_delta<T, OT_PESKIN4, true>), v, x, y, z, n, field, u, host_out);
         else
-            OT_LAUNCH((k_delta<T, OT_PESKIN4, false>), v, t->root, x, y, z, n, field, u, host_out);
+            OT_LAUNCH((k_delta<T, OT_PESKIN4, false>), v, x, y, z, n, field, u, host_out);
     } else {
         if (learned)
-            OT_LAUNCH((k_delta<T, OT_ROMA3, true>), v, t->root, x, y, z, n, field, u, host_out);
+            OT_LAUNCH((k_delta<T, OT_ROMA3, true>), v, x, y, z, n, field, u, host_out);
         else
-            OT_LAUNCH((k_delta<T, OT_ROMA3, false>), v, t->root, x, y, z, n, field, u, host_out);
+            OT_LAUNCH((k_delta<T, OT_ROMA3, false>), v, x, y, z, n, field, u, host_out);
     }
 #undef OT_LAUNCH
     count_launch();

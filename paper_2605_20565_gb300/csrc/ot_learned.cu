@@ -481,6 +481,8 @@ ot_status train_index(ot_octree* t, const ot_index_params* prm, cudaStream_t s) 
     }
     OT_CUDA(cudaStreamSynchronize(s));
     t->root = rm;
+    if (!t->d_root) OT_CUDA(cudaMalloc(&t->d_root, sizeof(RootModel)));
+    OT_CUDA(cudaMemcpy(t->d_root, &rm, sizeof(RootModel), cudaMemcpyHostToDevice));
     t->n_models = M;
     t->n_mids = three ? prm->n_mid_models : 0;
     t->has_index = true;

@@ -1,10 +1,12 @@
 // ot_spread.cu -- force spreading, the adjoint of the delta-kernel interpolation (Sec. 2.2):
 //   f(cell) += sum_k F_k phi(rx) phi(ry) phi(rz) dV_k / h^3.
 // OT_ATOMIC: each marker adds its stencil contributions with float atomics.
-// OT_SORTED: each marker emits one 64-bit pair per stencil slot, (leaf << 32) | (k W^3 + slot);
-//   a stable radix sort by leaf groups the pairs of a leaf in marker order; one thread per
-//   leaf then recomputes the weights and sums in that order and adds once to f (no atomics,
-//   bit-identical from run to run and for any launch shape).
+// OT_SORTED: each marker emits one 64-bit pair per overlapping parent block (2x2x2 finest
+//   cells), (first child leaf << 32) | (k PS + slot); a stable radix sort by parent groups the
+//   pairs of a block in marker order; one thread per block then recomputes the weights, sums
+//   its 8 children in that order and adds each once to f (no atomics, bit-identical from run
+//   to run and for any launch shape; per leaf the same sum in the same order as a per-cell
+//   reduction).
 #include <algorithm>
 
 #include "ot_internal.h"
@@ -33,14 +35,10 @@ __device__ __forceinline__ T marker_volume(const T* __restrict__ dV, int64_t k, 
 }
 
 template <typename T, int K>
-__global__ void __launch_bounds__(256) k_spread_atomic(TreeView t, RootModel rm, const double* __restrict__ x,
+__global__ void __launch_bounds__(256) k_spread_atomic(TreeView t, const double* __restrict__ x,
                                                        const double* __restrict__ y, const double* __restrict__ z,
                                                        const T* __restrict__ F, const T* __restrict__ dV, int64_t n,
                                                        T* __restrict__ f) {
-    extern __shared__ uint64_t s_sample[];
-    const bool staged = t.nsample > 1;
-    if (staged) load_sample(t, s_sample);
-    const uint64_t* ss = staged ? s_sample : nullptr;
     constexpr int W = Stencil<K>::W;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         uint64_t X[3];
@@ -53,7 +51,7 @@ __global__ void __launch_bounds__(256) k_spread_atomic(TreeView t, RootModel rm,
         stencil_weights<K, T>(t.lmax, X, i0, w);
         const T vol = marker_volume(dV, k, t.lmax);
         const T F0 = F[k] * vol, F1 = F[n + k] * vol, F2 = F[2 * n + k] * vol;
-        const bool ok = visit_stencil<K, false>(t, rm, ss, i0, [&](int leaf, int ax, int ay, int az) {
+        const bool ok = visit_stencil<K, false>(t, i0, [&](int leaf, int ax, int ay, int az) {
             const T wt = w[0][ax] * w[1][ay] * w[2][az];
             add3<T>(f, leaf, F0 * wt, F1 * wt, F2 * wt);
         });
@@ -61,19 +59,22 @@ __global__ void __launch_bounds__(256) k_spread_atomic(TreeView t, RootModel rm,
     }
 }
 
+// Parent slots per marker: the stencil spans up to PW parent blocks per axis.
+template <int K> struct ParentSlots {
+    static constexpr int PW = Stencil<K>::W == 4 ? 3 : 2;
+    static constexpr int PS = PW * PW * PW;
+};
+
+// One pair per (marker, overlapping parent block): (first child leaf << 32) | (k PS + slot).
 template <int K>
-__global__ void __launch_bounds__(256) k_spread_emit(TreeView t, RootModel rm, const double* __restrict__ x,
+__global__ void __launch_bounds__(256) k_spread_emit(TreeView t, const double* __restrict__ x,
                                                      const double* __restrict__ y, const double* __restrict__ z,
                                                      int64_t n, uint64_t* __restrict__ pairs) {
-    extern __shared__ uint64_t s_sample[];
-    const bool staged = t.nsample > 1;
-    if (staged) load_sample(t, s_sample);
-    const uint64_t* ss = staged ? s_sample : nullptr;
-    constexpr int W = Stencil<K>::W, W3 = W * W * W;
+    constexpr int PW = ParentSlots<K>::PW, PS = ParentSlots<K>::PS;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t* out = pairs + k * W3;
-        const uint64_t id0 = (uint64_t)k * W3;
-        for (int sl = 0; sl < W3; ++sl) out[sl] = (INVALID_HI << 32) | (id0 + sl);
+        uint64_t* out = pairs + k * PS;
+        const uint64_t id0 = (uint64_t)k * PS;
+        for (int sl = 0; sl < PS; ++sl) out[sl] = (INVALID_HI << 32) | (id0 + sl);
         uint64_t X[3];
         if (!fixpoint3(x[k], y[k], z[k], X)) {
             atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
@@ -82,49 +83,85 @@ __global__ void __launch_bounds__(256) k_spread_emit(TreeView t, RootModel rm, c
         int i0[3];
         for (int d = 0; d < 3; ++d)
             i0[d] = Stencil<K>::first((int)fix_cell(X[d], t.lmax), fix_upper_half(X[d], t.lmax) ? 1 : 0);
-        const bool ok = visit_stencil<K, false>(t, rm, ss, i0, [&](int leaf, int ax, int ay, int az) {
-            const int sl = ax + W * (ay + W * az);
-            out[sl] = ((uint64_t)(uint32_t)leaf << 32) | (id0 + sl);
+        bool ok = true;
+        visit_parents<K, false>(t, i0, [&](int a0, int bx, int by, int bz, const int*) {
+            if (a0 < 0) {
+                ok = false;
+                return;
+            }
+            const int sl = bx + PW * (by + PW * bz);
+            out[sl] = ((uint64_t)(uint32_t)a0 << 32) | (id0 + sl);
         });
         if (!ok) atomicOr(t.err, (unsigned)OT_DEV_STENCIL);
     }
 }
 
-// One thread per sorted pair; the first pair of each leaf walks its run in order.
+// Each thread owns a chunk of RC consecutive sorted pairs and reduces every run (all pairs of
+// one parent block, markers in index order) that starts inside its chunk, reading past the
+// chunk's end to finish its last run: balanced work, no compaction of run heads.  Each run
+// accumulates its 8 children and adds each touched child to f once.
+constexpr int RC = 32;
+
 template <typename T, int K>
 __global__ void __launch_bounds__(256) k_spread_reduce(const uint64_t* __restrict__ pairs, int64_t npairs, int lmax,
                                                        const double* __restrict__ x, const double* __restrict__ y,
                                                        const double* __restrict__ z, const T* __restrict__ F,
                                                        const T* __restrict__ dV, int64_t n, T* __restrict__ f) {
-    constexpr int W = Stencil<K>::W, W3 = W * W * W;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npairs;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t pv = pairs[i];
-        const uint32_t leaf = (uint32_t)(pv >> 32);
-        if (leaf == (uint32_t)INVALID_HI) continue;
-        if (i > 0 && (uint32_t)(pairs[i - 1] >> 32) == leaf) continue;
-        T a0 = T(0), a1 = T(0), a2 = T(0);
-        for (int64_t j = i; j < npairs; ++j) {
-            const uint64_t pj = pairs[j];
-            if ((uint32_t)(pj >> 32) != leaf) break;
-            const uint32_t id = (uint32_t)pj;
-            const int64_t k = id / W3;
-            const int sl = (int)(id - (uint32_t)(k * W3));
-            const int slot[3] = {sl % W, (sl / W) % W, sl / (W * W)};
-            uint64_t X[3];
-            fixpoint3(x[k], y[k], z[k], X);  // inside: the pair was emitted
-            T wt = T(1);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) wt *= stencil_weight_1d<K, T>(lmax, X[d], slot[d]);
-            const T vol = marker_volume(dV, k, lmax);
-            a0 += F[k] * vol * wt;
-            a1 += F[n + k] * vol * wt;
-            a2 += F[2 * n + k] * vol * wt;
+    constexpr int W = Stencil<K>::W;
+    constexpr int PW = ParentSlots<K>::PW, PS = ParentSlots<K>::PS;
+    const int64_t nchunks = (npairs + RC - 1) / RC;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = c * RC;
+        const int64_t jend = min(j + RC, npairs);
+        if (j > 0) {  // the run in progress at the chunk start belongs to an earlier chunk
+            const uint32_t prev = (uint32_t)(pairs[j - 1] >> 32);
+            while (j < jend && (uint32_t)(pairs[j] >> 32) == prev) ++j;
         }
-        T* fp = f + 4 * (size_t)leaf;
-        fp[0] += a0;
-        fp[1] += a1;
-        fp[2] += a2;
+        while (j < jend) {
+            const uint32_t a0 = (uint32_t)(pairs[j] >> 32);
+            if (a0 == (uint32_t)INVALID_HI) break;  // invalid pairs sort last
+            T acc[8][3];
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) acc[ch][0] = acc[ch][1] = acc[ch][2] = T(0);
+            unsigned touched = 0;
+            for (; j < npairs; ++j) {
+                const uint64_t pj = pairs[j];
+                if ((uint32_t)(pj >> 32) != a0) break;
+                const uint32_t id = (uint32_t)pj;
+                const int64_t k = id / PS;
+                const int sl = (int)(id - (uint32_t)(k * PS));
+                uint64_t X[3];
+                fixpoint3(x[k], y[k], z[k], X);  // inside: the pair was emitted
+                int i0[3];
+                T w[3][W];
+                stencil_weights<K, T>(lmax, X, i0, w);
+                const int P[3] = {floordiv2(i0[0]) + sl % PW, floordiv2(i0[1]) + (sl / PW) % PW,
+                                  floordiv2(i0[2]) + sl / (PW * PW)};
+                const T vol = marker_volume(dV, k, lmax);
+                const T F0 = F[k] * vol, F1 = F[n + k] * vol, F2 = F[2 * n + k] * vol;
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
+                    const int ax = 2 * P[0] + (ch & 1) - i0[0];
+                    const int ay = 2 * P[1] + ((ch >> 1) & 1) - i0[1];
+                    const int az = 2 * P[2] + ((ch >> 2) & 1) - i0[2];
+                    if (ax < 0 || ay < 0 || az < 0 || ax >= W || ay >= W || az >= W) continue;
+                    const T wt = w[0][ax] * w[1][ay] * w[2][az];
+                    acc[ch][0] += F0 * wt;
+                    acc[ch][1] += F1 * wt;
+                    acc[ch][2] += F2 * wt;
+                    touched |= 1u << ch;
+                }
+            }
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) {
+                if (!((touched >> ch) & 1u)) continue;
+                T* fp = f + 4 * ((size_t)a0 + ch);
+                fp[0] += acc[ch][0];
+                fp[1] += acc[ch][1];
+                fp[2] += acc[ch][2];
+            }
+        }
     }
 }
 
@@ -149,28 +186,28 @@ int leaf_bits(int64_t n) {
     return b;
 }
 
-inline int stencil_cells(int kernel) { return kernel == OT_PESKIN4 ? 64 : 27; }
+// Pairs per marker in the sorted spreading: one per overlapping parent block slot.
+inline int stencil_cells(int kernel) { return kernel == OT_PESKIN4 ? ParentSlots<OT_PESKIN4>::PS : ParentSlots<OT_ROMA3>::PS; }
 
 template <typename T, int K>
 ot_status spread_sorted(const ot_octree* t, const double* x, const double* y, const double* z, const T* F,
                         const T* dV, int64_t n, T* f, void* ws, cudaStream_t s) {
-    constexpr int W3 = Stencil<K>::W * Stencil<K>::W * Stencil<K>::W;
-    const int64_t np = n * W3;
+    const int64_t np = n * ParentSlots<K>::PS;
     uint64_t* pairs = static_cast<uint64_t*>(ws);
     uint64_t* tmp = pairs + np;
     void* rws = tmp + np;
-    TreeView v = tree_view(t, true);
-    const size_t smem = (size_t)v.nsample * sizeof(uint64_t);
+    TreeView v = tree_view(t);
+    const size_t smem = 0;
     ot_status st;
     auto ke = k_spread_emit<K>;
     if ((st = prep(ke, smem)) != OT_OK) return st;
-    ke<<<grid_for(ke, 256, smem, n), 256, smem, s>>>(v, t->root, x, y, z, n, pairs);
+    ke<<<grid_for(ke, 256, smem, n), 256, smem, s>>>(v, x, y, z, n, pairs);
     count_launch();
     OT_CUDA(cudaGetLastError());
     const int bits = leaf_bits(t->n);
     if ((st = radix_sort_u64_ws(pairs, tmp, np, 32, 32 + bits, rws, s)) != OT_OK) return st;
     auto kr = k_spread_reduce<T, K>;
-    kr<<<grid_for(kr, 256, 0, np), 256, 0, s>>>(pairs, np, t->lmax, x, y, z, F, dV, n, f);
+    kr<<<grid_for(kr, 256, 0, (np + RC - 1) / RC), 256, 0, s>>>(pairs, np, t->lmax, x, y, z, F, dV, n, f);
     count_launch();
     OT_CUDA(cudaGetLastError());
     return OT_OK;
@@ -193,17 +230,17 @@ ot_status launch_spread(const ot_octree* t, int kernel, int mode, const double* 
         if (kernel == OT_PESKIN4) return spread_sorted<T, OT_PESKIN4>(t, x, y, z, F, dV, n, f, ws, s);
         return spread_sorted<T, OT_ROMA3>(t, x, y, z, F, dV, n, f, ws, s);
     }
-    TreeView v = tree_view(t, true);
-    const size_t smem = (size_t)v.nsample * sizeof(uint64_t);
+    TreeView v = tree_view(t);
+    const size_t smem = 0;
     ot_status st;
     if (kernel == OT_PESKIN4) {
         auto k = k_spread_atomic<T, OT_PESKIN4>;
         if ((st = prep(k, smem)) != OT_OK) return st;
-        k<<<grid_for(k, 256, smem, n), 256, smem, s>>>(v, t->root, x, y, z, F, dV, n, f);
+        k<<<grid_for(k, 256, smem, n), 256, smem, s>>>(v, x, y, z, F, dV, n, f);
     } else {
         auto k = k_spread_atomic<T, OT_ROMA3>;
         if ((st = prep(k, smem)) != OT_OK) return st;
-        k<<<grid_for(k, 256, smem, n), 256, smem, s>>>(v, t->root, x, y, z, F, dV, n, f);
+        k<<<grid_for(k, 256, smem, n), 256, smem, s>>>(v, x, y, z, F, dV, n, f);
     }
     count_launch();
     OT_CUDA(cudaGetLastError());
@@ -231,22 +268,21 @@ namespace {
 template <int K>
 ot_status sorted_noalloc(const ot_octree* t, const double* x, const double* y, const double* z, const float* F,
                          const float* dV, int64_t n, float* f, void* scratch, cudaStream_t s) {
-    constexpr int W3 = Stencil<K>::W * Stencil<K>::W * Stencil<K>::W;
-    const int64_t np = n * W3;
+    const int64_t np = n * ParentSlots<K>::PS;
     uint64_t* pairs = static_cast<uint64_t*>(scratch);
     uint64_t* tmp = pairs + np;
     void* rws = tmp + np;
-    TreeView v = tree_view(t, true);
-    const size_t smem = (size_t)v.nsample * sizeof(uint64_t);
+    TreeView v = tree_view(t);
+    const size_t smem = 0;
     ot_status st;
     auto ke = k_spread_emit<K>;
     if ((st = prep(ke, smem)) != OT_OK) return st;
-    ke<<<grid_for(ke, 256, smem, n), 256, smem, s>>>(v, t->root, x, y, z, n, pairs);
+    ke<<<grid_for(ke, 256, smem, n), 256, smem, s>>>(v, x, y, z, n, pairs);
     count_launch();
     OT_CUDA(cudaGetLastError());
     if ((st = radix_sort_u64_noalloc(pairs, tmp, np, 32, 32 + leaf_bits(t->n), rws, s)) != OT_OK) return st;
     auto kr = k_spread_reduce<float, K>;
-    kr<<<grid_for(kr, 256, 0, np), 256, 0, s>>>(pairs, np, t->lmax, x, y, z, F, dV, n, f);
+    kr<<<grid_for(kr, 256, 0, (np + RC - 1) / RC), 256, 0, s>>>(pairs, np, t->lmax, x, y, z, F, dV, n, f);
     count_launch();
     OT_CUDA(cudaGetLastError());
     return OT_OK;

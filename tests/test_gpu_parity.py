@@ -140,6 +140,30 @@ def special_points(ko, lo, rng, n_rand):
     return P
 
 
+@pytest.mark.parametrize("map_level", [0, 2, 3, 5])
+def test_level_map_levels(ot, tiny, tiny_fields, map_level):
+    """Every level of the level map gives the same hosts and values: a covered cell answers from
+    the map, any other point is searched among its cell's leaves."""
+    w, ko, lo, tree = tiny
+    t2 = ot.ot_octree_build(w.spheres, w.lmin, w.lmax)
+    ot.ot_octree_set_map_level(t2, map_level)
+    P = special_points(ko, lo, np.random.default_rng(77), 4000)
+    h = ot.ot_locate(t2, *pts(P.T))
+    assert np.array_equal(h.cpu().numpy(), oracle.locate_ub(ko, lo, *P.T))
+    f32 = tiny_fields["sin"].astype(np.float32)
+    Pi = P[:-6]
+    u = ot.ot_interpolate(t2, ot.OT_TRILINEAR, *pts(Pi.T), dev(f32)).cpu().numpy()
+    href = oracle.locate_ub(ko, lo, *Pi.T)
+    ref = oracle.interp_trilinear(ko, lo, f32.astype(np.float64), *Pi.T, href)
+    assert rel_err(u, ref) <= TOL32
+    um = ot.ot_interpolate(t2, 2, *pts(w.markers), dev(f32)).cpu().numpy()
+    refm, _ = oracle.interp_delta(ko, lo, w.lmax, 2, f32.astype(np.float64), *w.markers)
+    assert rel_err(um, refm) <= TOL32
+    ot.ot_index_train(t2, root=ot.OT_ROOT_MLP, n_leaf_models=512, n_mid_models=32, epochs=1, batch=4096)
+    hl = ot.ot_locate(t2, *pts(P.T), search=ot.OT_LEARNED)
+    assert np.array_equal(hl.cpu().numpy(), h.cpu().numpy())
+
+
 @pytest.mark.parametrize("n", [0, 1, 31, 33, 1007])
 def test_locate_binary_ragged(ot, tiny, n):
     w, ko, lo, tree = tiny
