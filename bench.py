@@ -43,8 +43,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="many_bubbles",
-                   choices=["many_bubbles", "single_bubble", "learned_index", "tiny"])
-    p.add_argument("--search", default="learned", choices=["learned", "binary"])
+                   choices=["many_bubbles", "single_bubble", "learned_index", "tiny", "tracking"])
+    p.add_argument("--search", default="auto", choices=["auto", "learned", "binary"],
+                   help="form timed for `value`; auto = the faster of the two (both are reported)")
     p.add_argument("--index", default="mlp3", choices=["mlp3", "mlp2", "linear2"],
                    help="mlp3: MLP root -> 4096 mid -> 2^18 leaf models; mlp2: MLP root -> 4096 leaf models")
     p.add_argument("--spread", default="sorted", choices=["sorted", "atomic"])
@@ -302,10 +303,12 @@ def run_ours(args):
         b, t, s = [int(v) for v in args.launch.split(",")]
         launch = dict(block=b, tile=t, blocks_per_sm=s)
     groups = [dict(kernel=ot.OT_PESKIN4, x=mx, y=my, z=mz, u=um), dict(kernel=ot.OT_TRILINEAR, x=px, y=py, z=pz, u=up)]
-    batch = ot.ot_batch_create(tree, groups, field, search=search, launch=launch)
+    # both search forms over the same groups: the learned index and the plain binary search
+    batches = {"learned": ot.ot_batch_create(tree, groups, field, search=ot.OT_LEARNED, launch=launch),
+               "plain": ot.ot_batch_create(tree, groups, field, search=ot.OT_BINARY, launch=launch)}
     stream = torch.cuda.current_stream()
 
-    def step(ev=None):
+    def step(batch, ev=None):
         if ev:
             ev[0].record(stream)
         ot.ot_batch_run(batch)
@@ -316,12 +319,30 @@ def run_ours(args):
         if ev:
             ev[2].record(stream)
 
-    for _ in range(max(3, args.warmup)):
-        step()
+    def time_steps(batch, k):
+        evs_ = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(k)]
+        for e in evs_:
+            step(batch, e)
+        torch.cuda.synchronize()
+        li = statistics.mean(e[0].elapsed_time(e[1]) for e in evs_)
+        sp = statistics.mean(e[1].elapsed_time(e[2]) for e in evs_)
+        return {"step_ms": statistics.mean(e[0].elapsed_time(e[2]) for e in evs_), "locate_interpolate_ms": li,
+                "spread_ms": sp}
+
+    for b in batches.values():
+        for _ in range(max(3, args.warmup)):
+            step(b)
     torch.cuda.synchronize()
     assert ot.ot_last_error(tree) & (ot.OT_DEV_STENCIL | ot.OT_DEV_OUTSIDE | ot.OT_DEV_REFINED_CAP) == 0
+    if args.search == "auto":
+        cal = {k: time_steps(b, 3)["step_ms"] for k, b in batches.items()}
+        chosen = min(cal, key=cal.get)
+    else:
+        chosen = "learned" if args.search == "learned" else "plain"
+    other = "plain" if chosen == "learned" else "learned"
+    ot.ot_index_get_stats(tree, reset=True)
 
-    # timed region
+    # timed region: the chosen form
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     clocks = Clocks(local) if rank == 0 else None
     barrier()
@@ -331,7 +352,7 @@ def run_ours(args):
     torch.cuda.nvtx.range_push("timed")
     start.record(stream)
     for k in range(args.steps):
-        step(evs[k])
+        step(batches[chosen], evs[k])
     stop.record(stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
@@ -343,32 +364,24 @@ def run_ours(args):
     batch_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     spread_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
     value = job_value(npts, world, ms_step)
-    fb = ot.ot_index_get_stats(tree, reset=True)["fallbacks"]
+    fb = ot.ot_index_get_stats(tree, reset=True)["fallbacks"] if chosen == "learned" else None
 
-    # plain binary search, same batch shape (learned vs plain)
-    plain = None
-    if search == ot.OT_LEARNED:
-        bplain = ot.ot_batch_create(tree, groups, field, search=ot.OT_BINARY, launch=launch)
-        for _ in range(3):
-            ot.ot_batch_run(bplain)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.steps):
-            ot.ot_batch_run(bplain)
-        b.record(stream)
-        torch.cuda.synchronize()
-        plain_batch_ms = a.elapsed_time(b) / args.steps
-        plain = {"batch_ms": plain_batch_ms, "points_per_s_locate_interp": npts / (plain_batch_ms / 1e3),
-                 "step_points_per_s": npts / ((plain_batch_ms + spread_ms) / 1e3)}
-        del bplain
+    # the other form, same steps (learned vs plain)
+    forms = {chosen: {"step_ms": ms_step, "locate_interpolate_ms": batch_ms, "spread_ms": spread_ms},
+             other: time_steps(batches[other], args.steps)}
+    for v_ in forms.values():
+        v_["points_per_s"] = npts / (v_["step_ms"] / 1e3)
+        v_["locate_interpolate_points_per_s"] = npts / (v_["locate_interpolate_ms"] / 1e3)
+    learned_vs_plain = {
+        "locate_interpolate": forms["plain"]["locate_interpolate_ms"] / forms["learned"]["locate_interpolate_ms"],
+        "step": forms["plain"]["step_ms"] / forms["learned"]["step_ms"]}
+    search = ot.OT_LEARNED if chosen == "learned" else ot.OT_BINARY
+    batch = batches[chosen]
 
     # per-group timing (markers only, particles only), learned and plain
     groups_t = {}
     for gname, gsel in (("markers", groups[:1]), ("particles", groups[1:])):
         for sname, sv in (("learned", ot.OT_LEARNED), ("binary", ot.OT_BINARY)):
-            if sv == ot.OT_LEARNED and search != ot.OT_LEARNED:
-                continue
             bb = ot.ot_batch_create(tree, gsel, field, search=sv, launch=launch)
             for _ in range(2):
                 ot.ot_batch_run(bb)
@@ -396,7 +409,7 @@ def run_ours(args):
             for d in range(3):
                 (mx, my, mz)[d].copy_(hm[d], non_blocking=True)
                 (px, py, pz)[d].copy_(hp[d], non_blocking=True)
-            step()
+            step(batches[chosen])
             hum.copy_(um, non_blocking=True)
             hup.copy_(up, non_blocking=True)
             hf.copy_(f, non_blocking=True)
@@ -459,13 +472,13 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": describe(w, n_leaves, INDEX_DESC[args.index] if args.search == "learned" else "binary"),
+           "config": describe(w, n_leaves, INDEX_DESC[args.index] if chosen == "learned" else
+                              "plain: level map + binary search"),
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": int(launches), "clocks": clk,
            "breakdown_ms": {"locate_interpolate": batch_ms, "spread": spread_ms, "step": ms_step},
            "locate_interpolate_points_per_s": world * npts / (batch_ms / 1e3),
-           "plain": plain, "groups_ms": groups_t,
-           "learned_speedup_locate_interp": (plain["batch_ms"] / batch_ms) if plain else None,
+           "forms": forms, "learned_vs_plain": learned_vs_plain, "groups_ms": groups_t,
            "index": {"n_mid": n_mid, "n_leaf": n_leaf, "mean_window": istats["mean_window"], "max_window": istats["max_window"],
                      "empty_models": istats["empty_models"], "fallbacks_timed": fb,
                      "final_loss": istats["final_loss"], "train_s": train_s},
@@ -477,10 +490,56 @@ def run_ours(args):
     return 0
 
 
+def run_tracking(args):
+    """The time-stepped workload: 256 bubbles moving, 200M particles advected by AB2, markers
+    spread every step, octree rebuilt and index retrained every 10 steps (all timed)."""
+    import torch
+    import paper_2605_20565_gb300 as ot
+    from paper_2605_20565_gb300 import _build, synth, tracking
+    torch.cuda.set_device(0)
+    _build.build()
+    w = synth.tracking(n_particles=int(200_000_000 * args.scale))
+    search = ot.OT_BINARY if args.search == "binary" else ot.OT_LEARNED
+    t0 = time.time()
+    tr = tracking.Tracker(w, search=search, rebuild_every=10)
+    setup_s = time.time() - t0
+    n_leaves = ot.ot_octree_info(tr.tree)[0]
+    for _ in range(args.warmup):
+        tr.step()
+    torch.cuda.synchronize()
+    tr.timings = {"rebuild_s": 0.0, "rebuilds": 0}
+    clocks = Clocks(0)
+    launches0 = ot.ot_launch_count()
+    t0 = time.perf_counter()
+    pts = 0
+    for _ in range(args.steps):
+        pts += tr.step()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    clk = clocks.stop()
+    out = {"metric": METRIC, "value": pts / el, "unit": "points/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "bubbles": int(w.spheres.shape[0]), "levels": [w.lmin, w.lmax],
+                      "leaves": int(n_leaves), "markers_peskin4": int(w.markers.shape[1]),
+                      "particles_trilinear": int(w.particles.shape[1]), "search": args.search,
+                      "step": "locate+interpolate all points, AB2 advect particles, sorted spread of markers; "
+                              "octree rebuild + index retrain + field resample every 10 steps",
+                      "l2": "inputs larger than L2; no flush"},
+           "rebuild": {"rebuilds_timed": tr.timings["rebuilds"], "rebuild_s_timed": tr.timings["rebuild_s"],
+                       "setup_s": setup_s},
+           "gpu_launches": int(ot.ot_launch_count() - launches0), "clocks": clk,
+           "roofline": None, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "tracking":
+        return run_tracking(args)
     return run_ours(args)
 
 

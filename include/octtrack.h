@@ -275,11 +275,12 @@ ot_status ot_batch_destroy(ot_batch* b);
  * Point-particle advection (Sec. 2.3.2, Eq. PointParticle, gravity off): per particle
  *   a = f_p (u - v)/tau, f_p = 1 + 0.15 (re_coef |u - v|)^0.687 (re_coef = 0: f_p = 1),
  *   v += dt (3/2 a - 1/2 a_prev), x += dt (3/2 v_old - 1/2 v_prev); Euler when first != 0.
+ * periodic != 0 wraps the new positions into [0, 1) per axis (x - floor(x)).
  * d_x: 3 planes of n doubles (positions, FP64); d_v, d_a_prev, d_v_prev: 3 planes of n
  * floats; d_u: 3 planes of n floats (interpolated fluid velocity).
  * -------------------------------------------------------------------------------------*/
 ot_status ot_advect_ab2(double* d_x, float* d_v, float* d_a_prev, float* d_v_prev, const float* d_u, int64_t n,
-                        float tau, float re_coef, float dt, int first, void* stream);
+                        float tau, float re_coef, float dt, int first, int periodic, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Diagnostics

@@ -65,7 +65,7 @@ def _L():
                 "or_interp_trilinear": (None, [P, P, i64, P, P, P, P, P, i64, P]),
                 "or_mlp_forward1": (dbl, [P, dbl]),
                 "or_mlp_loss_grad": (dbl, [P, P, P, i64, P]),
-                "or_advect_ab2": (None, [P, P, P, P, P, i64, dbl, dbl, dbl, i32]),
+                "or_advect_ab2": (None, [P, P, P, P, P, i64, dbl, dbl, dbl, i32, i32]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -223,12 +223,12 @@ def mlp_loss_grad(params, xin, tgt):
 
 # --- Point-particle advection (Sec. 2.3.2) ----------------------------------------------
 
-def advect_ab2(state: dict, u, tau: float, re_coef: float, dt: float, first: bool):
+def advect_ab2(state: dict, u, tau: float, re_coef: float, dt: float, first: bool, periodic: bool = False):
     """Advance state {'x','v','a_prev','v_prev'} (each (3, n) float64, in place) one step."""
     u = _c(u, np.float64).reshape(3, -1)
     for key in ("x", "v", "a_prev", "v_prev"):
         a = state[key]
         assert a.dtype == np.float64 and a.flags.c_contiguous
     _L().or_advect_ab2(_p(state["x"]), _p(state["v"]), _p(state["a_prev"]), _p(state["v_prev"]), _p(u),
-                       u.shape[1], tau, re_coef, dt, int(first))
+                       u.shape[1], tau, re_coef, dt, int(first), int(periodic))
     return state

@@ -627,12 +627,12 @@ double or_mlp_loss_grad(const double *prm, const double *xin, const double *tgt,
 /*   a = f_p (u(x_p) - v) / tau,  f_p = 1 + 0.15 Re_p^0.687,  Re_p = re_coef |u - v|       */
 /*   (re_coef = 2 r_p / nu; re_coef = 0 gives Stokes drag, f_p = 1),                        */
 /*   v_{n+1} = v_n + dt (3/2 a_n - 1/2 a_{n-1}),  x_{n+1} = x_n + dt (3/2 v_n - 1/2 v_{n-1}); */
-/*   the first step (no history) is explicit Euler.                                        */
+/*   the first step (no history) is explicit Euler; periodic != 0 wraps positions into [0,1). */
 /* State planes of np each: x[3], v[3], a_prev[3], v_prev[3]; u: 3 planes.                  */
 /* ------------------------------------------------------------------------------------ */
 
 void or_advect_ab2(double *x, double *v, double *a_prev, double *v_prev, const double *u, int64_t np,
-                   double tau, double re_coef, double dt, int first) {
+                   double tau, double re_coef, double dt, int first, int periodic) {
 #pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < np; ++p) {
         double rel[3], mag2 = 0.0;
@@ -648,7 +648,12 @@ void or_advect_ab2(double *x, double *v, double *a_prev, double *v_prev, const d
             double am = first ? an : a_prev[d * np + p];
             double vm = first ? vn : v_prev[d * np + p];
             v[d * np + p] = vn + dt * (1.5 * an - 0.5 * am);
-            x[d * np + p] = x[d * np + p] + dt * (1.5 * vn - 0.5 * vm);
+            double xn = x[d * np + p] + dt * (1.5 * vn - 0.5 * vm);
+            if (periodic) { /* wrap into [0, 1) */
+                xn = xn - floor(xn);
+                if (xn >= 1.0) xn = 0.0;
+            }
+            x[d * np + p] = xn;
             a_prev[d * np + p] = an;
             v_prev[d * np + p] = vn;
         }

@@ -106,7 +106,7 @@ def _L():
                 "ot_batch_create": (st, [P, P, i32, P, i32, P, P, P]),
                 "ot_batch_run": (st, [P, P]),
                 "ot_batch_destroy": (st, [P]),
-                "ot_advect_ab2": (st, [P, P, P, P, P, i64, C.c_float, C.c_float, C.c_float, i32, P]),
+                "ot_advect_ab2": (st, [P, P, P, P, P, i64, C.c_float, C.c_float, C.c_float, i32, i32, P]),
                 "ot_last_error": (st, [P, P, i32, P]),
             }
             for name, (res, args) in sigs.items():
@@ -377,13 +377,15 @@ def ot_batch_destroy(batch: Batch):
 
 # --- advection / diagnostics ----------------------------------------------------------------
 
-def ot_advect_ab2(x, v, a_prev, v_prev, u, tau: float, re_coef: float, dt: float, first: bool, stream=None):
+def ot_advect_ab2(x, v, a_prev, v_prev, u, tau: float, re_coef: float, dt: float, first: bool,
+                  periodic: bool = False, stream=None):
     """x: (3, n) float64; v, a_prev, v_prev, u: (3, n) float32 (updated in place)."""
     torch = _torch()
     n = x.shape[1]
     _check(_L().ot_advect_ab2(_dptr(x, torch.float64, "x"), _dptr(v, torch.float32, "v"),
                               _dptr(a_prev, torch.float32, "a_prev"), _dptr(v_prev, torch.float32, "v_prev"),
-                              _dptr(u, torch.float32, "u"), n, tau, re_coef, dt, int(first), _stream(stream)))
+                              _dptr(u, torch.float32, "u"), n, tau, re_coef, dt, int(first), int(periodic),
+                              _stream(stream)))
 
 
 def ot_last_error(tree: Octree, clear: bool = True, stream=None) -> int:

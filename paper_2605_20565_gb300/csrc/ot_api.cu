@@ -22,7 +22,7 @@ ot_status check_points(const ot_octree* t, const void* x, const void* y, const v
 // AB2 step of point-particle velocity and position, FP32 state, FP64 positions.
 __global__ void k_advect(double* __restrict__ x, float* __restrict__ v, float* __restrict__ ap,
                          float* __restrict__ vp, const float* __restrict__ u, int64_t n, float tau, float re_coef,
-                         float dt, int first) {
+                         float dt, int first, int periodic) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float rel[3], mag2 = 0.0f;
 #pragma unroll
@@ -39,7 +39,12 @@ __global__ void k_advect(double* __restrict__ x, float* __restrict__ v, float* _
             const float am = first ? an : ap[d * n + i];
             const float vm = first ? vn : vp[d * n + i];
             v[d * n + i] = vn + dt * (1.5f * an - 0.5f * am);
-            x[d * n + i] = x[d * n + i] + (double)dt * (1.5 * (double)vn - 0.5 * (double)vm);
+            double xn = x[d * n + i] + (double)dt * (1.5 * (double)vn - 0.5 * (double)vm);
+            if (periodic) {
+                xn -= floor(xn);
+                if (xn >= 1.0) xn = 0.0;  // -tiny - floor(-tiny) rounds to 1
+            }
+            x[d * n + i] = xn;
             ap[d * n + i] = an;
             vp[d * n + i] = vn;
         }
@@ -277,11 +282,11 @@ ot_status ot_spread_f64(const ot_octree* t, int kernel, int mode, const double* 
 }
 
 ot_status ot_advect_ab2(double* x, float* v, float* ap, float* vp, const float* u, int64_t n, float tau, float re_coef,
-                        float dt, int first, void* stream) {
+                        float dt, int first, int periodic, void* stream) {
     if (n < 0 || (n > 0 && (!x || !v || !ap || !vp || !u)) || !(tau > 0.0f) || !(re_coef >= 0.0f)) return OT_ERR_ARG;
     if (n == 0) return OT_OK;
     const int64_t g = std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
-    k_advect<<<(unsigned)g, 256, 0, (cudaStream_t)stream>>>(x, v, ap, vp, u, n, tau, re_coef, dt, first);
+    k_advect<<<(unsigned)g, 256, 0, (cudaStream_t)stream>>>(x, v, ap, vp, u, n, tau, re_coef, dt, first, periodic);
     count_launch();
     OT_CUDA(cudaGetLastError());
     return OT_OK;

@@ -90,10 +90,11 @@ def largest_remainder(total: int, weights) -> np.ndarray:
     return base
 
 
-def place_bubbles(seed: int, n: int, dmin: float, dmax: float, wall: str = "d", max_tries: int = 200000):
+def place_bubbles(seed: int, n: int, dmin: float, dmax: float, wall: str = "d", max_tries: int = 200000,
+                  extra_margin: float = 0.0):
     """n non-overlapping bubbles, diameters log-uniform in [dmin, dmax], centres at least one
-    diameter from every wall (``wall='d'``) and |c_i - c_j| >= r_i + r_j.  Rejection
-    sampling on one counter stream; returns centres (n, 3) and diameters (n,)."""
+    diameter (plus ``extra_margin``) from every wall (``wall='d'``) and |c_i - c_j| >= r_i + r_j.
+    Rejection sampling on one counter stream; returns centres (n, 3) and diameters (n,)."""
     cs, ds = [], []
     t = 0
     while len(cs) < n:
@@ -102,7 +103,7 @@ def place_bubbles(seed: int, n: int, dmin: float, dmax: float, wall: str = "d", 
         u = uniform(seed, 10, 4, offset=4 * t)
         t += 1
         d = dmin * (dmax / dmin) ** u[0]
-        m = d if wall == "d" else 0.0
+        m = (d + extra_margin) if wall == "d" else 0.0
         c = m + (1.0 - 2.0 * m) * u[1:4]
         ok = all(np.linalg.norm(c - c2) >= 0.5 * (d + d2) for c2, d2 in zip(cs, ds))
         if ok:
@@ -275,10 +276,10 @@ def single_bubble(seed: int = 1, n_markers: int = 50_000, n_particles: int = 10_
 
 
 # Shell half-width as a multiple of the bubble diameter, chosen so that the leaf counts of
-# the many-bubble workloads land near the stated sizes (the literal two-diameter shell
-# gives about 10^8 leaves at level 10).
+# the many-bubble workloads land near the stated sizes: ~30M leaves for 64 bubbles at level
+# 10 (the literal two-diameter shell gives about 10^8) and ~80M for 256 bubbles at level 11.
 MANY_BUBBLE_SHELL = 0.25
-TRACKING_SHELL = 0.25
+TRACKING_SHELL = 0.06
 
 
 def many_bubbles(seed: int = 2, n_markers: int = 2_000_000, n_particles: int = 50_000_000,
@@ -320,11 +321,13 @@ def learned_index(seed: int = 3, n_particles: int = 100_000_000, n_markers: int 
 
 def tracking(seed: int = 4, n_particles: int = 200_000_000, shell: float = TRACKING_SHELL,
              lmin: int = 4, lmax: int = 11, n_bubbles: int = 256) -> Workload:
-    """256 bubbles, d log-uniform in [0.01, 0.08], levels 4-11; markers per bubble
-    round(pi (d/h)^2) at h = 2^-lmax; uniform particles; bubble velocities in extra."""
-    cs, ds = place_bubbles(seed, n_bubbles, 0.01, 0.08)
-    sph = np.column_stack([cs, 0.5 * ds, shell * ds])
+    """256 bubbles, d log-uniform in [0.01, 0.08], levels 4-11, shell max(0.06 d, 4 h); markers
+    per bubble round(pi (d/h)^2) at h = 2^-lmax; uniform particles; bubble velocities in extra."""
     h = 2.0 ** -lmax
+    cs, ds = place_bubbles(seed, n_bubbles, 0.01, 0.08, extra_margin=4.0 * h)  # stencils stay inside
+    # at least 4 finest cells: the 4-point stencil of every marker (reach ~2.6 h) stays on the
+    # finest level while the bubbles move between re-adaptations
+    sph = np.column_stack([cs, 0.5 * ds, np.maximum(shell * ds, 4.0 * h)])
     counts = np.round(np.pi * (ds / h) ** 2).astype(np.int64)
     pos, nrm, grp = _markers_on(cs, ds, counts, seed)
     vel = 0.05 * normal(seed, 8, 3 * n_bubbles).reshape(n_bubbles, 3)

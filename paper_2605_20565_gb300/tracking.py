@@ -1,0 +1,127 @@
+"""Time-stepped tracking of point particles among moving bubbles (Sec. 2.3.2 particle
+update; Sec. 2.4 re-adaptation; Algorithm 2's post-refinement re-location on one GPU).
+
+Every step, through the C ABI:
+  1. one batched launch locates and interpolates every IBM marker (Peskin-4) and every point
+     particle (trilinear) -- ``ot_batch_run``;
+  2. the particles advance by AB2 with Schiller-Naumann drag (``ot_advect_ab2``, periodic
+     wrap into the unit cube);
+  3. the marker forces are spread back to the cells by the deterministic sorted reduction
+     (``ot_spread``);
+  4. the bubbles translate at constant velocities carrying their markers.
+Every ``rebuild_every`` steps the octree is rebuilt around the moved bubbles
+(``ot_octree_build``), the learned index is retrained on the device (``ot_index_train``), the
+velocity field is re-sampled at the new leaf centres, and the batch graph is re-captured:
+the single-GPU form of re-locating every point after a mesh change.
+
+The time step keeps particle motion below one finest cell per step: dt = h_lmax / max|u|.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import synth
+
+
+class Tracker:
+    def __init__(self, w: synth.Workload, search: int = 1, rebuild_every: int = 10, tau_steps: float = 10.0,
+                 re_coef: float = 0.0, n_leaf_models: int = 1 << 18, n_mid_models: int = 4096, device=None):
+        import torch
+        from . import OT_PESKIN4, OT_SORTED, OT_TRILINEAR
+        self.torch = torch
+        self.w = w
+        self.dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.search = search
+        self.rebuild_every = rebuild_every
+        self.re_coef = re_coef
+        self.n_leaf_models = n_leaf_models
+        self.n_mid_models = n_mid_models
+        self.centres0 = np.asarray(w.extra["centres"], np.float64)
+        self.vel = np.asarray(w.extra["velocities"], np.float64)
+        self.radii = 0.5 * np.asarray(w.extra["diameters"], np.float64)
+        self.shells = w.spheres[:, 4].copy()
+        self.t = 0.0
+        self.step_no = 0
+        T = torch
+        dev = self.dev
+        self.x = T.as_tensor(np.ascontiguousarray(w.particles), device=dev)            # (3, n) FP64
+        n = self.x.shape[1]
+        self.v = T.zeros((3, n), dtype=T.float32, device=dev)
+        self.a_prev = T.zeros_like(self.v)
+        self.v_prev = T.zeros_like(self.v)
+        self.u = T.empty_like(self.v)
+        # markers: offsets from their bubble centre (moved rigidly), forces = outward normals
+        self.m_grp = T.as_tensor(w.marker_group.astype(np.int64), device=dev)
+        self.m_off = T.as_tensor(w.markers - self.centres0[w.marker_group].T, device=dev)
+        self.mx = T.empty((3, w.markers.shape[1]), dtype=T.float64, device=dev)
+        self.F = T.as_tensor(np.ascontiguousarray(w.forces, dtype=np.float32), device=dev)
+        self.um = T.empty((3, w.markers.shape[1]), dtype=T.float32, device=dev)
+        self._place_markers()
+        self.h = 2.0 ** -w.lmax
+        self.kinds = (OT_PESKIN4, OT_SORTED, OT_TRILINEAR)
+        self.ws = T.empty(1, dtype=T.uint8, device=dev)  # sized at the first rebuild
+        self.timings = {"rebuild_s": 0.0, "rebuilds": 0}
+        self._rebuild()
+        umax = float(self.field[:, :3].abs().max())
+        self.dt = self.h / max(umax, 1e-12)
+        self.tau = tau_steps * self.dt
+
+    def spheres_now(self) -> np.ndarray:
+        c = self.centres0 + self.vel * self.t
+        return np.column_stack([c, self.radii, self.shells])
+
+    def _place_markers(self):
+        c = self.torch.as_tensor(self.centres0 + self.vel * self.t, device=self.dev)  # (B, 3)
+        self.mx.copy_(c[self.m_grp].T + self.m_off)
+
+    def _rebuild(self):
+        import paper_2605_20565_gb300 as ot
+        T = self.torch
+        t0 = time.time()
+        w = self.w
+        self.tree = ot.ot_octree_build(self.spheres_now(), w.lmin, w.lmax)
+        ot.ot_index_train(self.tree, root=ot.OT_ROOT_MLP, n_leaf_models=self.n_leaf_models,
+                          n_mid_models=self.n_mid_models, epochs=2, batch=65536, lr=1e-3, seed=self.step_no)
+        n_leaves = ot.ot_octree_info(self.tree)[0]
+        cen = ot.ot_octree_centres(self.tree)
+        self.field = synth.fourier_field(w.modes, cen.T.contiguous()).to(T.float32).contiguous()
+        del cen
+        self.f = T.zeros((n_leaves, 4), dtype=T.float32, device=self.dev)
+        mx, my, mz = self.mx[0], self.mx[1], self.mx[2]
+        px, py, pz = self.x[0], self.x[1], self.x[2]
+        K_P4, _, K_TRI = self.kinds
+        self.batch = ot.ot_batch_create(self.tree, [dict(kernel=K_P4, x=mx, y=my, z=mz, u=self.um),
+                                                    dict(kernel=K_TRI, x=px, y=py, z=pz, u=self.u)],
+                                        self.field, search=self.search)
+        need = ot.ot_spread_workspace_size(self.tree, K_P4, self.mx.shape[1])
+        if self.ws.numel() < need:
+            self.ws = T.empty(need, dtype=T.uint8, device=self.dev)
+        T.cuda.synchronize()
+        self.timings["rebuild_s"] += time.time() - t0
+        self.timings["rebuilds"] += 1
+
+    def step(self):
+        """One coupled step; returns the number of points located and interpolated."""
+        import paper_2605_20565_gb300 as ot
+        K_P4, K_SORTED, _ = self.kinds
+        ot.ot_batch_run(self.batch)
+        ot.ot_advect_ab2(self.x, self.v, self.a_prev, self.v_prev, self.u, self.tau, self.re_coef, self.dt,
+                         first=self.step_no == 0, periodic=True)
+        self.f.zero_()
+        ot.ot_spread(self.tree, K_P4, K_SORTED, self.mx[0], self.mx[1], self.mx[2], self.F, self.f, workspace=self.ws)
+        self.step_no += 1
+        self.t += self.dt
+        self._place_markers()
+        if self.step_no % self.rebuild_every == 0:
+            self._rebuild()
+        return self.x.shape[1] + self.mx.shape[1]
+
+
+def scaled_tracking(n_particles: int, n_bubbles: int = 256, lmax: int = 11, seed: int = 4) -> synth.Workload:
+    """The tracking workload with a chosen particle count (the full size is 200M)."""
+    return synth.tracking(seed=seed, n_particles=n_particles, lmax=lmax, n_bubbles=n_bubbles)
+
+
+__all__ = ["Tracker", "scaled_tracking"]
