@@ -64,7 +64,7 @@ enum {
     OT_DEV_OUTSIDE = 1u,     /* a point outside [0,1)^3 or NaN (host = -1)                   */
     OT_DEV_STENCIL = 2u,     /* a delta-kernel stencil cell outside the domain or not a leaf
                                 of the finest level: its weight was dropped                */
-    OT_DEV_REFINED_CAP = 4u, /* a refined level-mate held more leaves than the averaging cap */
+    OT_DEV_REFINED_CAP = 4u, /* reserved (never set: refined level-mates have no leaf cap)  */
     OT_DEV_WINDOW = 8u       /* a learned prediction missed; plain search answered instead  */
 };
 
@@ -72,7 +72,6 @@ enum {
 #define OT_MAX_LEAVES 2000000000LL /* leaf indices are int32 */
 #define OT_MAX_SPHERES 4096
 #define OT_MAX_LEVEL 20            /* lmax; keys need 3*lmax <= 63 bits and one spare level  */
-#define OT_REFINED_CAP 4096        /* leaves averaged for one refined level-mate (trilinear) */
 
 /* A refinement sphere: cells whose closed box lies within `shell` of the sphere surface
  * |p - c| = r are refined (Sec. 3.1 refinement; Sec. 3.3 auxiliary IBM forest). */
@@ -186,6 +185,9 @@ ot_status ot_locate(const ot_octree* t, const double* d_x, const double* d_y, co
  *     c + {0, s_d} per axis where s_d = sign of the offset from the host centre; a
  *     level-mate inside a coarser leaf takes that leaf's value, a refined one the
  *     volume-weighted mean of its leaves, one outside the cube the host's index on that axis.
+ *     The refined means come from a pyramid of cell means over levels 0 .. L = min(lmax, 7),
+ *     rebuilt by each call (stream-ordered scratch of 32 * (8^(L+1) - 1) / 7 bytes, 19 MB
+ *     at L = 7); refined level-mates of deeper levels sum their few leaves directly.
  *   OT_PESKIN4 / OT_ROMA3 (Sec. 2.2, Eq. ibm_interpolate): u(X) = sum over the 4^3 / 3^3
  *     finest-level cells around X of phi(rx) phi(ry) phi(rz) u(cell); Peskin's 4-point or
  *     the paper's 3-point function.  Cells outside the cube or not finest-level leaves are
@@ -265,7 +267,11 @@ typedef struct {
 } ot_launch;
 
 /* Create a batch over groups (copied) reading d_field (float4 per leaf).  search selects
- * the host-cell search.  launch may be NULL.  Captures the graph on `stream`. */
+ * the host-cell search.  launch may be NULL.  Captures the graph on `stream`.  The graph
+ * holds the octree's device pointers: the octree must outlive the batch, and a batch made
+ * before ot_octree_set_map_level or ot_index_train on the same octree must be recreated.
+ * A replay recomputes the pyramid of cell means of d_field (when some group is trilinear)
+ * and then runs the batch kernel, so the field may change between replays. */
 ot_status ot_batch_create(const ot_octree* t, const ot_group* groups, int n_groups, const float* d_field,
                           int search, const ot_launch* launch, void* stream, ot_batch** out);
 ot_status ot_batch_run(ot_batch* b, void* stream);

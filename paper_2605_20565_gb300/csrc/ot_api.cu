@@ -191,7 +191,8 @@ ot_status ot_octree_destroy(ot_octree* t) {
     if (!t) return OT_OK;
     if (t->d_key) cudaFree(t->d_key);
     if (t->d_level) cudaFree(t->d_level);
-    if (t->d_lmap) cudaFree(t->d_lmap);
+    if (t->d_lmap && t->d_lmap != t->d_pmap) cudaFree(t->d_lmap);
+    if (t->d_pmap) cudaFree(t->d_pmap);
     if (t->d_models) cudaFree(t->d_models);
     if (t->d_mids) cudaFree(t->d_mids);
     if (t->d_root) cudaFree(t->d_root);

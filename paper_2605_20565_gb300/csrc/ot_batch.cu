@@ -1,8 +1,8 @@
 // ot_batch.cu -- one persistent launch over every group of points (IBM markers with a delta
 // kernel, point particles with trilinear interpolation), replayed from a CUDA graph.
 //
-// A graph replay first recomputes the prefix of the volume-weighted field (refined trilinear
-// level-mates read it), then runs the batch kernel.  Work is cut into tiles of 32 * tile points; warps take tiles from a global counter, the
+// A graph replay first recomputes the pyramid of cell means of the field (refined trilinear
+// level-mates read it; pyr_level + 1 small launches), then runs the batch kernel.  Work is cut into tiles of 32 * tile points; warps take tiles from a global counter, the
 // expensive marker groups first (their tiles come first in the tile space), so uneven groups
 // balance across the SMs without a host round trip.  The counter is reset by a memset node
 // captured in the same graph.
@@ -11,6 +11,7 @@
 
 #include "ot_internal.h"
 #include "ot_points.cuh"
+#include "ot_queue.cuh"
 
 struct ot_batch {
     const ot_octree* tree = nullptr;
@@ -18,7 +19,7 @@ struct ot_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned* d_counter = nullptr;
-    void* d_prefix = nullptr;  // volume-weighted field prefix, recomputed at every replay
+    float* d_pyr = nullptr;    // pyramid of cell means, recomputed at every replay
     int kernels = 1;           // kernels in one replay of the graph
 };
 
@@ -44,7 +45,11 @@ struct BatchArgs {
 
 template <bool LEARNED>
 __global__ void __launch_bounds__(256) k_batch(TreeView t, BatchArgs a, const float* __restrict__ field,
-                                               const double4* __restrict__ P, unsigned* __restrict__ counter) {
+                                               const float* __restrict__ pyr, unsigned* __restrict__ counter) {
+    __shared__ WarpQueue s_queue[256 / 32];
+    __shared__ RootModel s_root;
+    WarpQueue& wq = s_queue[threadIdx.x >> 5];
+    stage_root<LEARNED>(t, s_root);
     const int lane = threadIdx.x & 31;
     const int64_t tile_pts = 32 * (int64_t)a.tile;
     for (;;) {
@@ -64,7 +69,7 @@ __global__ void __launch_bounds__(256) k_batch(TreeView t, BatchArgs a, const fl
             int h;
             const double x = active ? gr.x[i] : 0.0, y = active ? gr.y[i] : 0.0, z = active ? gr.z[i] : 0.0;
             if (gr.kernel == OT_TRILINEAR)
-                h = trilinear_point<float, LEARNED>(t, field, P, active, x, y, z, -1, o);
+                h = trilinear_queued<float, LEARNED>(t, s_root, field, pyr, wq, active, x, y, z, -1, o);
             else if (!active)
                 h = -1;
             else if (gr.kernel == OT_PESKIN4)
@@ -129,8 +134,8 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned))) != cudaSuccess) return fail(e);
     bool has_tri = false;
     for (int k = 0; k < n_groups; ++k) has_tri = has_tri || groups[k].kernel == OT_TRILINEAR;
-    if (has_tri && (e = cudaMalloc(&b->d_prefix, prefix_bytes(t->n))) != cudaSuccess) return fail(e);
-    b->kernels = has_tri ? 4 : 1;
+    if (has_tri && (e = cudaMalloc(&b->d_pyr, pyramid_bytes(t))) != cudaSuccess) return fail(e);
+    b->kernels = has_tri ? 2 + t->pyr_level : 1;
     TreeView v = tree_view(t);
     const size_t smem = 0;
     void* kfn = search == OT_LEARNED ? (void*)k_batch<true> : (void*)k_batch<false>;
@@ -146,15 +151,14 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e);
     cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), cs);
-    if (has_tri && launch_prefix<float>(t, d_field, b->d_prefix, cs) != OT_OK) {
+    if (has_tri && launch_pyramid<float>(t, d_field, b->d_pyr, cs) != OT_OK) {
         cudaGraph_t g = nullptr;
         cudaStreamEndCapture(cs, &g);
         if (g) cudaGraphDestroy(g);
         return fail(cudaErrorUnknown);
     }
-    const double4* P = static_cast<const double4*>(b->d_prefix);
     {
-        void* args[] = {&v, &a, (void*)&d_field, (void*)&P, &b->d_counter};
+        void* args[] = {&v, &a, (void*)&d_field, (void*)&b->d_pyr, &b->d_counter};
         cudaLaunchKernel(kfn, dim3(grid), dim3(block), args, smem, cs);
     }
     e = cudaStreamEndCapture(cs, &b->graph);
@@ -178,7 +182,7 @@ extern "C" ot_status ot_batch_destroy(ot_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->d_counter) cudaFree(b->d_counter);
-    if (b->d_prefix) cudaFree(b->d_prefix);
+    if (b->d_pyr) cudaFree(b->d_pyr);
     delete b;
     return OT_OK;
 }

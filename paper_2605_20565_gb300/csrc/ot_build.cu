@@ -479,12 +479,24 @@ ot_status leaf_centres(const ot_octree* t, double* d_xyz, cudaStream_t s) {
 
 ot_status finish_tree(ot_octree* t, cudaStream_t s, int map_level) {
     const int L = map_level >= 0 ? std::min(map_level, t->lmax) : std::min(t->lmax, 7);
-    const int64_t ncell = (int64_t)1 << (3 * L);
-    if (t->d_lmap) cudaFree(t->d_lmap);
+    const int Lp = std::min(t->lmax, 7);
+    if (!t->d_pmap) {
+        const int64_t np = (int64_t)1 << (3 * Lp);
+        OT_CUDA(cudaMalloc(&t->d_pmap, sizeof(uint32_t) * np));
+        k_lmap<<<grid1d(np, 256), 256, 0, s>>>(t->d_key, (int)t->n, Lp, np, t->d_pmap);
+        count_launch();
+        t->pyr_level = Lp;
+    }
+    if (t->d_lmap && t->d_lmap != t->d_pmap) cudaFree(t->d_lmap);
     t->d_lmap = nullptr;
-    OT_CUDA(cudaMalloc(&t->d_lmap, sizeof(uint32_t) * ncell));
-    k_lmap<<<grid1d(ncell, 256), 256, 0, s>>>(t->d_key, (int)t->n, L, ncell, t->d_lmap);
-    count_launch();
+    if (L == Lp) {
+        t->d_lmap = t->d_pmap;
+    } else {
+        const int64_t ncell = (int64_t)1 << (3 * L);
+        OT_CUDA(cudaMalloc(&t->d_lmap, sizeof(uint32_t) * ncell));
+        k_lmap<<<grid1d(ncell, 256), 256, 0, s>>>(t->d_key, (int)t->n, L, ncell, t->d_lmap);
+        count_launch();
+    }
     t->lmap_level = L;
     if (!t->d_err) {
         OT_CUDA(cudaMalloc(&t->d_err, 64));
@@ -505,6 +517,7 @@ TreeView tree_view(const ot_octree* t) {
     v.lmax = t->lmax;
     v.lmap = t->d_lmap;
     v.lmap_level = t->lmap_level;
+    v.pyr_level = t->pyr_level;
     v.root = t->d_root;
     v.models = t->d_models;
     v.mids = t->d_mids;

@@ -132,6 +132,7 @@ struct TreeView {
     // top levels of the tree, staged as a dense table)
     const uint32_t* __restrict__ lmap;
     int lmap_level;
+    int pyr_level;  // deepest level of the pyramid of cell means (refined trilinear level-mates)
     // learned search: root -> (optional mid models) -> leaf models
     const RootModel* __restrict__ root;  // device copy
     const LeafModel* __restrict__ models;
@@ -155,13 +156,14 @@ __device__ __forceinline__ int search_range(const uint64_t* __restrict__ key, in
 }
 
 // Cell of the level map holding key q, and the leaf range [a, e) of that cell: a is the leaf
-// holding the cell's anchor; when that leaf's level is <= the map level it covers the whole
-// cell (then it is the answer for every key in the cell).
+// holding the cell's anchor, e the one holding the next cell's.  One leaf covers the whole cell
+// (and is the answer for every key in it) exactly when e - a <= 1: a refined cell holds at
+// least 8 leaves, the first starting at its anchor.
 __device__ __forceinline__ void map_range(const TreeView& t, uint64_t q, int& a, int& e, bool& covered) {
     const uint32_t c = (uint32_t)(q >> (3 * (MAXLEVEL - t.lmap_level)));
     a = (int)t.lmap[c];
-    covered = (int)t.level[a] <= t.lmap_level;
     e = (c + 1 < (1u << (3 * t.lmap_level))) ? (int)t.lmap[c + 1] : t.n;
+    covered = e - a <= 1;
 }
 
 // Plain host search (Algorithm 1's answer, upper bound - 1): the level map gives the leaf
@@ -314,14 +316,14 @@ template <> struct Stencil<OT_ROMA3> {
 template <typename T> struct Vec4;
 template <> struct Vec4<float> {
     using type = float4;
-    __device__ static float4 load(const float* f, int i) { return __ldg(reinterpret_cast<const float4*>(f) + i); }
+    __device__ static float4 load(const float* f, long long i) { return __ldg(reinterpret_cast<const float4*>(f) + i); }
 };
 struct __align__(32) dbl4 {
     double x, y, z, w;
 };
 template <> struct Vec4<double> {
     using type = dbl4;
-    __device__ static dbl4 load(const double* f, int i) {
+    __device__ static dbl4 load(const double* f, long long i) {
         const double2* p = reinterpret_cast<const double2*>(f) + 2 * (size_t)i;
         double2 a = __ldg(p), b = __ldg(p + 1);
         return dbl4{a.x, a.y, b.x, b.y};

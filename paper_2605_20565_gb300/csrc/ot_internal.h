@@ -18,6 +18,10 @@ struct ot_octree {
     // level map: the leaf holding the anchor of every cell of level lmap_level
     uint32_t* d_lmap = nullptr;
     int lmap_level = 0;
+    // the same table at the pyramid level min(lmax, 7), fixed for the octree's life (it is
+    // d_lmap when the two levels agree): leaf ranges of the cells of the pyramid of means
+    uint32_t* d_pmap = nullptr;
+    int pyr_level = 0;
     // learned index
     bool has_index = false;
     ot::RootModel root{};
@@ -94,10 +98,14 @@ template <typename T>
 ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const double* y, const double* z, int64_t n,
                         const int32_t* host_in, int search, const T* field, T* u, int32_t* host_out, cudaStream_t s);
 
-// volume-weighted field prefix (ot_prefix.cu) --------------------------------------------------
-// P (n + 1 double4 entries, P[i] = sum_{j<i} f_j 8^-level_j) and tile sums in ws.
-size_t prefix_bytes(int64_t n);
-template <typename T> ot_status launch_prefix(const ot_octree* t, const T* field, void* ws, cudaStream_t s);
+// pyramid of cell means over levels 0 .. lmap_level (ot_pyramid.cu) ---------------------------
+// Level l occupies cells [pyramid_offset(l), pyramid_offset(l) + 8^l), 4 values per cell.
+int64_t pyramid_offset(int l);
+// Node means of levels pyr_level+1 .. lmax-1 follow the pyramid: node_levels arrays of n
+// entries (4 values each), indexed by the refined cell's first leaf.
+int node_levels(const ot_octree* t);
+size_t pyramid_bytes(const ot_octree* t);  // enough for either precision
+template <typename T> ot_status launch_pyramid(const ot_octree* t, const T* field, T* pyr, cudaStream_t s);
 
 // spreading (ot_spread.cu) ---------------------------------------------------------------------
 size_t spread_ws_bytes(const ot_octree* t, int kernel, int64_t n);

@@ -4,6 +4,7 @@
 
 #include "ot_internal.h"
 #include "ot_points.cuh"
+#include "ot_queue.cuh"
 
 namespace ot {
 
@@ -34,10 +35,14 @@ template <typename T, bool LEARNED>
 __global__ void __launch_bounds__(256) k_trilinear(TreeView t, const double* __restrict__ x,
                                                    const double* __restrict__ y, const double* __restrict__ z,
                                                    int64_t n, const int32_t* __restrict__ host_in,
-                                                   const T* __restrict__ field, const double4* __restrict__ P,
+                                                   const T* __restrict__ field, const T* __restrict__ pyr,
                                                    T* __restrict__ u, int32_t* __restrict__ host_out) {
     // warp-aligned iteration: every lane of a warp runs the same trip count (the trilinear
     // routine is warp-cooperative)
+    __shared__ WarpQueue s_queue[256 / 32];
+    __shared__ RootModel s_root;
+    WarpQueue& wq = s_queue[threadIdx.x >> 5];
+    stage_root<LEARNED>(t, s_root);
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -55,7 +60,7 @@ __global__ void __launch_bounds__(256) k_trilinear(TreeView t, const double* __r
                 active = false;
             }
         }
-        const int h = trilinear_point<T, LEARNED>(t, field, P, active, inr ? x[i] : 0.0, inr ? y[i] : 0.0,
+        const int h = trilinear_queued<T, LEARNED>(t, s_root, field, pyr, wq, active, inr ? x[i] : 0.0, inr ? y[i] : 0.0,
                                                   inr ? z[i] : 0.0, hin, o);
         if (inr) {
             u[i] = o[0];
@@ -138,18 +143,18 @@ ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const d
         k_<<<persistent_grid(k_, block, smem, n), block, smem, s>>>(__VA_ARGS__);          \
     } while (0)
     if (kernel == OT_TRILINEAR) {
-        // prefix of the volume-weighted field (refined level-mates), stream-ordered scratch
+        // pyramid of cell means (refined level-mates), stream-ordered scratch
         void* pws = nullptr;
-        OT_CUDA(cudaMallocAsync(&pws, prefix_bytes(t->n), s));
-        if ((st = launch_prefix<T>(t, field, pws, s)) != OT_OK) {
+        OT_CUDA(cudaMallocAsync(&pws, pyramid_bytes(t), s));
+        T* pyr = static_cast<T*>(pws);
+        if ((st = launch_pyramid<T>(t, field, pyr, s)) != OT_OK) {
             cudaFreeAsync(pws, s);
             return st;
         }
-        const double4* P = static_cast<const double4*>(pws);
         if (learned)
-            OT_LAUNCH((k_trilinear<T, true>), v, x, y, z, n, host_in, field, P, u, host_out);
+            OT_LAUNCH((k_trilinear<T, true>), v, x, y, z, n, host_in, field, pyr, u, host_out);
         else
-            OT_LAUNCH((k_trilinear<T, false>), v, x, y, z, n, host_in, field, P, u, host_out);
+            OT_LAUNCH((k_trilinear<T, false>), v, x, y, z, n, host_in, field, pyr, u, host_out);
         cudaFreeAsync(pws, s);
     } else if (kernel == OT_PESKIN4) {
         if (learned)

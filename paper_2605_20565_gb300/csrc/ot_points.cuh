@@ -1,5 +1,6 @@
-// ot_points.cuh -- per-point device routines: trilinear interpolation with level-mates,
-// delta-kernel interpolation and stencil enumeration, all on exact fixed-point coordinates.
+// ot_points.cuh -- per-point device routines: delta-kernel interpolation and stencil
+// enumeration on exact fixed-point coordinates (the trilinear routine, which searches
+// cooperatively across the warp, is in ot_queue.cuh).
 // Used by the single-op kernels, the persistent batched kernel and the spreading kernels.
 #pragma once
 
@@ -14,117 +15,8 @@ template <> __device__ __forceinline__ float qnan<float>() { return __int_as_flo
 template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
 
 
-// 2^k as a double, built from the bits (0 <= k < 1000).
-__device__ __forceinline__ double exp2_pos(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
-
-// Trilinear interpolation at one point (Sec. 2.3.2) with the level-mate rule:
-//   host leaf of level l, cell c; t_d = offset from the cell centre; s_d = +1 if t_d >= 0;
-//   level-mates c + {0, s_d}; weights prod (1 - |t_d|) or |t_d|;
-//   level-mate value: leaf of level l -> its value; inside a coarser leaf -> that leaf's
-//   value; refined -> volume-weighted mean of its leaves, (P[e] - P[a]) 8^l from the prefix P
-//   of the volume-weighted field over its leaf range [a, e); outside the cube -> the host's
-//   index on that axis.
-// Lanes with active == false do nothing.  Returns the host leaf (-1 when inactive or outside
-// the cube, out = NaN).
-template <typename T, bool LEARNED>
-__device__ __forceinline__ int trilinear_point(const TreeView& t, const T* __restrict__ field,
-                                               const double4* __restrict__ P, bool active, double x, double y,
-                                               double z, int host_in, T out[3]) {
-    using V = Vec4<T>;
-    uint64_t X[3] = {0, 0, 0};
-    const bool ok = active && fixpoint3(x, y, z, X);
-    if (active && !ok) atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
-    if (!ok) {
-        out[0] = out[1] = out[2] = qnan<T>();
-        return -1;
-    }
-    const int h = host_in >= 0 ? host_in
-                               : search<LEARNED>(t,
-                                                 morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32),
-                                                         (uint32_t)(X[2] >> 32)));
-    const int l = t.level[h];
-    const int ncell = 1 << l;
-    int c[3], sg[3];
-    T at[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        c[d] = (int)fix_cell(X[d], l);
-        sg[d] = fix_upper_half(X[d], l) ? 1 : -1;
-        const T td = fix_offset<T>(X[d], l);
-        at[d] = td < T(0) ? -td : td;
-    }
-    const int sh = MAXLEVEL - l;
-    const uint64_t span = key_span(l);
-    // level-mates: anchors, weights; a sibling of the host cell is usually h + (difference of
-    // child numbers), which one key comparison proves (keys are unique); the rest are searched
-    uint64_t anc[8];
-    T w[8];
-    int a[8];
-    unsigned self_mask = 0;
-#pragma unroll
-    for (int corner = 0; corner < 8; ++corner) {
-        int m[3];
-        T wc = T(1);
-        bool self = true;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int off = (corner >> d) & 1;
-            int v = c[d] + off * sg[d];
-            if (v < 0 || v >= ncell) v = c[d];
-            m[d] = v;
-            self = self && (v == c[d]);
-            wc *= off ? at[d] : T(1) - at[d];
-        }
-        w[corner] = wc;
-        anc[corner] = morton3((uint32_t)m[0] << sh, (uint32_t)m[1] << sh, (uint32_t)m[2] << sh);
-        a[corner] = h;
-        if (self) {
-            self_mask |= 1u << corner;
-            continue;
-        }
-        int g = -1;
-        if ((m[0] >> 1) == (c[0] >> 1) && (m[1] >> 1) == (c[1] >> 1) && (m[2] >> 1) == (c[2] >> 1)) {
-            const int gi = h + ((m[0] & 1) | ((m[1] & 1) << 1) | ((m[2] & 1) << 2)) -
-                           ((c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2));
-            if (gi >= 0 && gi < t.n && ldg_key(t.key + gi) == anc[corner]) g = gi;
-        }
-        a[corner] = g >= 0 ? g : search<LEARNED>(t, anc[corner]);
-    }
-    T acc0 = T(0), acc1 = T(0), acc2 = T(0);
-#pragma unroll
-    for (int corner = 0; corner < 8; ++corner) {
-        const int ak = a[corner];
-        T v0, v1, v2;
-        if (((self_mask >> corner) & 1u) || (int)t.level[ak] <= l) {
-            const auto f = V::load(field, ak);
-            v0 = f.x, v1 = f.y, v2 = f.z;
-        } else {
-            // refined: its leaves are [ak, e); e is the leaf that starts right after the cell
-            const uint64_t endkey = anc[corner] + span;
-            int e;
-            if (endkey >> 63) {
-                e = t.n;
-            } else if (l <= t.lmap_level) {
-                const uint32_t ca = (uint32_t)(endkey >> (3 * (MAXLEVEL - t.lmap_level)));
-                e = (int)t.lmap[ca];
-            } else {
-                e = search<LEARNED>(t, endkey);
-            }
-            const double4 pa = P[ak], pe = P[e];
-            const double sc = exp2_pos(3 * l);
-            v0 = (T)((pe.x - pa.x) * sc);
-            v1 = (T)((pe.y - pa.y) * sc);
-            v2 = (T)((pe.z - pa.z) * sc);
-        }
-        acc0 += w[corner] * v0;
-        acc1 += w[corner] * v1;
-        acc2 += w[corner] * v2;
-    }
-    out[0] = acc0;
-    out[1] = acc1;
-    out[2] = acc2;
-    return h;
-}
+// First cell of level l in the pyramid of cell means: sum_{k<l} 8^k = (8^l - 1) / 7.
+__device__ __forceinline__ long long pyr_offset(int l) { return ((1LL << (3 * l)) - 1) / 7; }
 
 // Stencil origin and per-axis weights of a point with fixed-point coordinates X on the
 // finest level lmax (Sec. 2.2: W(x) = prod phi(x_d/dx)/dx).

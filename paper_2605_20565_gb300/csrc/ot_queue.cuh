@@ -1,0 +1,315 @@
+// ot_queue.cuh -- warp-cooperative host-cell search over a per-warp task list, and the
+// trilinear interpolation (Sec. 2.3.2, level-mate rule) built on it.
+//
+// A point needs up to 8 searches (its host, then the level-mates that are not siblings of the
+// host) and each search takes 0 to ~12 dependent key probes, so a warp that gives each lane its
+// own searches idles most lanes: every corner costs the longest lane's search.  Here the lanes
+// first append every search they need to a task list in shared memory (ballot + popc, no
+// atomics); then each lane takes the next task whenever its current one ends and performs one
+// probe per step.  The warp's step count follows the total number of probes / 32 instead of the
+// sum over corners of the longest lane's.  Results are exactly those of the per-lane searches
+// (the same halving over the same range).
+#pragma once
+
+#include "ot_points.cuh"
+
+namespace ot {
+
+constexpr int QCAP = 7 * 32;  // level-mate searches of a warp's 32 points (the host's need 32)
+constexpr unsigned FULL = 0xffffffffu;
+
+// A warp's task list: key searched, and the range to search (the uncovered level-map cell);
+// lo holds the answer once the task has run.
+struct WarpQueue {
+    uint64_t q[QCAP];
+    int lo[QCAP];
+    int len[QCAP];
+};
+
+// The root model of the learned index, staged in shared memory by every block that searches
+// with it (block-wide call; a no-op for the plain form).
+template <bool LEARNED>
+__device__ __forceinline__ void stage_root(const TreeView& t, RootModel& s_root) {
+    if (LEARNED) {
+        const int* src = reinterpret_cast<const int*>(t.root);
+        int* dst = reinterpret_cast<int*>(&s_root);
+        for (int i = threadIdx.x; i < (int)(sizeof(RootModel) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+}
+
+// Level-map cell of key q: the leaf holding its anchor (a) and the next cell's (e).  The cell
+// is covered by one leaf -- leaf a, the answer -- exactly when e - a <= 1 (a refined cell holds
+// at least 8 leaves, its first one starting at its anchor).
+__device__ __forceinline__ void map_cell_range(const TreeView& t, uint64_t q, int& a, int& e) {
+    const uint32_t cell = (uint32_t)(q >> (3 * (MAXLEVEL - t.lmap_level)));
+    a = (int)t.lmap[cell];
+    e = cell < (1u << (3 * t.lmap_level)) - 1u ? (int)t.lmap[cell + 1] : t.n;
+}
+
+// Appends a task for every lane with need set (warp-wide call); returns the lane's task index
+// or -1.  n is the warp-uniform task count.
+__device__ __forceinline__ int push_task(WarpQueue& w, int& n, bool need, uint64_t q, int lo, int len, unsigned lt) {
+    const unsigned m = __ballot_sync(FULL, need);
+    const int idx = n + __popc(m & lt);
+    n += __popc(m);
+    if (need) {
+        w.q[idx] = q;
+        w.lo[idx] = lo;
+        w.len[idx] = len;
+    }
+    return need ? idx : -1;
+}
+
+// Runs the warp's ntask tasks (warp-wide call).  Each step, a lane without a task takes the
+// next one, and every lane with a task advances it by one step of at most one memory round
+// trip:
+//   plain:   halving probes over the cell's leaves;
+//   learned: route (root model from shared memory, then the middle model's load), leaf model
+//            load and window (its prediction widened by the stored error bounds, clamped to
+//            the cell), halving probes over the window, and the check key[a] <= q < key[a+1];
+//            a window that missed is replaced by the whole cell (a counted fallback).
+// A finished task's answer (the last index in its range whose key is <= q) replaces its lo.
+// (Routing all tasks side by side before the loop was measured slower: it adds a round trip
+// and registers.)
+enum { ST_ROUTE = 0, ST_MODEL = 1, ST_PROBE = 2, ST_CHECK = 3, ST_DONE = 4 };
+
+template <bool LEARNED>
+__device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& root, WarpQueue& w, int ntask,
+                                          unsigned lt) {
+    __syncwarp();
+    int cur = -1, lo = 0, len = 0, next = 0, st = ST_DONE, clo = 0, clen = 0, j = 0;
+    bool checked = false;
+    uint64_t q = 0;
+    for (;;) {
+        const bool fin = cur >= 0 && st == ST_DONE;
+        if (fin) w.lo[cur] = lo;
+        const bool need = cur < 0 || fin;
+        const unsigned m = __ballot_sync(FULL, need);
+        if (need) {
+            const int idx = next + __popc(m & lt);
+            cur = -1;
+            if (idx < ntask) {
+                cur = idx;
+                q = w.q[idx];
+                lo = clo = w.lo[idx];
+                len = clen = w.len[idx];
+                st = LEARNED ? ST_ROUTE : ST_PROBE;
+                checked = false;
+            }
+        }
+        next += __popc(m);
+        if (!__any_sync(FULL, cur >= 0)) break;
+        if (cur < 0) continue;
+        if (LEARNED && st == ST_ROUTE) {
+            j = root_route(root, q);
+            if (t.mids) j = (int)(((int64_t)leaf_predict(t.mids[j], q, t.n) * t.n_leaf) / t.n);
+            st = ST_MODEL;
+        } else if (LEARNED && st == ST_MODEL) {
+            const LeafModel md = t.models[j];
+            int wl = clo, wh = clo + clen - 1;
+            if (md.count > 0) {
+                const int pc = leaf_predict(md, q, t.n);
+                wl = max(pc - md.err_lo - 1, clo);
+                wh = min(pc + md.err_hi + 1, clo + clen - 1);
+            }
+            if (md.count > 0 && wl <= wh) {
+                lo = wl;
+                len = wh - wl + 1;
+            } else {
+                atomicAdd(t.fallbacks, 1ULL);
+                atomicOr(t.err, (unsigned)OT_DEV_WINDOW);
+                checked = true;  // the whole cell: its answer needs no check
+            }
+            st = ST_PROBE;
+        } else if (st == ST_PROBE) {
+            if (len > 1) {
+                const int half = len >> 1;
+                const uint64_t k = ldg_key(t.key + lo + half);
+                lo = (k <= q) ? lo + half : lo;
+                len -= half;
+            }
+            if (len <= 1) st = (LEARNED && !checked) ? ST_CHECK : ST_DONE;
+        } else if (LEARNED && st == ST_CHECK) {
+            const uint64_t k0 = ldg_key(t.key + lo);
+            const uint64_t k1 = lo + 1 < t.n ? ldg_key(t.key + lo + 1) : ~0ULL;
+            checked = true;
+            st = ST_DONE;
+            if (!(k0 <= q && q < k1)) {
+                atomicAdd(t.fallbacks, 1ULL);
+                atomicOr(t.err, (unsigned)OT_DEV_WINDOW);
+                lo = clo;
+                len = clen;
+                st = len > 1 ? ST_PROBE : ST_DONE;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Trilinear interpolation at one point per lane (warp-wide call; Sec. 2.3.2 with the
+// level-mate rule):
+//   host leaf of level l, cell c; t_d = offset from the cell centre; s_d = +1 if t_d >= 0;
+//   level-mates c + {0, s_d}; weights prod (1 - |t_d|) or |t_d|;
+//   level-mate value: leaf of level l -> its value; inside a coarser leaf -> that leaf's
+//   value; refined -> volume-weighted mean of its leaves, one load: from the dense pyramid of
+//   cell means for l <= the pyramid level, else from the node means of level l (both in pyr);
+//   outside the cube -> the host's index on that axis.
+// Lanes with active == false take part in the warp's steps only.  host_in >= 0 gives the host.
+// Returns the host leaf (-1 when inactive or outside the cube, out = NaN).
+template <typename T, bool LEARNED>
+__device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootModel& root, const T* __restrict__ field,
+                                                const T* __restrict__ pyr, WarpQueue& w, bool active, double x,
+                                                double y, double z, int host_in, T out[3]) {
+    using V = Vec4<T>;
+    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+    uint64_t X[3] = {0, 0, 0};
+    const bool ok = active && fixpoint3(x, y, z, X);
+    if (active && !ok) atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
+
+    // host
+    int h = host_in;
+    {
+        const uint64_t q = morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32));
+        int ca = 0, ce = 0;
+        if (ok && h < 0) map_cell_range(t, q, ca, ce);
+        const bool need = ok && h < 0 && ce - ca > 1;
+        if (ok && h < 0 && !need) h = ca;
+        if (__any_sync(FULL, need)) {
+            int n = 0;
+            const int ix = push_task(w, n, need, q, ca, ce - ca, lt);
+            run_tasks<LEARNED>(t, root, w, n, lt);
+            if (ix >= 0) h = w.lo[ix];
+            __syncwarp();
+        }
+    }
+    if (!ok) h = 0;  // keeps the lane's reads in bounds; its result is discarded
+
+    const int l = t.level[h];
+    const int ncell = 1 << l;
+    int c[3], sg[3];
+    T at[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        c[d] = (int)fix_cell(X[d], l);
+        sg[d] = fix_upper_half(X[d], l) ? 1 : -1;
+        const T td = fix_offset<T>(X[d], l);
+        at[d] = td < T(0) ? -td : td;
+    }
+    const int sh = MAXLEVEL - l;
+    // The level-mates are resolved in stages, each issuing its loads for all 8 corners at once
+    // (independent loads in flight together instead of one dependent chain per corner).
+    // Stage 1: anchors, weights, and the sibling guess h + (difference of child numbers) for
+    // level-mates in the host's parent cell.
+    uint64_t anc[8];
+    T wt[8];
+    int a[8], gi[8];
+    unsigned self_m = 1u, sib_m = 0u;
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+        int m[3];
+        T wc = T(1);
+        bool self = true, sib = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int off = (corner >> d) & 1;
+            int v = c[d] + off * sg[d];
+            if (v < 0 || v >= ncell) v = c[d];
+            m[d] = v;
+            self = self && (v == c[d]);
+            sib = sib && ((v >> 1) == (c[d] >> 1));
+            wc *= off ? at[d] : T(1) - at[d];
+        }
+        wt[corner] = wc;
+        anc[corner] = morton3((uint32_t)m[0] << sh, (uint32_t)m[1] << sh, (uint32_t)m[2] << sh);
+        a[corner] = h;
+        gi[corner] = min(max(h + ((m[0] & 1) | ((m[1] & 1) << 1) | ((m[2] & 1) << 2)) -
+                                 ((c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2)),
+                             0),
+                         t.n - 1);
+        if (self) self_m |= 1u << corner;
+        if (sib && !self) sib_m |= 1u << corner;
+    }
+    if (!ok) self_m = 0xffu, sib_m = 0u;
+    // Stage 2: the guessed siblings' keys (a match proves the guess: keys are unique) and, in
+    // the same round of loads, the level-map cells of the other level-mates (a cell covered by
+    // one leaf settles its level-mate).  Stage 3: a failed guess's cell.  Stage 4: the rest
+    // become tasks of the warp's list.
+    unsigned pend_m = ~self_m & 0xffu;
+    int ca[8], ce[8];
+    {
+        uint64_t gk[8];
+#pragma unroll
+        for (int corner = 1; corner < 8; ++corner) {
+            ca[corner] = 0;
+            ce[corner] = 0;
+            gk[corner] = 0;
+            if ((sib_m >> corner) & 1u)
+                gk[corner] = ldg_key(t.key + gi[corner]);
+            else if ((pend_m >> corner) & 1u)
+                map_cell_range(t, anc[corner], ca[corner], ce[corner]);
+        }
+#pragma unroll
+        for (int corner = 1; corner < 8; ++corner) {
+            if (!((sib_m >> corner) & 1u)) continue;
+            if (gk[corner] == anc[corner]) {
+                a[corner] = gi[corner];
+                pend_m &= ~(1u << corner);
+            } else {
+                map_cell_range(t, anc[corner], ca[corner], ce[corner]);
+            }
+        }
+#pragma unroll
+        for (int corner = 1; corner < 8; ++corner)
+            if (((pend_m >> corner) & 1u) && ce[corner] - ca[corner] <= 1) {
+                a[corner] = ca[corner];
+                pend_m &= ~(1u << corner);
+            }
+    }
+    if (__any_sync(FULL, pend_m != 0u)) {
+        int n = 0;
+        int tix[8];
+#pragma unroll
+        for (int corner = 1; corner < 8; ++corner)
+            tix[corner] = push_task(w, n, (pend_m >> corner) & 1u, anc[corner], ca[corner], ce[corner] - ca[corner], lt);
+        run_tasks<LEARNED>(t, root, w, n, lt);
+#pragma unroll
+        for (int corner = 1; corner < 8; ++corner)
+            if (tix[corner] >= 0) a[corner] = w.lo[tix[corner]];
+        __syncwarp();
+    }
+    if (!ok) {
+        out[0] = out[1] = out[2] = qnan<T>();
+        return -1;
+    }
+    // Stage 6: levels of the level-mates' leaves; stage 7: their values.
+    int lvl[8];
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) lvl[corner] = ((self_m >> corner) & 1u) ? l : (int)t.level[a[corner]];
+    // a refined level-mate: the pyramid cell (l <= pyramid level) or the node mean of level l
+    // indexed by its first leaf
+    const bool in_pyr = l <= t.pyr_level;
+    const T* rbase = in_pyr ? pyr + 4 * pyr_offset(l) : pyr + 4 * (pyr_offset(t.pyr_level + 1) +
+                                                               (long long)(l - t.pyr_level - 1) * t.n);
+    T v[8][3];
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+        const bool refined = lvl[corner] > l;
+        const long long ri = in_pyr ? (long long)(anc[corner] >> (3 * sh)) : (long long)a[corner];
+        const auto f = V::load(refined ? rbase : field, refined ? ri : (long long)a[corner]);
+        v[corner][0] = f.x, v[corner][1] = f.y, v[corner][2] = f.z;
+    }
+    T acc0 = T(0), acc1 = T(0), acc2 = T(0);
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+        acc0 += wt[corner] * v[corner][0];
+        acc1 += wt[corner] * v[corner][1];
+        acc2 += wt[corner] * v[corner][2];
+    }
+    out[0] = acc0;
+    out[1] = acc1;
+    out[2] = acc2;
+    return h;
+}
+
+} // namespace ot

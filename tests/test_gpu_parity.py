@@ -441,3 +441,49 @@ def test_advect_ab2_matches_oracle(ot, torch_mod):
         ot.ot_advect_ab2(dx, dv, da, dvp, dev(u), 0.05, 2.0, 1e-3, step == 0)
     assert rel_err(dv.cpu().numpy(), st["v"]) <= TOL32
     assert np.abs(dx.cpu().numpy() - st["x"]).max() <= 1e-9
+
+
+@pytest.fixture(scope="module")
+def deep(ot):
+    """Levels 3-9 around two small spheres (~294k leaves): host leaves of levels 7-9 have refined
+    level-mates both inside the pyramid of cell means (level <= 7) and below it."""
+    sph = np.array([[0.53, 0.47, 0.51, 0.05, 0.02], [0.2, 0.7, 0.3, 0.03, 0.015]])
+    ko, lo = oracle.octree_build(sph, 3, 9)
+    rng = np.random.default_rng(91)
+    d = rng.normal(size=(30000, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    which = rng.integers(0, 2, 30000)
+    rad = sph[which, 3] + rng.uniform(-3, 3, 30000) * sph[which, 4]
+    P = np.concatenate([sph[which, :3] + d * rad[:, None], rng.uniform(0, 1, (5000, 3))])
+    P = P[np.all((P >= 0) & (P < 1), axis=1)]
+    from paper_2605_20565_gb300 import synth
+    field = synth.sin_field(oracle.leaf_centres(ko, lo))
+    return sph, ko, lo, P, field
+
+
+@pytest.mark.parametrize("map_level", [-1, 0, 8])
+def test_deep_tree_trilinear(ot, deep, map_level, torch_mod):
+    sph, ko, lo, P, field = deep
+    t = ot.ot_octree_build(sph, 3, 9)
+    kt, lt = leaves_np(ot, t)
+    assert np.array_equal(kt, ko) and np.array_equal(lt, lo)
+    if map_level >= 0:
+        ot.ot_octree_set_map_level(t, map_level)
+    href = oracle.locate_ub(ko, lo, *P.T)
+    f32 = field.astype(np.float32)
+    ref32 = oracle.interp_trilinear(ko, lo, f32.astype(np.float64), *P.T, href)
+    hout = torch_mod.empty(P.shape[0], dtype=torch_mod.int32, device="cuda")
+    u = ot.ot_interpolate(t, ot.OT_TRILINEAR, *pts(P.T), dev(f32), host_out=hout).cpu().numpy()
+    assert np.array_equal(hout.cpu().numpy(), href)
+    assert rel_err(u, ref32) <= TOL32
+    u64 = ot.ot_interpolate_f64(t, ot.OT_TRILINEAR, *pts(P.T), dev(field)).cpu().numpy()
+    assert rel_err(u64, oracle.interp_trilinear(ko, lo, field, *P.T, href)) <= TOL64
+    # the batched form (pyramid rebuilt inside the graph) gives the same values
+    ot.ot_index_train(t, root=ot.OT_ROOT_MLP, n_leaf_models=4096, n_mid_models=64, epochs=1, batch=16384)
+    for search in (0, 1):
+        ub = torch_mod.empty((3, P.shape[0]), dtype=torch_mod.float32, device="cuda")
+        x, y, z = pts(P.T)
+        b = ot.ot_batch_create(t, [dict(kernel=ot.OT_TRILINEAR, x=x, y=y, z=z, u=ub)], dev(f32), search=search)
+        ot.ot_batch_run(b)
+        assert rel_err(ub.cpu().numpy(), ref32) <= TOL32
+    assert ot.ot_last_error(t) & (ot.OT_DEV_OUTSIDE | ot.OT_DEV_STENCIL) == 0
