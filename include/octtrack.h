@@ -151,14 +151,17 @@ typedef struct {
 /* Train on the device over the octree's keys; replaces a previous index.  Synchronises. */
 ot_status ot_index_train(ot_octree* t, const ot_index_params* params, void* stream);
 
-/* Index statistics (host values): mean and max window length over the leaf models,
- * number of empty models, and learned-query fallbacks counted since the last reset. */
+/* Index statistics (host values): window length (mean over the stored keys, max over the
+ * leaf models), number of empty models, learned-query fallbacks counted since the last reset,
+ * and the mean number of halving probes a stored key's window takes (ceil(log2(window));
+ * a plain binary search of the whole array takes ceil(log2(N))). */
 typedef struct {
     double mean_window;
     int64_t max_window;
     int64_t empty_models;
     uint64_t fallbacks;
     float final_loss; /* MLP root: last minibatch loss (0 for a linear root) */
+    double mean_probes;
 } ot_index_stats;
 ot_status ot_index_get_stats(const ot_octree* t, ot_index_stats* s, int reset_fallbacks);
 
@@ -185,9 +188,10 @@ ot_status ot_locate(const ot_octree* t, const double* d_x, const double* d_y, co
  *     c + {0, s_d} per axis where s_d = sign of the offset from the host centre; a
  *     level-mate inside a coarser leaf takes that leaf's value, a refined one the
  *     volume-weighted mean of its leaves, one outside the cube the host's index on that axis.
- *     The refined means come from a pyramid of cell means over levels 0 .. L = min(lmax, 7),
- *     rebuilt by each call (stream-ordered scratch of 32 * (8^(L+1) - 1) / 7 bytes, 19 MB
- *     at L = 7); refined level-mates of deeper levels sum their few leaves directly.
+ *     The refined means are rebuilt by each call from the field, in stream-ordered scratch:
+ *     a dense pyramid of cell means over levels 0 .. L = min(lmax, 7) (16 * (8^(L+1) - 1) / 7
+ *     bytes in FP32, 38 MB at L = 7) and, for levels L+1 .. lmax-1, one array of N means per
+ *     level indexed by the refined cell's first leaf (16 N bytes per level in FP32).
  *   OT_PESKIN4 / OT_ROMA3 (Sec. 2.2, Eq. ibm_interpolate): u(X) = sum over the 4^3 / 3^3
  *     finest-level cells around X of phi(rx) phi(ry) phi(rz) u(cell); Peskin's 4-point or
  *     the paper's 3-point function.  Cells outside the cube or not finest-level leaves are
@@ -261,9 +265,9 @@ typedef struct {
 
 /* Launch shape of the batched kernel (0 = library default). */
 typedef struct {
-    int block;       /* threads per block: 64 .. 1024, multiple of 32                       */
-    int tile;        /* points per work item fetched from the queue                         */
-    int blocks_per_sm;
+    int block;       /* threads per block: 64 .. 256, multiple of 32 (default 256)          */
+    int tile;        /* 32-point rows per work item taken from the queue: 1 .. 64 (default 4) */
+    int blocks_per_sm; /* resident blocks per SM, capped by occupancy (0: the occupancy max) */
 } ot_launch;
 
 /* Create a batch over groups (copied) reading d_field (float4 per leaf).  search selects
@@ -276,6 +280,22 @@ ot_status ot_batch_create(const ot_octree* t, const ot_group* groups, int n_grou
                           int search, const ot_launch* launch, void* stream, ot_batch** out);
 ot_status ot_batch_run(ot_batch* b, void* stream);
 ot_status ot_batch_destroy(ot_batch* b);
+
+/* Autotuner of the batched launch (not in the paper): creates the batch for every launch
+ * shape of {128, 256} threads x {1, 2, 4, 8} rows per work item x {occupancy max, 2} blocks
+ * per SM and, when tune_map_level != 0, every level-map level from min(lmax, 6) to
+ * min(lmax, 8); times `reps` graph replays of each (CUDA events on `stream`, after one
+ * warm-up replay) and returns the fastest.  The octree is left at the chosen level-map level
+ * (batches made earlier on it must be recreated).  The groups' outputs are overwritten.
+ * Synchronises the stream; takes about (1 + reps) * 16 * levels replays. */
+typedef struct {
+    ot_launch launch; /* fastest launch shape                                                */
+    int map_level;    /* its level-map level                                                 */
+    float ms;         /* mean time of one replay there                                       */
+    int tried;        /* settings timed                                                      */
+} ot_tune_result;
+ot_status ot_batch_autotune(ot_octree* t, const ot_group* groups, int n_groups, const float* d_field, int search,
+                            int tune_map_level, int reps, void* stream, ot_tune_result* out);
 
 /* ---------------------------------------------------------------------------------------
  * Point-particle advection (Sec. 2.3.2, Eq. PointParticle, gravity off): per particle

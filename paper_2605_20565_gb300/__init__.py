@@ -21,7 +21,7 @@ __all__ = [
     "OtError", "Octree", "Batch", "library_path", "ot_octree_build", "ot_octree_from_leaves", "ot_octree_info",
     "ot_octree_copy_leaves", "ot_octree_set_map_level", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats",
     "ot_index_mlp_grad", "ot_locate", "ot_interpolate", "ot_interpolate_f64", "ot_spread_workspace_size",
-    "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
+    "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
     "ot_last_error", "ot_launch_count",
 ]
 
@@ -62,7 +62,7 @@ class _IndexParams(C.Structure):
 
 class _IndexStats(C.Structure):
     _fields_ = [("mean_window", C.c_double), ("max_window", C.c_int64), ("empty_models", C.c_int64),
-                ("fallbacks", C.c_uint64), ("final_loss", C.c_float)]
+                ("fallbacks", C.c_uint64), ("final_loss", C.c_float), ("mean_probes", C.c_double)]
 
 
 class _Group(C.Structure):
@@ -72,6 +72,10 @@ class _Group(C.Structure):
 
 class _Launch(C.Structure):
     _fields_ = [("block", C.c_int), ("tile", C.c_int), ("blocks_per_sm", C.c_int)]
+
+
+class _TuneResult(C.Structure):
+    _fields_ = [("launch", _Launch), ("map_level", C.c_int), ("ms", C.c_float), ("tried", C.c_int)]
 
 
 def _L():
@@ -104,6 +108,7 @@ def _L():
                 "ot_spread": (st, [P, i32, i32, P, P, P, P, P, i64, P, P, C.c_size_t, P]),
                 "ot_spread_f64": (st, [P, i32, i32, P, P, P, P, P, i64, P, P, C.c_size_t, P]),
                 "ot_batch_create": (st, [P, P, i32, P, i32, P, P, P]),
+                "ot_batch_autotune": (st, [P, P, i32, P, i32, i32, i32, P, P]),
                 "ot_batch_run": (st, [P, P]),
                 "ot_batch_destroy": (st, [P]),
                 "ot_advect_ab2": (st, [P, P, P, P, P, i64, C.c_float, C.c_float, C.c_float, i32, i32, P]),
@@ -248,7 +253,7 @@ def ot_index_get_stats(tree: Octree, reset: bool = False) -> dict:
     s = _IndexStats()
     _check(_L().ot_index_get_stats(tree.handle, C.byref(s), int(reset)))
     return {"mean_window": s.mean_window, "max_window": s.max_window, "empty_models": s.empty_models,
-            "fallbacks": s.fallbacks, "final_loss": s.final_loss}
+            "fallbacks": s.fallbacks, "final_loss": s.final_loss, "mean_probes": s.mean_probes}
 
 
 def ot_index_mlp_grad(params, x, t, stream=None):
@@ -341,12 +346,9 @@ def ot_spread_f64(tree: Octree, kernel: int, mode: int, x, y, z, F, f, dV=None, 
 
 # --- batch ----------------------------------------------------------------------------------
 
-def ot_batch_create(tree: Octree, groups, field, search: int = OT_BINARY, launch: dict | None = None,
-                    stream=None) -> Batch:
-    """groups: list of dicts {kernel, x, y, z, u, host (optional)}; tensors stay referenced."""
+def _groups(groups):
     torch = _torch()
     arr = (_Group * len(groups))()
-    keep = [field]
     for i, g in enumerate(groups):
         n, px, py, pz = _xyz(g["x"], g["y"], g["z"])
         arr[i].kernel = g["kernel"]
@@ -354,7 +356,15 @@ def ot_batch_create(tree: Octree, groups, field, search: int = OT_BINARY, launch
         arr[i].n = n
         arr[i].d_u = _dptr(g["u"], torch.float32, "u")
         arr[i].d_host = _dptr(g.get("host"), torch.int32, "host")
-        keep.append(g)
+    return arr
+
+
+def ot_batch_create(tree: Octree, groups, field, search: int = OT_BINARY, launch: dict | None = None,
+                    stream=None) -> Batch:
+    """groups: list of dicts {kernel, x, y, z, u, host (optional)}; tensors stay referenced."""
+    torch = _torch()
+    arr = _groups(groups)
+    keep = [field] + list(groups)
     lp = None
     if launch:
         lp = _Launch(launch.get("block", 0), launch.get("tile", 0), launch.get("blocks_per_sm", 0))
@@ -363,6 +373,19 @@ def ot_batch_create(tree: Octree, groups, field, search: int = OT_BINARY, launch
                                 C.byref(lp) if lp is not None else None, _stream(stream), C.byref(h)))
     keep.append(tree)
     return Batch(h, keep)
+
+
+def ot_batch_autotune(tree: Octree, groups, field, search: int = OT_BINARY, tune_map_level: bool = True,
+                      reps: int = 3, stream=None) -> dict:
+    """Fastest launch shape (and level-map level) for a batch over these groups; the octree is
+    left at the chosen level map.  Returns {launch: {block, tile, blocks_per_sm}, map_level, ms,
+    tried}."""
+    torch = _torch()
+    r = _TuneResult()
+    _check(_L().ot_batch_autotune(tree.handle, _groups(groups), len(groups), _dptr(field, torch.float32, "field"),
+                                  search, int(tune_map_level), reps, _stream(stream), C.byref(r)))
+    return {"launch": {"block": r.launch.block, "tile": r.launch.tile, "blocks_per_sm": r.launch.blocks_per_sm},
+            "map_level": r.map_level, "ms": r.ms, "tried": r.tried}
 
 
 def ot_batch_run(batch: Batch, stream=None):

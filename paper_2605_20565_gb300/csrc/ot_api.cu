@@ -215,7 +215,7 @@ ot_status ot_index_get_stats(const ot_octree* t, ot_index_stats* s, int reset) {
     if (!t->has_index) return OT_ERR_NO_INDEX;
     std::vector<LeafModel> m(t->n_models);
     OT_CUDA(cudaMemcpy(m.data(), t->d_models, sizeof(LeafModel) * m.size(), cudaMemcpyDeviceToHost));
-    double sum = 0.0;
+    double sum = 0.0, probes = 0.0;
     int64_t mx = 0, empty = 0, used = 0;
     for (const LeafModel& x : m) {
         if (x.count == 0 || x.err_lo < 0) {  // no stored key routed here (filled model)
@@ -224,10 +224,12 @@ ot_status ot_index_get_stats(const ot_octree* t, ot_index_stats* s, int reset) {
         }
         const int64_t w = (int64_t)x.err_lo + x.err_hi + 3;
         sum += (double)w * x.count; // weighted by the keys the model serves
+        probes += std::ceil(std::log2((double)w)) * x.count;
         used += x.count;
         mx = std::max(mx, w);
     }
     s->mean_window = used ? sum / (double)used : 0.0;
+    s->mean_probes = used ? probes / (double)used : 0.0;
     s->max_window = mx;
     s->empty_models = empty;
     unsigned long long fb = 0;

@@ -134,7 +134,7 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned))) != cudaSuccess) return fail(e);
     bool has_tri = false;
     for (int k = 0; k < n_groups; ++k) has_tri = has_tri || groups[k].kernel == OT_TRILINEAR;
-    if (has_tri && (e = cudaMalloc(&b->d_pyr, pyramid_bytes(t))) != cudaSuccess) return fail(e);
+    if (has_tri && (e = cudaMalloc(&b->d_pyr, pyramid_bytes(t, sizeof(float)))) != cudaSuccess) return fail(e);
     b->kernels = has_tri ? 2 + t->pyr_level : 1;
     TreeView v = tree_view(t);
     const size_t smem = 0;

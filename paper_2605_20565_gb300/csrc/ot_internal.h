@@ -104,7 +104,7 @@ int64_t pyramid_offset(int l);
 // Node means of levels pyr_level+1 .. lmax-1 follow the pyramid: node_levels arrays of n
 // entries (4 values each), indexed by the refined cell's first leaf.
 int node_levels(const ot_octree* t);
-size_t pyramid_bytes(const ot_octree* t);  // enough for either precision
+size_t pyramid_bytes(const ot_octree* t, size_t elem);  // elem: sizeof the field type
 template <typename T> ot_status launch_pyramid(const ot_octree* t, const T* field, T* pyr, cudaStream_t s);
 
 // spreading (ot_spread.cu) ---------------------------------------------------------------------

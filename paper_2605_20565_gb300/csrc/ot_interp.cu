@@ -145,7 +145,7 @@ ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const d
     if (kernel == OT_TRILINEAR) {
         // pyramid of cell means (refined level-mates), stream-ordered scratch
         void* pws = nullptr;
-        OT_CUDA(cudaMallocAsync(&pws, pyramid_bytes(t), s));
+        OT_CUDA(cudaMallocAsync(&pws, pyramid_bytes(t, sizeof(T)), s));
         T* pyr = static_cast<T*>(pws);
         if ((st = launch_pyramid<T>(t, field, pyr, s)) != OT_OK) {
             cudaFreeAsync(pws, s);

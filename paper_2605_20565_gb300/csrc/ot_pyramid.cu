@@ -119,9 +119,8 @@ int64_t pyramid_offset(int l) { return ((int64_t)1 << (3 * l)) / 7; }  // sum_{k
 
 int node_levels(const ot_octree* t) { return std::max(0, t->lmax - 1 - t->pyr_level); }
 
-size_t pyramid_bytes(const ot_octree* t) {
-    return sizeof(double) * 4 * ((size_t)pyramid_offset(t->pyr_level + 1) + (size_t)node_levels(t) * (size_t)t->n) +
-           256;
+size_t pyramid_bytes(const ot_octree* t, size_t elem) {
+    return elem * 4 * ((size_t)pyramid_offset(t->pyr_level + 1) + (size_t)node_levels(t) * (size_t)t->n) + 256;
 }
 
 template <typename T>
