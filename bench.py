@@ -56,7 +56,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--launch", default="", help="block,tile,blocks_per_sm")
-    p.add_argument("--map-level", type=int, default=None, help="level of the level map (default min(lmax, 7))")
+    p.add_argument("--map-level", type=int, default=None, help="level of the level map (default: autotuned)")
+    p.add_argument("--no-autotune", action="store_true", help="default launch shape and level map")
+    p.add_argument("--no-nomap", action="store_true", help="skip the forms without a level map")
     return p.parse_args()
 
 
@@ -101,7 +103,7 @@ def describe(w, n_leaves, search):
         "search": search,
         "index": search,
         "spread": "Peskin-4 sorted deterministic",
-        "level_map": "top levels staged as a dense level map (default level min(lmax, 7))",
+        "level_map": "top levels staged as a dense level map (level autotuned over 6-8 unless given)",
         "l2": "inputs larger than L2 (tree+field ~0.7 GB, points 1.2 GB); no flush",
     }
 
@@ -255,7 +257,6 @@ def run_ours(args):
             dist.barrier()
 
     w = make_workload(args.workload, args.scale, rank)
-    search = ot.OT_LEARNED if args.search == "learned" else ot.OT_BINARY
     t0 = time.time()
     tree = ot.ot_octree_build(w.spheres, w.lmin, w.lmax)
     torch.cuda.synchronize()
@@ -303,10 +304,30 @@ def run_ours(args):
         b, t, s = [int(v) for v in args.launch.split(",")]
         launch = dict(block=b, tile=t, blocks_per_sm=s)
     groups = [dict(kernel=ot.OT_PESKIN4, x=mx, y=my, z=mz, u=um), dict(kernel=ot.OT_TRILINEAR, x=px, y=py, z=pz, u=up)]
-    # both search forms over the same groups: the learned index and the plain binary search
-    batches = {"learned": ot.ot_batch_create(tree, groups, field, search=ot.OT_LEARNED, launch=launch),
-               "plain": ot.ot_batch_create(tree, groups, field, search=ot.OT_BINARY, launch=launch)}
     stream = torch.cuda.current_stream()
+
+    # search forms over the same groups: (search, level-map level, launch shape).  "plain" and
+    # "learned" are autotuned (launch shape and level-map level) unless a launch or map level is
+    # given; the "_nomap" forms search the whole key array (level map of one cell), the plain
+    # one being Algorithm 1's binary search and the learned one the index without any map.
+    base_level = ot.ot_octree_get_map_level(tree)
+    forms_cfg, tune = {}, {}
+    for name, sv in (("plain", ot.OT_BINARY), ("learned", ot.OT_LEARNED)):
+        if launch is None and not args.no_autotune:
+            r = ot.ot_batch_autotune(tree, groups, field, search=sv, tune_map_level=args.map_level is None, reps=2)
+            tune[name] = r
+            forms_cfg[name] = (sv, r["map_level"], r["launch"])
+        else:
+            forms_cfg[name] = (sv, base_level, launch)
+    if not args.no_nomap:
+        forms_cfg["plain_nomap"] = (ot.OT_BINARY, 0, launch)
+        forms_cfg["learned_nomap"] = (ot.OT_LEARNED, 0, launch)
+
+    def make_batch(name):
+        sv, lvl, lp = forms_cfg[name]
+        if ot.ot_octree_get_map_level(tree) != lvl:
+            ot.ot_octree_set_map_level(tree, lvl)
+        return ot.ot_batch_create(tree, groups, field, search=sv, launch=lp)
 
     def step(batch, ev=None):
         if ev:
@@ -329,17 +350,24 @@ def run_ours(args):
         return {"step_ms": statistics.mean(e[0].elapsed_time(e[2]) for e in evs_), "locate_interpolate_ms": li,
                 "spread_ms": sp}
 
-    for b in batches.values():
+    def warm(batch):
         for _ in range(max(3, args.warmup)):
-            step(b)
-    torch.cuda.synchronize()
-    assert ot.ot_last_error(tree) & (ot.OT_DEV_STENCIL | ot.OT_DEV_OUTSIDE | ot.OT_DEV_REFINED_CAP) == 0
+            step(batch)
+        torch.cuda.synchronize()
+
     if args.search == "auto":
-        cal = {k: time_steps(b, 3)["step_ms"] for k, b in batches.items()}
+        cal = {}
+        for name in ("plain", "learned"):
+            bb = make_batch(name)
+            warm(bb)
+            cal[name] = time_steps(bb, 3)["step_ms"]
+            del bb
         chosen = min(cal, key=cal.get)
     else:
         chosen = "learned" if args.search == "learned" else "plain"
-    other = "plain" if chosen == "learned" else "learned"
+    batch = make_batch(chosen)
+    warm(batch)
+    assert ot.ot_last_error(tree) & (ot.OT_DEV_STENCIL | ot.OT_DEV_OUTSIDE | ot.OT_DEV_REFINED_CAP) == 0
     ot.ot_index_get_stats(tree, reset=True)
 
     # timed region: the chosen form
@@ -352,7 +380,7 @@ def run_ours(args):
     torch.cuda.nvtx.range_push("timed")
     start.record(stream)
     for k in range(args.steps):
-        step(batches[chosen], evs[k])
+        step(batch, evs[k])
     stop.record(stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
@@ -365,35 +393,7 @@ def run_ours(args):
     spread_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
     value = job_value(npts, world, ms_step)
     fb = ot.ot_index_get_stats(tree, reset=True)["fallbacks"] if chosen == "learned" else None
-
-    # the other form, same steps (learned vs plain)
-    forms = {chosen: {"step_ms": ms_step, "locate_interpolate_ms": batch_ms, "spread_ms": spread_ms},
-             other: time_steps(batches[other], args.steps)}
-    for v_ in forms.values():
-        v_["points_per_s"] = npts / (v_["step_ms"] / 1e3)
-        v_["locate_interpolate_points_per_s"] = npts / (v_["locate_interpolate_ms"] / 1e3)
-    learned_vs_plain = {
-        "locate_interpolate": forms["plain"]["locate_interpolate_ms"] / forms["learned"]["locate_interpolate_ms"],
-        "step": forms["plain"]["step_ms"] / forms["learned"]["step_ms"]}
-    search = ot.OT_LEARNED if chosen == "learned" else ot.OT_BINARY
-    batch = batches[chosen]
-
-    # per-group timing (markers only, particles only), learned and plain
-    groups_t = {}
-    for gname, gsel in (("markers", groups[:1]), ("particles", groups[1:])):
-        for sname, sv in (("learned", ot.OT_LEARNED), ("binary", ot.OT_BINARY)):
-            bb = ot.ot_batch_create(tree, gsel, field, search=sv, launch=launch)
-            for _ in range(2):
-                ot.ot_batch_run(bb)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(5):
-                ot.ot_batch_run(bb)
-            b.record(stream)
-            torch.cuda.synchronize()
-            groups_t[f"{gname}_{sname}_ms"] = a.elapsed_time(b) / 5
-            del bb
-
+    search = forms_cfg[chosen][0]
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -409,7 +409,7 @@ def run_ours(args):
             for d in range(3):
                 (mx, my, mz)[d].copy_(hm[d], non_blocking=True)
                 (px, py, pz)[d].copy_(hp[d], non_blocking=True)
-            step(batches[chosen])
+            step(batch)
             hum.copy_(um, non_blocking=True)
             hup.copy_(up, non_blocking=True)
             hf.copy_(f, non_blocking=True)
@@ -426,6 +426,51 @@ def run_ours(args):
         e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / k_e2e, dist, dev)
         e2e = {"value": job_value(npts, world, e2e_ms), "unit": "points/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": k_e2e}
+
+    # the other forms, same steps (the chosen form's level map is restored afterwards)
+    forms = {chosen: {"step_ms": ms_step, "locate_interpolate_ms": batch_ms, "spread_ms": spread_ms}}
+    groups_t = {}
+    del batch
+    for name in forms_cfg:
+        if name != chosen:
+            bb = make_batch(name)
+            warm(bb)
+            forms[name] = time_steps(bb, args.steps)
+            del bb
+        # per-group timing (markers only, particles only) at the form's settings
+        sv, lvl, lp = forms_cfg[name]
+        for gname, gsel in (("markers", groups[:1]), ("particles", groups[1:])):
+            if ot.ot_octree_get_map_level(tree) != lvl:
+                ot.ot_octree_set_map_level(tree, lvl)
+            bb = ot.ot_batch_create(tree, gsel, field, search=sv, launch=lp)
+            for _ in range(2):
+                ot.ot_batch_run(bb)
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            for _ in range(5):
+                ot.ot_batch_run(bb)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            groups_t[f"{gname}_{name}_ms"] = a_.elapsed_time(b_) / 5
+            del bb
+    for name, v_ in forms.items():
+        v_["points_per_s"] = npts / (v_["step_ms"] / 1e3)
+        v_["locate_interpolate_points_per_s"] = npts / (v_["locate_interpolate_ms"] / 1e3)
+        v_["search"] = "learned" if forms_cfg[name][0] == ot.OT_LEARNED else "binary"
+        v_["map_level"] = forms_cfg[name][1]
+        v_["launch"] = forms_cfg[name][2]
+    learned_vs_plain = {
+        "with_level_map": {
+            "locate_interpolate": forms["plain"]["locate_interpolate_ms"] / forms["learned"]["locate_interpolate_ms"],
+            "step": forms["plain"]["step_ms"] / forms["learned"]["step_ms"]}}
+    if "plain_nomap" in forms:
+        learned_vs_plain["without_level_map"] = {
+            "locate_interpolate": forms["plain_nomap"]["locate_interpolate_ms"] /
+            forms["learned_nomap"]["locate_interpolate_ms"],
+            "step": forms["plain_nomap"]["step_ms"] / forms["learned_nomap"]["step_ms"]}
+    lvl_c = forms_cfg[chosen][1]
+    if ot.ot_octree_get_map_level(tree) != lvl_c:
+        ot.ot_octree_set_map_level(tree, lvl_c)
 
     if rank != 0:
         if dist:
@@ -472,15 +517,17 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": describe(w, n_leaves, INDEX_DESC[args.index] if chosen == "learned" else
-                              "plain: level map + binary search"),
+           "config": dict(describe(w, n_leaves, INDEX_DESC[args.index] if chosen == "learned" else
+                                   "plain: level map + binary search"),
+                          form=chosen, map_level=forms_cfg[chosen][1], launch=forms_cfg[chosen][2]),
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": int(launches), "clocks": clk,
            "breakdown_ms": {"locate_interpolate": batch_ms, "spread": spread_ms, "step": ms_step},
            "locate_interpolate_points_per_s": world * npts / (batch_ms / 1e3),
-           "forms": forms, "learned_vs_plain": learned_vs_plain, "groups_ms": groups_t,
+           "forms": forms, "learned_vs_plain": learned_vs_plain, "groups_ms": groups_t, "autotune": tune,
            "index": {"n_mid": n_mid, "n_leaf": n_leaf, "mean_window": istats["mean_window"], "max_window": istats["max_window"],
                      "empty_models": istats["empty_models"], "fallbacks_timed": fb,
+                     "mean_probes": istats["mean_probes"],
                      "final_loss": istats["final_loss"], "train_s": train_s},
            "setup_s": {"octree_build": build_s, "index_train": train_s},
            "parity": parity}

@@ -122,6 +122,8 @@ ot_status ot_octree_copy_leaves(const ot_octree* t, uint64_t* d_keys, uint8_t* d
  * among its cell's leaves.  8^level * 4 bytes of device memory.  Octrees are created with
  * min(lmax, 7).  Synchronises the stream. */
 ot_status ot_octree_set_map_level(ot_octree* t, int level, void* stream);
+/* The current level-map level. */
+ot_status ot_octree_get_map_level(const ot_octree* t, int* level);
 
 /* Leaf centres, FP64, written as 3 planes of N (x..., y..., z...). */
 ot_status ot_octree_centres(const ot_octree* t, double* d_xyz, void* stream);

@@ -19,7 +19,7 @@ __all__ = [
     "OT_TRILINEAR", "OT_PESKIN4", "OT_ROMA3", "OT_BINARY", "OT_LEARNED", "OT_SORTED", "OT_ATOMIC",
     "OT_ROOT_LINEAR", "OT_ROOT_MLP", "OT_DEV_OUTSIDE", "OT_DEV_STENCIL", "OT_DEV_REFINED_CAP", "OT_DEV_WINDOW",
     "OtError", "Octree", "Batch", "library_path", "ot_octree_build", "ot_octree_from_leaves", "ot_octree_info",
-    "ot_octree_copy_leaves", "ot_octree_set_map_level", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats",
+    "ot_octree_copy_leaves", "ot_octree_set_map_level", "ot_octree_get_map_level", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats",
     "ot_index_mlp_grad", "ot_locate", "ot_interpolate", "ot_interpolate_f64", "ot_spread_workspace_size",
     "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
     "ot_last_error", "ot_launch_count",
@@ -97,6 +97,7 @@ def _L():
                 "ot_octree_copy_leaves": (st, [P, P, P, P]),
                 "ot_octree_centres": (st, [P, P, P]),
                 "ot_octree_set_map_level": (st, [P, i32, P]),
+                "ot_octree_get_map_level": (st, [P, P]),
                 "ot_octree_destroy": (st, [P]),
                 "ot_index_train": (st, [P, P, P]),
                 "ot_index_get_stats": (st, [P, P, i32]),
@@ -224,6 +225,12 @@ def ot_octree_copy_leaves(tree: Octree, stream=None):
 
 def ot_octree_set_map_level(tree: Octree, level: int, stream=None):
     _check(_L().ot_octree_set_map_level(tree.handle, level, _stream(stream)))
+
+
+def ot_octree_get_map_level(tree: Octree) -> int:
+    v = C.c_int()
+    _check(_L().ot_octree_get_map_level(tree.handle, C.byref(v)))
+    return v.value
 
 
 def ot_octree_centres(tree: Octree, out=None, stream=None):

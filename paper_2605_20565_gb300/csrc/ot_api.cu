@@ -177,6 +177,12 @@ ot_status ot_octree_copy_leaves(const ot_octree* t, uint64_t* d_keys, uint8_t* d
     return OT_OK;
 }
 
+ot_status ot_octree_get_map_level(const ot_octree* t, int* level) {
+    if (!t || !level) return OT_ERR_ARG;
+    *level = t->lmap_level;
+    return OT_OK;
+}
+
 ot_status ot_octree_set_map_level(ot_octree* t, int level, void* stream) {
     if (!t || level < 0 || level > 8) return OT_ERR_ARG;
     return finish_tree(t, (cudaStream_t)stream, level);
@@ -193,6 +199,7 @@ ot_status ot_octree_destroy(ot_octree* t) {
     if (t->d_level) cudaFree(t->d_level);
     if (t->d_lmap && t->d_lmap != t->d_pmap) cudaFree(t->d_lmap);
     if (t->d_pmap) cudaFree(t->d_pmap);
+    if (t->d_nodes) cudaFree(t->d_nodes);
     if (t->d_models) cudaFree(t->d_models);
     if (t->d_mids) cudaFree(t->d_mids);
     if (t->d_root) cudaFree(t->d_root);

@@ -2,7 +2,7 @@
 // kernel, point particles with trilinear interpolation), replayed from a CUDA graph.
 //
 // A graph replay first recomputes the pyramid of cell means of the field (refined trilinear
-// level-mates read it; pyr_level + 1 small launches), then runs the batch kernel.  Work is cut into tiles of 32 * tile points; warps take tiles from a global counter, the
+// level-mates read it; a few small launches), then runs the batch kernel.  Work is cut into tiles of 32 * tile points; warps take tiles from a global counter, the
 // expensive marker groups first (their tiles come first in the tile space), so uneven groups
 // balance across the SMs without a host round trip.  The counter is reset by a memset node
 // captured in the same graph.
@@ -135,7 +135,9 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     bool has_tri = false;
     for (int k = 0; k < n_groups; ++k) has_tri = has_tri || groups[k].kernel == OT_TRILINEAR;
     if (has_tri && (e = cudaMalloc(&b->d_pyr, pyramid_bytes(t, sizeof(float)))) != cudaSuccess) return fail(e);
-    b->kernels = has_tri ? 2 + t->pyr_level : 1;
+    int pyr_kernels = 1 + t->pyr_level;  // base level and the coarser levels
+    for (int k = 0; k < node_levels(t); ++k) pyr_kernels += t->node_cnt[k] > 0 ? 1 : 0;
+    b->kernels = has_tri ? 1 + pyr_kernels : 1;
     TreeView v = tree_view(t);
     const size_t smem = 0;
     void* kfn = search == OT_LEARNED ? (void*)k_batch<true> : (void*)k_batch<false>;

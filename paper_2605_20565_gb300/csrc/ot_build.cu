@@ -486,6 +486,8 @@ ot_status finish_tree(ot_octree* t, cudaStream_t s, int map_level) {
         k_lmap<<<grid1d(np, 256), 256, 0, s>>>(t->d_key, (int)t->n, Lp, np, t->d_pmap);
         count_launch();
         t->pyr_level = Lp;
+        ot_status st = build_node_lists(t, s);
+        if (st != OT_OK) return st;
     }
     if (t->d_lmap && t->d_lmap != t->d_pmap) cudaFree(t->d_lmap);
     t->d_lmap = nullptr;

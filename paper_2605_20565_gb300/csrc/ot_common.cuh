@@ -121,6 +121,12 @@ struct RootModel {
     float a, b; // linear root: y = a + b x
     float w1[MLP_H], b1[MLP_H], w2[MLP_H];
     float b2;
+    // the trained network in its piecewise-linear form (a 1 -> H ReLU -> 1 network is linear
+    // between the breakpoints -b1/w1 of its units): nknot sorted breakpoints inside (0, 1) and
+    // one line y = sa x + sb per segment.  Index building and queries both evaluate this form.
+    int nknot;
+    float knot[MLP_H];
+    float sa[MLP_H + 1], sb[MLP_H + 1];
 };
 
 struct TreeView {
@@ -184,13 +190,12 @@ __device__ __forceinline__ float key_to_x(uint64_t q) { return u64_to_float_rz(q
 __device__ __forceinline__ float root_predict(const RootModel& r, uint64_t q) {
     const float x = key_to_x(q);
     if (r.kind == OT_ROOT_LINEAR) return __fadd_rn(r.a, __fmul_rn(r.b, x));
-    float y = r.b2;
+    // segment: the number of breakpoints <= x (branch-free halving over the sorted breakpoints)
+    int s = 0;
 #pragma unroll
-    for (int k = 0; k < MLP_H; ++k) {
-        const float z = __fadd_rn(__fmul_rn(r.w1[k], x), r.b1[k]);
-        y = __fadd_rn(y, __fmul_rn(r.w2[k], fmaxf(z, 0.0f)));
-    }
-    return y;
+    for (int step = 32; step > 0; step >>= 1)
+        if (s + step <= r.nknot && r.knot[s + step - 1] <= x) s += step;
+    return __fadd_rn(__fmul_rn(r.sa[s], x), r.sb[s]);
 }
 __device__ __forceinline__ int root_route(const RootModel& r, uint64_t q) {
     float y = root_predict(r, q) * (float)r.n_models;

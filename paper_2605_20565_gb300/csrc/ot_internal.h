@@ -22,6 +22,11 @@ struct ot_octree {
     // d_lmap when the two levels agree): leaf ranges of the cells of the pyramid of means
     uint32_t* d_pmap = nullptr;
     int pyr_level = 0;
+    // refined cells of the node levels pyr_level+1 .. lmax-1, by first leaf: level
+    // pyr_level+1+k is d_nodes[node_off[k] .. node_off[k] + node_cnt[k])
+    int* d_nodes = nullptr;
+    int64_t node_off[ot::MAXLEVEL] = {};
+    int64_t node_cnt[ot::MAXLEVEL] = {};
     // learned index
     bool has_index = false;
     ot::RootModel root{};
@@ -104,6 +109,7 @@ int64_t pyramid_offset(int l);
 // Node means of levels pyr_level+1 .. lmax-1 follow the pyramid: node_levels arrays of n
 // entries (4 values each), indexed by the refined cell's first leaf.
 int node_levels(const ot_octree* t);
+ot_status build_node_lists(ot_octree* t, cudaStream_t s);
 size_t pyramid_bytes(const ot_octree* t, size_t elem);  // elem: sizeof the field type
 template <typename T> ot_status launch_pyramid(const ot_octree* t, const T* field, T* pyr, cudaStream_t s);
 

@@ -351,6 +351,36 @@ ot_status mlp_grad(const float* d_params, const float* d_x, const float* d_t, in
     return OT_OK;
 }
 
+// The trained 1 -> H ReLU -> 1 network as a piecewise-linear function on [0, 1): the units'
+// breakpoints -b1/w1 inside (0, 1), sorted, and on each segment the line through the units
+// active there (slope sum w2 w1, intercept b2 + sum w2 b1; a unit with w1 = 0 is a constant,
+// active when b1 > 0).  Computed in FP64 and rounded once.
+static void piecewise_form(RootModel& rm) {
+    std::vector<double> kn;
+    for (int k = 0; k < MLP_H; ++k)
+        if (rm.w1[k] != 0.0f) {
+            const double x = -(double)rm.b1[k] / (double)rm.w1[k];
+            if (x > 0.0 && x < 1.0) kn.push_back(x);
+        }
+    std::sort(kn.begin(), kn.end());
+    kn.erase(std::unique(kn.begin(), kn.end()), kn.end());
+    rm.nknot = (int)kn.size();
+    for (int k = 0; k < MLP_H; ++k) rm.knot[k] = k < rm.nknot ? (float)kn[k] : 2.0f;
+    for (int sgm = 0; sgm <= rm.nknot; ++sgm) {
+        const double lo = sgm == 0 ? 0.0 : kn[sgm - 1], hi = sgm == rm.nknot ? 1.0 : kn[sgm];
+        const double xm = 0.5 * (lo + hi);
+        double a = 0.0, b = (double)rm.b2;
+        for (int k = 0; k < MLP_H; ++k)
+            if ((double)rm.w1[k] * xm + (double)rm.b1[k] > 0.0) {
+                a += (double)rm.w2[k] * rm.w1[k];
+                b += (double)rm.w2[k] * rm.b1[k];
+            }
+        rm.sa[sgm] = (float)a;
+        rm.sb[sgm] = (float)b;
+    }
+    for (int sgm = rm.nknot + 1; sgm <= MLP_H; ++sgm) rm.sa[sgm] = rm.sb[sgm] = 0.0f;
+}
+
 ot_status train_index(ot_octree* t, const ot_index_params* prm, cudaStream_t s) {
     const int64_t n = t->n;
     const int M = prm->n_leaf_models;
@@ -429,6 +459,7 @@ ot_status train_index(ot_octree* t, const ot_index_params* prm, cudaStream_t s) 
             rm.w2[k] = p[2 * MLP_H + k];
         }
         rm.b2 = p[3 * MLP_H];
+        piecewise_form(rm);
     }
     const bool three = prm->n_mid_models > 0;
     rm.n_models = three ? prm->n_mid_models : M;

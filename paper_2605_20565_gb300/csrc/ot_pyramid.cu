@@ -1,10 +1,17 @@
-// ot_pyramid.cu -- pyramid of cell means of the field over the top levels of the tree (0 .. the
-// pyramid level Lc = min(lmax, 7)): the value a refined trilinear level-mate of level l <= Lc takes, the
-// volume-weighted mean of the leaves inside it (the coalescence average of Sec. 2.1.1), in one
-// load.  Level Lc: each map cell's mean (the covering leaf's value, or the volume-weighted mean
-// of its leaves, one warp per cell, fixed-order reduction); every coarser level: the mean of the
-// 8 children.  Recomputed whenever the field changes (every replay of a batch graph).
+// ot_pyramid.cu -- means of the field over refined cells: the value a refined trilinear
+// level-mate takes, the volume-weighted mean of the leaves inside it (the coalescence average
+// of Sec. 2.1.1), in one load whatever its level.
+//   Node means, levels Lc+1 .. lmax-1 (Lc = min(lmax, 7)): one array of N entries per level,
+//   indexed by the refined cell's first leaf (the leaf holding its anchor, which the level-mate
+//   search finds).  The refined cells of each level are listed once per octree; every
+//   recomputation takes each listed cell as the mean of its 8 children, deepest level first, a
+//   child being a leaf or a refined cell of the next level whose leaf count (kept in the 4th
+//   component, as integer bits) gives the start of the next child.
+//   Dense pyramid, levels 0 .. Lc: level Lc holds each cell's mean (the covering leaf's value,
+//   or the mean of its 8 children as above); every coarser level the mean of its 8 children.
+// Recomputed whenever the field changes (every replay of a batch graph).
 #include <algorithm>
+#include <vector>
 
 #include "ot_internal.h"
 
@@ -12,44 +19,68 @@ namespace ot {
 
 namespace {
 
+// bit-exact integer count in the 4th component
+__device__ __forceinline__ float count_bits(int c, float) { return __int_as_float(c); }
+__device__ __forceinline__ double count_bits(int c, double) { return __longlong_as_double((long long)c); }
+__device__ __forceinline__ int bits_count(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int bits_count(double v) { return (int)__double_as_longlong(v); }
+
+// Mean of the 8 children of the refined cell of level l whose first leaf is a, written to p
+// with the cell's leaf count.  child: node means of level l + 1 (null when l + 1 == lmax: every
+// child is a leaf).
 template <typename T>
-__global__ void __launch_bounds__(256) k_pyr_base(const uint64_t* __restrict__ key, const uint8_t* __restrict__ level,
-                                                  int n, const uint32_t* __restrict__ lmap, int Lc,
-                                                  const T* __restrict__ field, T* __restrict__ out) {
+__device__ __forceinline__ void children_mean(const uint8_t* __restrict__ level, int l, const T* __restrict__ field,
+                                              const T* __restrict__ child, int a, T* __restrict__ p) {
     using V = Vec4<T>;
-    const int lane = threadIdx.x & 31;
+    int pos = a;
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+    for (int ch = 0; ch < 8; ++ch) {
+        typename V::type f;
+        int step = 1;
+        if ((int)level[pos] == l + 1) {
+            f = V::load(field, pos);
+        } else {
+            f = V::load(child, pos);
+            step = bits_count(f.w);
+        }
+        s0 += f.x;
+        s1 += f.y;
+        s2 += f.z;
+        pos += step;
+    }
+    p[0] = s0 * T(0.125), p[1] = s1 * T(0.125), p[2] = s2 * T(0.125), p[3] = count_bits(pos - a, T(0));
+}
+
+// Level Lc of the pyramid: cell c holds leaves [pmap[c], pmap[c+1]); one leaf covers it when
+// that range has at most one leaf.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pyr_base(const uint32_t* __restrict__ pmap, const uint8_t* __restrict__ level,
+                                                  int n, int Lc, const T* __restrict__ field,
+                                                  const T* __restrict__ child, T* __restrict__ out) {
+    using V = Vec4<T>;
     const int64_t ncell = (int64_t)1 << (3 * Lc);
-    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = w0; c < ncell; c += nw) {
-        const int a = (int)lmap[c];
-        const int la = level[a];
-        T s0 = T(0), s1 = T(0), s2 = T(0);
-        if (la <= Lc) {  // one leaf covers the cell
-            if (lane == 0) {
-                const auto f = V::load(field, a);
-                s0 = f.x, s1 = f.y, s2 = f.z;
-            }
-        } else {  // the cell's leaves [a, e), weight 8^-(level - Lc)
-            const int e = c + 1 < ncell ? (int)lmap[c + 1] : n;
-            for (int b = a + lane; b < e; b += 32) {
-                const T vol = (T)exp2_neg(3 * ((int)level[b] - Lc));
-                const auto f = V::load(field, b);
-                s0 += vol * f.x;
-                s1 += vol * f.y;
-                s2 += vol * f.z;
-            }
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)pmap[c];
+        const int e = c + 1 < ncell ? (int)pmap[c + 1] : n;
+        T* p = out + 4 * c;
+        if (e - a <= 1) {
+            const auto f = V::load(field, a);
+            p[0] = f.x, p[1] = f.y, p[2] = f.z, p[3] = T(0);
+        } else {
+            children_mean<T>(level, Lc, field, child, a, p);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        }
-        if (lane == 0) {
-            T* p = out + 4 * c;
-            p[0] = s0, p[1] = s1, p[2] = s2, p[3] = T(0);
-        }
+    }
+}
+
+// Refined cells of level l listed in nodes[0, cnt): their means, at index first leaf.
+template <typename T>
+__global__ void __launch_bounds__(256) k_node_means(const int* __restrict__ nodes, int64_t cnt,
+                                                    const uint8_t* __restrict__ level, int l,
+                                                    const T* __restrict__ field, const T* __restrict__ child,
+                                                    T* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int a = nodes[i];
+        children_mean<T>(level, l, field, child, a, out + 4 * (int64_t)a);
     }
 }
 
@@ -70,43 +101,18 @@ __global__ void __launch_bounds__(256) k_pyr_up(const T* __restrict__ fine, T* _
     }
 }
 
-// bit-exact integer count in the 4th component
-__device__ __forceinline__ float count_bits(int c, float) { return __int_as_float(c); }
-__device__ __forceinline__ double count_bits(int c, double) { return __longlong_as_double((long long)c); }
-__device__ __forceinline__ int bits_count(float v) { return __float_as_int(v); }
-__device__ __forceinline__ int bits_count(double v) { return (int)__double_as_longlong(v); }
-
-// Refined cells of level l (l >= Lc + 1): the ones whose first leaf a has level > l and a key
-// aligned to level l.  child: node means of level l + 1 (unused when l + 1 == lmax: all
-// children are leaves).
-template <typename T>
-__global__ void __launch_bounds__(256) k_nodes(const uint64_t* __restrict__ key, const uint8_t* __restrict__ level,
-                                               int n, int l, const T* __restrict__ field, const T* __restrict__ child,
-                                               T* __restrict__ out) {
-    using V = Vec4<T>;
+// The leaves that start a refined cell of level l: level > l and key aligned to level l.
+__global__ void k_flag_nodes(const uint64_t* __restrict__ key, const uint8_t* __restrict__ level, int n, int l,
+                             uint32_t* __restrict__ flag) {
     const uint64_t mask = key_span(l) - 1;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int a = (int)i;
-        if ((int)level[a] <= l || (key[a] & mask) != 0) continue;
-        int pos = a;
-        T s0 = T(0), s1 = T(0), s2 = T(0);
-        for (int ch = 0; ch < 8; ++ch) {
-            typename V::type f;
-            int step = 1;
-            if ((int)level[pos] == l + 1) {
-                f = V::load(field, pos);
-            } else {
-                f = V::load(child, pos);
-                step = bits_count(f.w);
-            }
-            s0 += f.x;
-            s1 += f.y;
-            s2 += f.z;
-            pos += step;
-        }
-        T* p = out + 4 * (int64_t)a;
-        p[0] = s0 * T(0.125), p[1] = s1 * T(0.125), p[2] = s2 * T(0.125), p[3] = count_bits(pos - a, T(0));
-    }
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n; a += (int64_t)gridDim.x * blockDim.x)
+        flag[a] = ((int)level[a] > l && (key[a] & mask) == 0) ? 1u : 0u;
+}
+
+__global__ void k_scatter_nodes(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos, int n,
+                                int* __restrict__ out) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n; a += (int64_t)gridDim.x * blockDim.x)
+        if (flag[a]) out[pos[a]] = (int)a;
 }
 
 unsigned grid_n(int64_t n, int b) {
@@ -123,23 +129,68 @@ size_t pyramid_bytes(const ot_octree* t, size_t elem) {
     return elem * 4 * ((size_t)pyramid_offset(t->pyr_level + 1) + (size_t)node_levels(t) * (size_t)t->n) + 256;
 }
 
+// Lists, once per octree, the refined cells of every node level (by first leaf, in key order).
+ot_status build_node_lists(ot_octree* t, cudaStream_t s) {
+    const int nl = node_levels(t);
+    if (t->d_nodes) cudaFree(t->d_nodes);
+    t->d_nodes = nullptr;
+    if (nl == 0 || t->n == 0) return OT_OK;
+    uint32_t *flag = nullptr, *pos = nullptr, *tot = nullptr;
+    OT_CUDA(cudaMallocAsync(&flag, sizeof(uint32_t) * t->n, s));
+    OT_CUDA(cudaMallocAsync(&pos, sizeof(uint32_t) * t->n, s));
+    OT_CUDA(cudaMallocAsync(&tot, sizeof(uint32_t), s));
+    std::vector<int64_t> cnt(nl);
+    for (int k = 0; k < nl; ++k) {  // counts first, then one allocation
+        k_flag_nodes<<<grid_n(t->n, 256), 256, 0, s>>>(t->d_key, t->d_level, (int)t->n, t->pyr_level + 1 + k, flag);
+        count_launch();
+        ot_status st = scan_u32(flag, pos, t->n, tot, s);
+        if (st != OT_OK) return st;
+        uint32_t h = 0;
+        OT_CUDA(cudaMemcpyAsync(&h, tot, sizeof(h), cudaMemcpyDeviceToHost, s));
+        OT_CUDA(cudaStreamSynchronize(s));
+        cnt[k] = h;
+    }
+    int64_t total = 0;
+    for (int k = 0; k < nl; ++k) {
+        t->node_off[k] = total;
+        t->node_cnt[k] = cnt[k];
+        total += cnt[k];
+    }
+    OT_CUDA(cudaMalloc(&t->d_nodes, sizeof(int) * std::max<int64_t>(total, 1)));
+    for (int k = 0; k < nl; ++k) {
+        k_flag_nodes<<<grid_n(t->n, 256), 256, 0, s>>>(t->d_key, t->d_level, (int)t->n, t->pyr_level + 1 + k, flag);
+        ot_status st = scan_u32(flag, pos, t->n, nullptr, s);
+        if (st != OT_OK) return st;
+        k_scatter_nodes<<<grid_n(t->n, 256), 256, 0, s>>>(flag, pos, (int)t->n, t->d_nodes + t->node_off[k]);
+        count_launch(2);
+    }
+    cudaFreeAsync(flag, s);
+    cudaFreeAsync(pos, s);
+    cudaFreeAsync(tot, s);
+    OT_CUDA(cudaGetLastError());
+    OT_CUDA(cudaStreamSynchronize(s));
+    return OT_OK;
+}
+
 template <typename T>
 ot_status launch_pyramid(const ot_octree* t, const T* field, T* pyr, cudaStream_t s) {
     const int Lc = t->pyr_level;
-    const int64_t ncell = (int64_t)1 << (3 * Lc);
-    k_pyr_base<T><<<grid_n(ncell * 32, 256), 256, 0, s>>>(t->d_key, t->d_level, (int)t->n, t->d_pmap, Lc, field,
-                                                         pyr + 4 * pyramid_offset(Lc));
-    count_launch();
-    // node means below the pyramid, deepest level first
-    T* nodes = pyr + 4 * pyramid_offset(Lc + 1);
     const int nl = node_levels(t);
+    T* nodes = pyr + 4 * pyramid_offset(Lc + 1);
+    // node means, deepest level first (each reads the next level's)
     for (int k = nl - 1; k >= 0; --k) {
-        const int l = Lc + 1 + k;
         T* out = nodes + 4 * (int64_t)k * t->n;
         const T* child = k + 1 < nl ? out + 4 * (int64_t)t->n : nullptr;
-        k_nodes<T><<<grid_n(t->n, 256), 256, 0, s>>>(t->d_key, t->d_level, (int)t->n, l, field, child, out);
-        count_launch();
+        if (t->node_cnt[k] > 0) {
+            k_node_means<T><<<grid_n(t->node_cnt[k], 256), 256, 0, s>>>(t->d_nodes + t->node_off[k], t->node_cnt[k],
+                                                                       t->d_level, Lc + 1 + k, field, child, out);
+            count_launch();
+        }
     }
+    const int64_t ncell = (int64_t)1 << (3 * Lc);
+    k_pyr_base<T><<<grid_n(ncell, 256), 256, 0, s>>>(t->d_pmap, t->d_level, (int)t->n, Lc, field,
+                                                    nl > 0 ? nodes : nullptr, pyr + 4 * pyramid_offset(Lc));
+    count_launch();
     for (int l = Lc - 1; l >= 0; --l) {
         const int64_t nc = (int64_t)1 << (3 * l);
         k_pyr_up<T><<<grid_n(nc, 256), 256, 0, s>>>(pyr + 4 * pyramid_offset(l + 1), pyr + 4 * pyramid_offset(l), nc);

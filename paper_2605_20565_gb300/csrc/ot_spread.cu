@@ -165,6 +165,127 @@ __global__ void __launch_bounds__(256) k_spread_reduce(const uint64_t* __restric
     }
 }
 
+// Per-marker record of the sorted spreading, written once by the emit pass: the stencil's
+// per-axis weights, the marker's force times its volume factor, and the parity of the stencil's
+// first cell per axis (which fixes where a parent block's children sit in the stencil).
+template <typename T>
+struct __align__(16) MarkerRec {
+    T w[3][4];
+    T F[3];
+    int par;  // bit d: i0[d] & 1
+};
+
+// Emit pass: the marker's record and one pair per overlapping parent block, as k_spread_emit.
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_spread_emit_rec(TreeView t, const double* __restrict__ x,
+                                                         const double* __restrict__ y, const double* __restrict__ z,
+                                                         const T* __restrict__ F, const T* __restrict__ dV,
+                                                         int64_t n, uint64_t* __restrict__ pairs,
+                                                         MarkerRec<T>* __restrict__ recs) {
+    constexpr int W = Stencil<K>::W;
+    constexpr int PW = ParentSlots<K>::PW, PS = ParentSlots<K>::PS;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t* out = pairs + k * PS;
+        const uint64_t id0 = (uint64_t)k * PS;
+        for (int sl = 0; sl < PS; ++sl) out[sl] = (INVALID_HI << 32) | (id0 + sl);
+        uint64_t X[3];
+        if (!fixpoint3(x[k], y[k], z[k], X)) {
+            atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
+            continue;
+        }
+        int i0[3];
+        T w[3][W];
+        stencil_weights<K, T>(t.lmax, X, i0, w);
+        MarkerRec<T> r;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) r.w[d][a] = a < W ? w[d][a] : T(0);
+        const T vol = marker_volume(dV, k, t.lmax);
+        r.F[0] = F[k] * vol, r.F[1] = F[n + k] * vol, r.F[2] = F[2 * n + k] * vol;
+        r.par = (i0[0] & 1) | ((i0[1] & 1) << 1) | ((i0[2] & 1) << 2);
+        recs[k] = r;
+        bool ok = true;
+        visit_parents<K, false>(t, i0, [&](int a0, int bx, int by, int bz, const int*) {
+            if (a0 < 0) {
+                ok = false;
+                return;
+            }
+            const int sl = bx + PW * (by + PW * bz);
+            out[sl] = ((uint64_t)(uint32_t)a0 << 32) | (id0 + sl);
+        });
+        if (!ok) atomicOr(t.err, (unsigned)OT_DEV_STENCIL);
+    }
+}
+
+// Reduce pass over the sorted pairs (chunk ownership as k_spread_reduce), reading each pair's
+// marker record instead of recomputing its weights: a child (cx, cy, cz) of parent slot
+// (bx, by, bz) is stencil cell 2 b + c - parity on each axis.  Same products, same order: the
+// result is bit-identical to k_spread_reduce's.
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_spread_reduce_rec(const uint64_t* __restrict__ pairs, int64_t npairs,
+                                                           const MarkerRec<T>* __restrict__ recs,
+                                                           T* __restrict__ f) {
+    constexpr int W = Stencil<K>::W;
+    constexpr int PW = ParentSlots<K>::PW, PS = ParentSlots<K>::PS;
+    const int64_t nchunks = (npairs + RC - 1) / RC;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = c * RC;
+        const int64_t jend = min(j + RC, npairs);
+        if (j > 0) {  // the run in progress at the chunk start belongs to an earlier chunk
+            const uint32_t prev = (uint32_t)(pairs[j - 1] >> 32);
+            while (j < jend && (uint32_t)(pairs[j] >> 32) == prev) ++j;
+        }
+        while (j < jend) {
+            const uint32_t a0 = (uint32_t)(pairs[j] >> 32);
+            if (a0 == (uint32_t)INVALID_HI) break;  // invalid pairs sort last
+            T acc[8][3];
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) acc[ch][0] = acc[ch][1] = acc[ch][2] = T(0);
+            unsigned touched = 0;
+            for (; j < npairs; ++j) {
+                const uint64_t pj = pairs[j];
+                if ((uint32_t)(pj >> 32) != a0) break;
+                const uint32_t id = (uint32_t)pj;
+                const int64_t k = id / PS;
+                const int sl = (int)(id - (uint32_t)(k * PS));
+                const MarkerRec<T> r = recs[k];
+                const int b[3] = {sl % PW, (sl / PW) % PW, sl / (PW * PW)};
+                // per axis, the two children's stencil cells 2 b + e - parity (register selects)
+                T wa[3][2];
+                bool va[3][2];
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int cc = 2 * b[d] + e - ((r.par >> d) & 1);
+                        va[d][e] = cc >= 0 && cc < W;
+                        wa[d][e] = cc == 1 ? r.w[d][1] : cc == 2 ? r.w[d][2] : cc == 3 ? r.w[d][3] : r.w[d][0];
+                    }
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
+                    const int ex = ch & 1, ey = (ch >> 1) & 1, ez = (ch >> 2) & 1;
+                    if (!(va[0][ex] && va[1][ey] && va[2][ez])) continue;
+                    const T wt = wa[0][ex] * wa[1][ey] * wa[2][ez];
+                    acc[ch][0] += r.F[0] * wt;
+                    acc[ch][1] += r.F[1] * wt;
+                    acc[ch][2] += r.F[2] * wt;
+                    touched |= 1u << ch;
+                }
+            }
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) {
+                if (!((touched >> ch) & 1u)) continue;
+                T* fp = f + 4 * ((size_t)a0 + ch);
+                fp[0] += acc[ch][0];
+                fp[1] += acc[ch][1];
+                fp[2] += acc[ch][2];
+            }
+        }
+    }
+}
+
 template <typename Kern>
 unsigned grid_for(Kern k, int block, size_t smem, int64_t n) {
     int per_sm = 0;
@@ -179,6 +300,8 @@ ot_status prep(Kern k, size_t smem) {
     if (smem > 48 * 1024) OT_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return OT_OK;
 }
+
+size_t align_up(size_t b) { return (b + 255) & ~(size_t)255; }
 
 int leaf_bits(int64_t n) {
     int b = 1;
@@ -199,15 +322,16 @@ ot_status spread_sorted(const ot_octree* t, const double* x, const double* y, co
     TreeView v = tree_view(t);
     const size_t smem = 0;
     ot_status st;
-    auto ke = k_spread_emit<K>;
+    MarkerRec<T>* recs = reinterpret_cast<MarkerRec<T>*>(static_cast<char*>(rws) + align_up(radix_ws_bytes(np)));
+    auto ke = k_spread_emit_rec<T, K>;
     if ((st = prep(ke, smem)) != OT_OK) return st;
-    ke<<<grid_for(ke, 256, smem, n), 256, smem, s>>>(v, x, y, z, n, pairs);
+    ke<<<grid_for(ke, 256, smem, n), 256, smem, s>>>(v, x, y, z, F, dV, n, pairs, recs);
     count_launch();
     OT_CUDA(cudaGetLastError());
     const int bits = leaf_bits(t->n);
     if ((st = radix_sort_u64_ws(pairs, tmp, np, 32, 32 + bits, rws, s)) != OT_OK) return st;
-    auto kr = k_spread_reduce<T, K>;
-    kr<<<grid_for(kr, 256, 0, (np + RC - 1) / RC), 256, 0, s>>>(pairs, np, t->lmax, x, y, z, F, dV, n, f);
+    auto kr = k_spread_reduce_rec<T, K>;
+    kr<<<grid_for(kr, 256, 0, (np + RC - 1) / RC), 256, 0, s>>>(pairs, np, recs, f);
     count_launch();
     OT_CUDA(cudaGetLastError());
     return OT_OK;
@@ -218,7 +342,7 @@ ot_status spread_sorted(const ot_octree* t, const double* x, const double* y, co
 size_t spread_ws_bytes(const ot_octree* t, int kernel, int64_t n) {
     (void)t;
     const int64_t np = n * stencil_cells(kernel);
-    return (size_t)np * 16 + radix_ws_bytes(np) + 256;
+    return (size_t)np * 16 + align_up(radix_ws_bytes(np)) + (size_t)n * sizeof(MarkerRec<double>) + 256;
 }
 
 template <typename T>
