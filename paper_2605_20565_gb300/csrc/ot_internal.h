@@ -67,6 +67,10 @@ ot_status scan_u32(const uint32_t* d_in, uint32_t* d_out, int64_t n, uint32_t* d
 ot_status radix_sort_u64(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bit0, int bit1, cudaStream_t s);
 // Histogram + offset workspace bytes for radix_sort_u64_ws.
 size_t radix_ws_bytes(int64_t n);
+// Sort of the first *d_n (device value, <= n_max) keys with workspace of radix_ws_bytes(n_max)
+// bytes; *result is the buffer (d_keys or d_tmp) holding the sorted keys.
+ot_status radix_sort_u64_dn(uint64_t* d_keys, uint64_t* d_tmp, int64_t n_max, const uint32_t* d_n, int bit0,
+                            int bit1, void* ws, uint64_t** result, cudaStream_t s);
 // Same sort with caller-provided workspace (no allocation): ws of radix_ws_bytes(n) bytes.
 ot_status radix_sort_u64_ws(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bit0, int bit1, void* ws,
                             cudaStream_t s);

@@ -127,10 +127,12 @@ ot_status scan_u32(const uint32_t* d_in, uint32_t* d_out, int64_t n, uint32_t* d
 // ------------------------------------------------------------------------------------------
 constexpr int RT = 256, RI = 8, RTILE = RT * RI, RW = RT / 32;
 
+// d_n (nullable): the element count in device memory, at most n (tiles past it stay empty).
 __global__ void k_radix_hist(const uint64_t* __restrict__ in, int64_t n, int shift, uint32_t mask,
-                             uint32_t* __restrict__ hist, int ntiles) {
+                             uint32_t* __restrict__ hist, int ntiles, const uint32_t* __restrict__ d_n) {
     __shared__ uint32_t cnt[256];
     cnt[threadIdx.x] = 0;
+    if (d_n) n = min(n, (int64_t)*d_n);
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * RTILE;
 #pragma unroll
@@ -143,10 +145,13 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ in, int64_t n, int shi
 }
 
 __global__ void k_radix_scatter(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n, int shift,
-                                uint32_t mask, const uint32_t* __restrict__ offs, int ntiles) {
+                                uint32_t mask, const uint32_t* __restrict__ offs, int ntiles,
+                                const uint32_t* __restrict__ d_n) {
     __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_w[RW][256];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (d_n) n = min(n, (int64_t)*d_n);
+    if ((int64_t)blockIdx.x * RTILE >= n) return;  // block-uniform
     const unsigned lt = (1u << lane) - 1u;
     s_base[tid] = offs[(int64_t)tid * ntiles + blockIdx.x];
     const int64_t base = (int64_t)blockIdx.x * RTILE;
@@ -185,24 +190,38 @@ size_t radix_ws_bytes(int64_t n) {
 }
 
 static ot_status radix_passes(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bit0, int bit1, uint32_t* hist,
-                              uint32_t* offs, cudaStream_t s) {
+                              uint32_t* offs, cudaStream_t s, const uint32_t* d_n = nullptr,
+                              uint64_t** result = nullptr) {
     const int nt = (int)((n + RTILE - 1) / RTILE);
     uint64_t* src = d_keys;
     uint64_t* dst = d_tmp;
     for (int sh = bit0; sh < bit1; sh += 8) {
         const int nb = std::min(8, bit1 - sh);
         const uint32_t mask = (1u << nb) - 1u;
-        k_radix_hist<<<nt, RT, 0, s>>>(src, n, sh, mask, hist, nt);
+        k_radix_hist<<<nt, RT, 0, s>>>(src, n, sh, mask, hist, nt, d_n);
         count_launch();
         ot_status st = scan_u32(hist, offs, (int64_t)256 * nt, nullptr, s);
         if (st != OT_OK) return st;
-        k_radix_scatter<<<nt, RT, 0, s>>>(src, dst, n, sh, mask, offs, nt);
+        k_radix_scatter<<<nt, RT, 0, s>>>(src, dst, n, sh, mask, offs, nt, d_n);
         count_launch();
         std::swap(src, dst);
     }
-    if (src != d_keys) OT_CUDA(cudaMemcpyAsync(d_keys, src, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+    if (result)
+        *result = src;  // the caller takes the sorted keys where the last pass left them
+    else if (src != d_keys)
+        OT_CUDA(cudaMemcpyAsync(d_keys, src, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
     OT_CUDA(cudaGetLastError());
     return OT_OK;
+}
+
+ot_status radix_sort_u64_dn(uint64_t* d_keys, uint64_t* d_tmp, int64_t n_max, const uint32_t* d_n, int bit0,
+                            int bit1, void* ws, uint64_t** result, cudaStream_t s) {
+    *result = d_keys;
+    if (n_max <= 1 || bit1 <= bit0) return OT_OK;
+    const int64_t nt = (n_max + RTILE - 1) / RTILE;
+    uint32_t* hist = static_cast<uint32_t*>(ws);
+    uint32_t* offs = hist + 256 * nt;
+    return radix_passes(d_keys, d_tmp, n_max, bit0, bit1, hist, offs, s, d_n, result);
 }
 
 ot_status radix_sort_u64(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bit0, int bit1, cudaStream_t s) {
@@ -342,11 +361,11 @@ ot_status radix_sort_u64_noalloc(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, i
     for (int sh = bit0; sh < bit1; sh += 8) {
         const int nb = std::min(8, bit1 - sh);
         const uint32_t mask = (1u << nb) - 1u;
-        k_radix_hist<<<nt, RT, 0, s>>>(src, n, sh, mask, hist, nt);
+        k_radix_hist<<<nt, RT, 0, s>>>(src, n, sh, mask, hist, nt, nullptr);
         count_launch();
         ot_status st = scan_u32_noalloc(hist, offs, (int64_t)256 * nt, stmp, s);
         if (st != OT_OK) return st;
-        k_radix_scatter<<<nt, RT, 0, s>>>(src, dst, n, sh, mask, offs, nt);
+        k_radix_scatter<<<nt, RT, 0, s>>>(src, dst, n, sh, mask, offs, nt, nullptr);
         count_launch();
         std::swap(src, dst);
     }

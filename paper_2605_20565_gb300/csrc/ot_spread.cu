@@ -175,19 +175,43 @@ struct __align__(16) MarkerRec {
     int par;  // bit d: i0[d] & 1
 };
 
-// Emit pass: the marker's record and one pair per overlapping parent block, as k_spread_emit.
+// Parent blocks overlapping a marker's stencil (2 or 3 per axis for Peskin-4, by the parity
+// of the stencil's first cell); 0 outside the cube.
+template <int K>
+__global__ void __launch_bounds__(256) k_spread_count(const double* __restrict__ x, const double* __restrict__ y,
+                                                      const double* __restrict__ z, int64_t n, int lmax,
+                                                      uint32_t* __restrict__ cnt) {
+    constexpr int W = Stencil<K>::W;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t X[3];
+        uint32_t c = 0;
+        if (fixpoint3(x[k], y[k], z[k], X)) {
+            c = 1;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int i0 = Stencil<K>::first((int)fix_cell(X[d], lmax), fix_upper_half(X[d], lmax) ? 1 : 0);
+                c *= (uint32_t)(floordiv2(i0 + W - 1) - floordiv2(i0) + 1);
+            }
+        }
+        cnt[k] = c;
+    }
+}
+
+// Emit pass: the marker's record and, from offset off[k], one pair per overlapping parent block
+// in slot order (a block outside the cube or not refined to the finest level gets an invalid
+// pair, which sorts last).
 template <typename T, int K>
 __global__ void __launch_bounds__(256) k_spread_emit_rec(TreeView t, const double* __restrict__ x,
                                                          const double* __restrict__ y, const double* __restrict__ z,
                                                          const T* __restrict__ F, const T* __restrict__ dV,
-                                                         int64_t n, uint64_t* __restrict__ pairs,
+                                                         int64_t n, const uint32_t* __restrict__ off,
+                                                         uint64_t* __restrict__ pairs,
                                                          MarkerRec<T>* __restrict__ recs) {
     constexpr int W = Stencil<K>::W;
     constexpr int PW = ParentSlots<K>::PW, PS = ParentSlots<K>::PS;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t* out = pairs + k * PS;
+        uint64_t* out = pairs + off[k];
         const uint64_t id0 = (uint64_t)k * PS;
-        for (int sl = 0; sl < PS; ++sl) out[sl] = (INVALID_HI << 32) | (id0 + sl);
         uint64_t X[3];
         if (!fixpoint3(x[k], y[k], z[k], X)) {
             atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
@@ -206,13 +230,11 @@ __global__ void __launch_bounds__(256) k_spread_emit_rec(TreeView t, const doubl
         r.par = (i0[0] & 1) | ((i0[1] & 1) << 1) | ((i0[2] & 1) << 2);
         recs[k] = r;
         bool ok = true;
+        int m = 0;
         visit_parents<K, false>(t, i0, [&](int a0, int bx, int by, int bz, const int*) {
-            if (a0 < 0) {
-                ok = false;
-                return;
-            }
             const int sl = bx + PW * (by + PW * bz);
-            out[sl] = ((uint64_t)(uint32_t)a0 << 32) | (id0 + sl);
+            if (a0 < 0) ok = false;
+            out[m++] = ((a0 < 0 ? INVALID_HI : (uint64_t)(uint32_t)a0) << 32) | (id0 + sl);
         });
         if (!ok) atomicOr(t.err, (unsigned)OT_DEV_STENCIL);
     }
@@ -223,11 +245,13 @@ __global__ void __launch_bounds__(256) k_spread_emit_rec(TreeView t, const doubl
 // (bx, by, bz) is stencil cell 2 b + c - parity on each axis.  Same products, same order: the
 // result is bit-identical to k_spread_reduce's.
 template <typename T, int K>
-__global__ void __launch_bounds__(256) k_spread_reduce_rec(const uint64_t* __restrict__ pairs, int64_t npairs,
+__global__ void __launch_bounds__(256) k_spread_reduce_rec(const uint64_t* __restrict__ pairs,
+                                                           const uint32_t* __restrict__ d_np,
                                                            const MarkerRec<T>* __restrict__ recs,
                                                            T* __restrict__ f) {
     constexpr int W = Stencil<K>::W;
     constexpr int PW = ParentSlots<K>::PW, PS = ParentSlots<K>::PS;
+    const int64_t npairs = *d_np;
     const int64_t nchunks = (npairs + RC - 1) / RC;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
          c += (int64_t)gridDim.x * blockDim.x) {
@@ -322,16 +346,30 @@ ot_status spread_sorted(const ot_octree* t, const double* x, const double* y, co
     TreeView v = tree_view(t);
     const size_t smem = 0;
     ot_status st;
-    MarkerRec<T>* recs = reinterpret_cast<MarkerRec<T>*>(static_cast<char*>(rws) + align_up(radix_ws_bytes(np)));
+    char* p = static_cast<char*>(rws) + align_up(radix_ws_bytes(np));
+    MarkerRec<T>* recs = reinterpret_cast<MarkerRec<T>*>(p);
+    p += align_up((size_t)n * sizeof(MarkerRec<double>));
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(p);
+    p += align_up((size_t)n * sizeof(uint32_t));
+    uint32_t* off = reinterpret_cast<uint32_t*>(p);
+    p += align_up((size_t)n * sizeof(uint32_t));
+    uint32_t* d_np = reinterpret_cast<uint32_t*>(p);
+    auto kc = k_spread_count<K>;
+    kc<<<grid_for(kc, 256, 0, n), 256, 0, s>>>(x, y, z, n, t->lmax, cnt);
+    count_launch();
+    if ((st = scan_u32(cnt, off, n, d_np, s)) != OT_OK) return st;
     auto ke = k_spread_emit_rec<T, K>;
     if ((st = prep(ke, smem)) != OT_OK) return st;
-    ke<<<grid_for(ke, 256, smem, n), 256, smem, s>>>(v, x, y, z, F, dV, n, pairs, recs);
+    ke<<<grid_for(ke, 256, smem, n), 256, smem, s>>>(v, x, y, z, F, dV, n, off, pairs, recs);
     count_launch();
     OT_CUDA(cudaGetLastError());
-    const int bits = leaf_bits(t->n);
-    if ((st = radix_sort_u64_ws(pairs, tmp, np, 32, 32 + bits, rws, s)) != OT_OK) return st;
+    // a parent block is identified by its first child leaf a0; blocks are 8 consecutive leaves,
+    // so a0 >> 3 is distinct for distinct blocks and keeps their order: sorting on it skips 3 bits
+    const int bits = leaf_bits(t->n + 8);
+    uint64_t* sorted = pairs;
+    if ((st = radix_sort_u64_dn(pairs, tmp, np, d_np, 35, 32 + bits, rws, &sorted, s)) != OT_OK) return st;
     auto kr = k_spread_reduce_rec<T, K>;
-    kr<<<grid_for(kr, 256, 0, (np + RC - 1) / RC), 256, 0, s>>>(pairs, np, recs, f);
+    kr<<<grid_for(kr, 256, 0, (np + RC - 1) / RC), 256, 0, s>>>(sorted, d_np, recs, f);
     count_launch();
     OT_CUDA(cudaGetLastError());
     return OT_OK;
@@ -342,7 +380,8 @@ ot_status spread_sorted(const ot_octree* t, const double* x, const double* y, co
 size_t spread_ws_bytes(const ot_octree* t, int kernel, int64_t n) {
     (void)t;
     const int64_t np = n * stencil_cells(kernel);
-    return (size_t)np * 16 + align_up(radix_ws_bytes(np)) + (size_t)n * sizeof(MarkerRec<double>) + 256;
+    return (size_t)np * 16 + align_up(radix_ws_bytes(np)) + align_up((size_t)n * sizeof(MarkerRec<double>)) +
+           2 * align_up((size_t)n * sizeof(uint32_t)) + 512;
 }
 
 template <typename T>
