@@ -269,7 +269,9 @@ typedef struct {
 typedef struct {
     int block;       /* threads per block: 64 .. 256, multiple of 32 (default 256)          */
     int tile;        /* 32-point rows per work item taken from the queue: 1 .. 64 (default 4) */
-    int blocks_per_sm; /* resident blocks per SM, capped by occupancy (0: the occupancy max) */
+    int blocks_per_sm; /* resident blocks per SM, capped by occupancy (0: the occupancy max);
+                          2 also selects the kernel compiled for 2 blocks per SM (more
+                          registers per thread, no spills) instead of 3                    */
 } ot_launch;
 
 /* Create a batch over groups (copied) reading d_field (float4 per leaf).  search selects

@@ -43,8 +43,10 @@ struct BatchArgs {
     int tile; // points per lane per tile
 };
 
-template <bool LEARNED>
-__global__ void __launch_bounds__(256) k_batch(TreeView t, BatchArgs a, const float* __restrict__ field,
+// MINB: the register budget (blocks of 256 resident per SM it is compiled for); 3 is the
+// default, 2 trades occupancy for no register spills and is picked with blocks_per_sm = 2.
+template <bool LEARNED, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_batch(TreeView t, BatchArgs a, const float* __restrict__ field,
                                                const float* __restrict__ pyr, unsigned* __restrict__ counter) {
     __shared__ WarpQueue s_queue[256 / 32];
     __shared__ RootModel s_root;
@@ -140,7 +142,9 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     b->kernels = has_tri ? 1 + pyr_kernels : 1;
     TreeView v = tree_view(t);
     const size_t smem = 0;
-    void* kfn = search == OT_LEARNED ? (void*)k_batch<true> : (void*)k_batch<false>;
+    const bool two = launch && launch->blocks_per_sm == 2;
+    void* kfn = search == OT_LEARNED ? (two ? (void*)k_batch<true, 2> : (void*)k_batch<true, 3>)
+                                     : (two ? (void*)k_batch<false, 2> : (void*)k_batch<false, 3>);
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return fail(e);

@@ -477,6 +477,34 @@ ot_status leaf_centres(const ot_octree* t, double* d_xyz, cudaStream_t s) {
     return OT_OK;
 }
 
+// Descriptor of every level-map cell of level L (see desc_leaf): the refined children and
+// grandchildren of an uncovered cell, valid when no leaf of the cell is deeper than L + 3.
+__global__ void k_desc(const uint64_t* __restrict__ key, const uint8_t* __restrict__ level, int n,
+                       const uint32_t* __restrict__ lmap, int L, int64_t ncell, uint4* __restrict__ desc) {
+    GRID_STRIDE(c, ncell) {
+        const int a = (int)lmap[c];
+        const int e = c + 1 < ncell ? (int)lmap[c + 1] : n;
+        uint32_t m1 = 0, valid = 1;
+        uint64_t m2 = 0;
+        if (e - a <= 1) {
+            valid = 0;  // covered: the map answers
+        } else {
+            for (int b = a; b < e; ++b) {
+                const int lb = level[b];
+                if (lb > L + 3) {
+                    valid = 0;
+                    break;
+                }
+                const uint64_t kb = key[b];
+                const int c1 = (int)(kb >> (3 * (MAXLEVEL - L - 1))) & 7;
+                if (lb >= L + 2) m1 |= 1u << c1;
+                if (lb >= L + 3) m2 |= 1ULL << (8 * c1 + ((int)(kb >> (3 * (MAXLEVEL - L - 2))) & 7));
+            }
+        }
+        desc[c] = valid ? make_uint4((uint32_t)m2, (uint32_t)(m2 >> 32), m1 | DESC_VALID, 0u) : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
 ot_status finish_tree(ot_octree* t, cudaStream_t s, int map_level) {
     const int L = map_level >= 0 ? std::min(map_level, t->lmax) : std::min(t->lmax, 7);
     const int Lp = std::min(t->lmax, 7);
@@ -500,6 +528,14 @@ ot_status finish_tree(ot_octree* t, cudaStream_t s, int map_level) {
         count_launch();
     }
     t->lmap_level = L;
+    if (t->d_desc) cudaFree(t->d_desc);
+    t->d_desc = nullptr;
+    if (L + 1 <= t->lmax && L + 1 < MAXLEVEL) {
+        const int64_t ncell = (int64_t)1 << (3 * L);
+        OT_CUDA(cudaMalloc(&t->d_desc, sizeof(uint4) * ncell));
+        k_desc<<<grid1d(ncell, 256), 256, 0, s>>>(t->d_key, t->d_level, (int)t->n, t->d_lmap, L, ncell, t->d_desc);
+        count_launch();
+    }
     if (!t->d_err) {
         OT_CUDA(cudaMalloc(&t->d_err, 64));
         OT_CUDA(cudaMemsetAsync(t->d_err, 0, 64, s));
@@ -519,6 +555,7 @@ TreeView tree_view(const ot_octree* t) {
     v.lmax = t->lmax;
     v.lmap = t->d_lmap;
     v.lmap_level = t->lmap_level;
+    v.desc = t->d_desc;
     v.pyr_level = t->pyr_level;
     v.root = t->d_root;
     v.models = t->d_models;

@@ -138,6 +138,9 @@ struct TreeView {
     // top levels of the tree, staged as a dense table)
     const uint32_t* __restrict__ lmap;
     int lmap_level;
+    // per level-map cell, the shape of its subtree when it is at most 3 levels deep (see
+    // desc_leaf); null when not built
+    const uint4* __restrict__ desc;
     int pyr_level;  // deepest level of the pyramid of cell means (refined trilinear level-mates)
     // learned search: root -> (optional mid models) -> leaf models
     const RootModel* __restrict__ root;  // device copy
@@ -175,11 +178,37 @@ __device__ __forceinline__ void map_range(const TreeView& t, uint64_t q, int& a,
 // Plain host search (Algorithm 1's answer, upper bound - 1): the level map gives the leaf
 // directly for a cell covered by one leaf, else the cell's range of leaves, which a
 // branch-free binary search finishes (key[a] <= q: a holds the cell's anchor).
+// Leaf holding key q inside an uncovered level-map cell (level L, first leaf a) whose subtree is
+// at most 3 levels deep, from the cell's descriptor d: m1 (d.z bits 0-7) marks the refined
+// children (level L+1, Morton child order), byte i of m2 (d.x | d.y << 32) the refined
+// grandchildren of child i; every deeper cell is a leaf.  A refined child holds 8 + 7 popc(its
+// m2 byte) leaves, so the leaves before child c1 number c1 + 7 popc(m1 below c1) + 7 popc(m2
+// bytes below c1); inside a refined child the same count one level down, and inside a refined
+// grandchild the great-grandchild's index.
+__device__ __forceinline__ int desc_leaf(uint4 d, int L, uint64_t q, int a) {
+    const uint32_t m1 = d.z & 0xFFu;
+    const uint64_t m2 = ((uint64_t)d.y << 32) | d.x;
+    const int c1 = (int)(q >> (3 * (MAXLEVEL - L - 1))) & 7;
+    const uint64_t low = c1 ? (~0ULL >> (64 - 8 * c1)) : 0ULL;
+    int idx = a + c1 + 7 * __popc(m1 & ((1u << c1) - 1u)) + 7 * __popcll(m2 & low);
+    if ((m1 >> c1) & 1u) {
+        const int c2 = (int)(q >> (3 * (MAXLEVEL - L - 2))) & 7;
+        const uint32_t g = (uint32_t)(m2 >> (8 * c1)) & 0xFFu;
+        idx += c2 + 7 * __popc(g & ((1u << c2) - 1u));
+        if ((g >> c2) & 1u) idx += (int)(q >> (3 * (MAXLEVEL - L - 3))) & 7;
+    }
+    return idx;
+}
+constexpr uint32_t DESC_VALID = 0x100u;
+
+// The cell's map entries and its descriptor are loaded together (one round trip).
 __device__ __forceinline__ int search_plain(const TreeView& t, uint64_t q) {
-    int a, e;
-    bool covered;
-    map_range(t, q, a, e, covered);
-    if (covered) return a;
+    const uint32_t c = (uint32_t)(q >> (3 * (MAXLEVEL - t.lmap_level)));
+    const int a = (int)t.lmap[c];
+    const int e = (c + 1 < (1u << (3 * t.lmap_level))) ? (int)t.lmap[c + 1] : t.n;
+    const uint4 d = t.desc ? __ldg(t.desc + c) : make_uint4(0u, 0u, 0u, 0u);
+    if (e - a <= 1) return a;
+    if (d.z & DESC_VALID) return desc_leaf(d, t.lmap_level, q, a);
     return search_range(t.key, a, e - a, q);
 }
 

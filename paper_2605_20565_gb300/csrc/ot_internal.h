@@ -18,6 +18,7 @@ struct ot_octree {
     // level map: the leaf holding the anchor of every cell of level lmap_level
     uint32_t* d_lmap = nullptr;
     int lmap_level = 0;
+    uint4* d_desc = nullptr;  // subtree descriptor of every level-map cell
     // the same table at the pyramid level min(lmax, 7), fixed for the octree's life (it is
     // d_lmap when the two levels agree): leaf ranges of the cells of the pyramid of means
     uint32_t* d_pmap = nullptr;

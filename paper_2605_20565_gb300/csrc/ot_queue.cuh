@@ -38,13 +38,15 @@ __device__ __forceinline__ void stage_root(const TreeView& t, RootModel& s_root)
     __syncthreads();
 }
 
-// Level-map cell of key q: the leaf holding its anchor (a) and the next cell's (e).  The cell
-// is covered by one leaf -- leaf a, the answer -- exactly when e - a <= 1 (a refined cell holds
-// at least 8 leaves, its first one starting at its anchor).
-__device__ __forceinline__ void map_cell_range(const TreeView& t, uint64_t q, int& a, int& e) {
+// Level-map lookup of key q: the leaf holding its cell's anchor (a) and the next cell's (e).
+// The cell is covered by one leaf -- leaf a, the answer -- exactly when e - a <= 1 (a refined
+// cell holds at least 8 leaves, its first one starting at its anchor).  Returns true with the
+// answer in a when covered, else false with the cell's leaf range [a, e) to search.
+__device__ __forceinline__ bool map_lookup(const TreeView& t, uint64_t q, int& a, int& e) {
     const uint32_t cell = (uint32_t)(q >> (3 * (MAXLEVEL - t.lmap_level)));
     a = (int)t.lmap[cell];
     e = cell < (1u << (3 * t.lmap_level)) - 1u ? (int)t.lmap[cell + 1] : t.n;
+    return e - a <= 1;
 }
 
 // Appends a task for every lane with need set (warp-wide call); returns the lane's task index
@@ -64,7 +66,8 @@ __device__ __forceinline__ int push_task(WarpQueue& w, int& n, bool need, uint64
 // Runs the warp's ntask tasks (warp-wide call).  Each step, a lane without a task takes the
 // next one, and every lane with a task advances it by one step of at most one memory round
 // trip:
-//   plain:   halving probes over the cell's leaves;
+//   plain:   the cell's subtree descriptor, which answers directly when the subtree is at most
+//            3 levels deep; else halving probes over the cell's leaves;
 //   learned: route (root model from shared memory, then the middle model's load), leaf model
 //            load and window (its prediction widened by the stored error bounds, clamped to
 //            the cell), halving probes over the window, and the check key[a] <= q < key[a+1];
@@ -72,7 +75,7 @@ __device__ __forceinline__ int push_task(WarpQueue& w, int& n, bool need, uint64
 // A finished task's answer (the last index in its range whose key is <= q) replaces its lo.
 // (Routing all tasks side by side before the loop was measured slower: it adds a round trip
 // and registers.)
-enum { ST_ROUTE = 0, ST_MODEL = 1, ST_PROBE = 2, ST_CHECK = 3, ST_DONE = 4 };
+enum { ST_ROUTE = 0, ST_MODEL = 1, ST_PROBE = 2, ST_CHECK = 3, ST_DONE = 4, ST_DESC = 5 };
 
 template <bool LEARNED>
 __device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& root, WarpQueue& w, int ntask,
@@ -94,14 +97,22 @@ __device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& ro
                 q = w.q[idx];
                 lo = clo = w.lo[idx];
                 len = clen = w.len[idx];
-                st = LEARNED ? ST_ROUTE : ST_PROBE;
+                st = LEARNED ? ST_ROUTE : (t.desc ? ST_DESC : ST_PROBE);
                 checked = false;
             }
         }
         next += __popc(m);
         if (!__any_sync(FULL, cur >= 0)) break;
         if (cur < 0) continue;
-        if (LEARNED && st == ST_ROUTE) {
+        if (!LEARNED && st == ST_DESC) {
+            const uint4 d = __ldg(t.desc + (q >> (3 * (MAXLEVEL - t.lmap_level))));
+            if (d.z & DESC_VALID) {
+                lo = desc_leaf(d, t.lmap_level, q, lo);
+                st = ST_DONE;
+            } else {
+                st = ST_PROBE;
+            }
+        } else if (LEARNED && st == ST_ROUTE) {
             j = root_route(root, q);
             if (t.mids) j = (int)(((int64_t)leaf_predict(t.mids[j], q, t.n) * t.n_leaf) / t.n);
             st = ST_MODEL;
@@ -172,8 +183,7 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
     {
         const uint64_t q = morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32));
         int ca = 0, ce = 0;
-        if (ok && h < 0) map_cell_range(t, q, ca, ce);
-        const bool need = ok && h < 0 && ce - ca > 1;
+        const bool need = ok && h < 0 && !map_lookup(t, q, ca, ce);
         if (ok && h < 0 && !need) h = ca;
         if (__any_sync(FULL, need)) {
             int n = 0;
@@ -232,9 +242,9 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
     }
     if (!ok) self_m = 0xffu, sib_m = 0u;
     // Stage 2: the guessed siblings' keys (a match proves the guess: keys are unique) and, in
-    // the same round of loads, the level-map cells of the other level-mates (a cell covered by
-    // one leaf settles its level-mate).  Stage 3: a failed guess's cell.  Stage 4: the rest
-    // become tasks of the warp's list.
+    // the same round of loads, the level-map lookups of the other level-mates (a covered cell
+    // settles its level-mate).  Stage 3: a failed guess's lookup.  Stage 4: the rest become
+    // tasks of the warp's list.
     unsigned pend_m = ~self_m & 0xffu;
     int ca[8], ce[8];
     {
@@ -244,27 +254,23 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
             ca[corner] = 0;
             ce[corner] = 0;
             gk[corner] = 0;
-            if ((sib_m >> corner) & 1u)
+            if ((sib_m >> corner) & 1u) {
                 gk[corner] = ldg_key(t.key + gi[corner]);
-            else if ((pend_m >> corner) & 1u)
-                map_cell_range(t, anc[corner], ca[corner], ce[corner]);
+            } else if ((pend_m >> corner) & 1u) {
+                if (map_lookup(t, anc[corner], ca[corner], ce[corner])) {
+                    a[corner] = ca[corner];
+                    pend_m &= ~(1u << corner);
+                }
+            }
         }
 #pragma unroll
         for (int corner = 1; corner < 8; ++corner) {
             if (!((sib_m >> corner) & 1u)) continue;
-            if (gk[corner] == anc[corner]) {
-                a[corner] = gi[corner];
+            if (gk[corner] == anc[corner] || map_lookup(t, anc[corner], ca[corner], ce[corner])) {
+                a[corner] = gk[corner] == anc[corner] ? gi[corner] : ca[corner];
                 pend_m &= ~(1u << corner);
-            } else {
-                map_cell_range(t, anc[corner], ca[corner], ce[corner]);
             }
         }
-#pragma unroll
-        for (int corner = 1; corner < 8; ++corner)
-            if (((pend_m >> corner) & 1u) && ce[corner] - ca[corner] <= 1) {
-                a[corner] = ca[corner];
-                pend_m &= ~(1u << corner);
-            }
     }
     if (__any_sync(FULL, pend_m != 0u)) {
         int n = 0;

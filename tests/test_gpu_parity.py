@@ -83,6 +83,18 @@ def test_random_octrees_bit_exact(ot, seed, full):
     tree = ot.ot_octree_build(sph, lmin, lmax, full)
     k, l = leaves_np(ot, tree)
     assert np.array_equal(k, ko) and np.array_equal(l, lo)
+    # every level-map level (subtree descriptors of every depth, and the search fallback)
+    # locates and interpolates exactly as the oracle
+    P = special_points(ko, lo, rng, 3000)
+    ref = oracle.locate_ub(ko, lo, *P.T)
+    Pi = P[ref >= 0]
+    f32 = rng.normal(size=(ko.size, 4)).astype(np.float32)
+    uref = oracle.interp_trilinear(ko, lo, f32.astype(np.float64), *Pi.T, ref[ref >= 0])
+    for L in range(0, min(lmax, 8) + 1):
+        ot.ot_octree_set_map_level(tree, L)
+        assert np.array_equal(ot.ot_locate(tree, *pts(P.T)).cpu().numpy(), ref), L
+        u = ot.ot_interpolate(tree, ot.OT_TRILINEAR, *pts(Pi.T), dev(f32)).cpu().numpy()
+        assert rel_err(u, uref) <= TOL32, L
 
 
 def test_uniform_and_single_leaf_trees(ot):
