@@ -108,6 +108,37 @@ def describe(w, n_leaves, search):
     }
 
 
+BATCH_SOURCES = ("ot_batch.cu", "ot_queue.cuh", "ot_points.cuh", "ot_common.cuh")
+
+
+def kernel_sources_hash() -> str:
+    """SHA-256 of the batch kernel's sources, to tell whether a stored ncu capture still applies."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in BATCH_SOURCES:
+        with open(os.path.join(ROOT, "paper_2605_20565_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def batch_traffic(workload: str, form: str, map_level: int):
+    """DRAM bytes of one batch launch from the committed ncu summary, when it was taken on this
+    workload, form and level map with the current kernel sources; else (None, reason)."""
+    path = os.path.join(ROOT, "profiles", f"k_batch_{workload.split('_l')[0]}_traffic.txt")
+    if not os.path.exists(path):
+        return None, "no capture"
+    d = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            d[k.strip()] = v.strip()
+    if d.get("workload") != workload or d.get("form") != form or int(d.get("map_level", -1)) != map_level:
+        return None, "capture taken on another workload, form or level map"
+    if d.get("kernel_sources_sha256") != kernel_sources_hash():
+        return None, "kernel changed since the capture"
+    return int(d["bytes_per_launch"]), os.path.relpath(path, ROOT)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -480,14 +511,9 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     alg_bytes = npts * BYTES_PER_POINT + n_leaves * BYTES_PER_LEAF
     achieved = alg_bytes / (batch_ms / 1e3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "k_batch_traffic.json")
-    if os.path.exists(prof):
-        d = json.load(open(prof))
-        if d.get("workload") == w.name and d.get("search") == args.search and d.get("valid", False):
-            traffic = d.get("bytes_per_launch")
+    traffic, traffic_src = batch_traffic(w.name, chosen, forms_cfg[chosen][1])
     roof = {"bound": "hbm", "kernel": "k_batch (locate + interpolate, persistent, graph)", "achieved": achieved,
-            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(alg_bytes),
             "bytes_rule": f"{BYTES_PER_POINT} B/point + {BYTES_PER_LEAF} B/leaf"}
 
