@@ -66,6 +66,7 @@ def _L():
                 "or_mlp_forward1": (dbl, [P, dbl]),
                 "or_mlp_loss_grad": (dbl, [P, P, P, i64, P]),
                 "or_advect_ab2": (None, [P, P, P, P, P, i64, dbl, dbl, dbl, i32, i32]),
+                "or_ibm_mdf": (i64, [P, P, i64, i32, i32, P, P, P, P, P, P, i64, dbl, dbl, i32, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -200,6 +201,25 @@ def interp_trilinear(keys, levels, field, x, y, z, host):
     u = np.empty((3, x.size), np.float64)
     _L().or_interp_trilinear(_p(k), _p(l), k.size, _p(f), _p(x), _p(y), _p(z), _p(h), x.size, _p(u))
     return u
+
+
+def ibm_mdf(keys, levels, lmax, kernel, u_star, X, U, rho, dt, n_iter, dV=None):
+    """Multi-direct forcing (Sec. 2.2): (u (N, 4), f (N, 4), slip (n_iter + 1,), skipped cells).
+    X, U: (3, nm) marker positions and prescribed velocities; u_star: (N, 4)."""
+    k, l = _c(keys, np.uint64), _c(levels, np.uint8)
+    us = _c(u_star, np.float64).reshape(-1, 4)
+    x, y, z = _pts(*np.asarray(X, np.float64))
+    Uc = _c(U, np.float64).reshape(3, -1)
+    dvp = None
+    if dV is not None:
+        dV = _c(dV, np.float64)
+        dvp = _p(dV)
+    u = np.empty_like(us)
+    f = np.empty_like(us)
+    slip = np.empty(n_iter + 1, np.float64)
+    bad = _L().or_ibm_mdf(_p(k), _p(l), k.size, lmax, kernel, _p(us), _p(x), _p(y), _p(z), _p(Uc), dvp, x.size,
+                          rho, dt, n_iter, _p(u), _p(f), _p(slip))
+    return u, f, slip, int(bad)
 
 
 # --- Learned-index root network (1 -> 32 ReLU -> 1) ------------------------------------

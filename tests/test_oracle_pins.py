@@ -342,6 +342,66 @@ def test_spread_adjoint_and_conservation(tiny_tree, tiny_workload, kernel, with_
 
 
 # ---------------------------------------------------------------------------------------
+# Multi-direct forcing (Sec. 2.2)
+# ---------------------------------------------------------------------------------------
+
+def _interp_spread_matrix(k, l, lmax, kernel, X, dV):
+    """A = I S on the markers X, column by column from unit marker forces (x component)."""
+    nm = X.shape[1]
+    A = np.zeros((nm, nm))
+    for j in range(nm):
+        e = np.zeros((3, nm))
+        e[0, j] = 1.0
+        f, _ = oracle.spread_delta(k, l, lmax, kernel, *X, e, dV)
+        u, _ = oracle.interp_delta(k, l, lmax, kernel, f, *X)
+        A[:, j] = u[0]
+    return A
+
+
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_mdf_one_round_follows_slip_recursion(tiny_tree, tiny_workload, kernel):
+    """One round moves the marker slip s = U - I u to s - A s / rho with A = I S built from
+    unit forces: catches a dropped dt or rho, a sign error and a missed correction."""
+    k, l = tiny_tree
+    w = tiny_workload
+    X = np.ascontiguousarray(w.markers[:, :40])
+    rng = np.random.default_rng(12)
+    u_star = np.zeros((k.size, 4))
+    u_star[:, :3] = rng.normal(size=(k.size, 3))
+    U = rng.normal(size=(3, X.shape[1]))
+    rho, dt = 1.7, 0.3
+    h3 = 2.0 ** (-3 * w.lmax)
+    dV = rng.uniform(0.5, 2.0, X.shape[1]) * h3
+    A = _interp_spread_matrix(k, l, w.lmax, kernel, X, dV)
+    u1, f1, slip, bad = oracle.ibm_mdf(k, l, w.lmax, kernel, u_star, X, U, rho, dt, 1, dV=dV)
+    assert bad == 0
+    I0, _ = oracle.interp_delta(k, l, w.lmax, kernel, u_star, *X)
+    I1, _ = oracle.interp_delta(k, l, w.lmax, kernel, u1, *X)
+    s0, s1 = U - I0, U - I1
+    assert np.abs(s1[0] - (s0[0] - A @ s0[0] / rho)).max() < 1e-12
+    assert abs(slip[0] - np.sqrt((s0 ** 2).sum())) < 1e-12 and abs(slip[1] - np.sqrt((s1 ** 2).sum())) < 1e-12
+    # the total force of one round is the spread of the marker forces, and it conserves them
+    assert np.allclose((f1[:, :3] * h3).sum(0), (s0 / dt * dV).sum(1), rtol=1e-12, atol=1e-14)
+    assert np.all(u1[:, 3] == u_star[:, 3])
+
+
+def test_mdf_slip_decreases_and_fixed_point(tiny_tree, tiny_workload):
+    k, l = tiny_tree
+    w = tiny_workload
+    X = w.markers
+    cen = oracle.leaf_centres(k, l)
+    u_star = synth.sin_field(cen)
+    U = np.zeros((3, X.shape[1]))  # a body at rest
+    u, f, slip, bad = oracle.ibm_mdf(k, l, w.lmax, 2, u_star, X, U, 1.0, 1.0, 8)
+    assert bad == 0
+    assert np.all(np.diff(slip) < 0) and slip[-1] < 0.5 * slip[0]
+    # no slip: nothing changes
+    Iu, _ = oracle.interp_delta(k, l, w.lmax, 2, u_star, *X)
+    u2, f2, slip2, _ = oracle.ibm_mdf(k, l, w.lmax, 2, u_star, X, Iu, 1.0, 1.0, 3)
+    assert np.all(f2 == 0.0) and np.array_equal(u2, u_star) and np.all(slip2 == 0.0)
+
+
+# ---------------------------------------------------------------------------------------
 # Trilinear interpolation of point particles (Sec. 2.3.2)
 # ---------------------------------------------------------------------------------------
 
