@@ -252,6 +252,25 @@ ot_status ot_spread_noalloc(const ot_octree* t, int kernel, const double* d_x, c
                             void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Multi-direct forcing (Sec. 2.2): n_iter rounds of
+ *   u_k = I u (Eq. ibm_interpolate, the delta kernel `kernel`),  F_k = (U_k - u_k) / dt,
+ *   F = S F_k (OT_SORTED spreading, marker volumes d_dV or h^3),  u += dt F / rho,  f += F.
+ * The printed correction u = u* + F / rho is read with the time step, u* + dt F / rho (equal
+ * in lattice units, dt = 1), applied to the velocity corrected so far.
+ *   d_u: float4 per leaf; in: the unforced velocity u*, out: the corrected velocity.
+ *   d_f: float4 per leaf; out: the total force of the rounds (overwritten).
+ *   d_U: 3 planes of n floats, the markers' prescribed velocities.
+ *   d_slip (nullable): n_iter + 1 floats, sqrt(sum_k |U_k - u_k|^2) before each round and
+ *     after the last (summed with FP64 atomics: its last bits may vary run to run).
+ *   d_workspace: ot_ibm_mdf_workspace_size bytes, 256-byte aligned.
+ * Deterministic (d_slip aside).  Asynchronous on `stream`.
+ * -------------------------------------------------------------------------------------*/
+ot_status ot_ibm_mdf_workspace_size(const ot_octree* t, int kernel, int64_t n, int n_iter, size_t* bytes);
+ot_status ot_ibm_mdf(const ot_octree* t, int kernel, const double* d_x, const double* d_y, const double* d_z,
+                     const float* d_U, const float* d_dV, int64_t n, float rho, float dt, int n_iter, float* d_u,
+                     float* d_f, float* d_slip, void* d_workspace, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Batched launch: every group of points (IBM markers with a delta kernel, point particles
  * with trilinear) located and interpolated by ONE persistent kernel, captured once in a
  * CUDA graph and replayed.

@@ -21,7 +21,7 @@ __all__ = [
     "OtError", "Octree", "Batch", "library_path", "ot_octree_build", "ot_octree_from_leaves", "ot_octree_info",
     "ot_octree_copy_leaves", "ot_octree_set_map_level", "ot_octree_get_map_level", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats",
     "ot_index_mlp_grad", "ot_locate", "ot_interpolate", "ot_interpolate_f64", "ot_spread_workspace_size",
-    "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
+    "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_ibm_mdf", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
     "ot_last_error", "ot_launch_count",
 ]
 
@@ -110,6 +110,8 @@ def _L():
                 "ot_spread_f64": (st, [P, i32, i32, P, P, P, P, P, i64, P, P, C.c_size_t, P]),
                 "ot_batch_create": (st, [P, P, i32, P, i32, P, P, P]),
                 "ot_batch_autotune": (st, [P, P, i32, P, i32, i32, i32, P, P]),
+                "ot_ibm_mdf_workspace_size": (st, [P, i32, i64, i32, P]),
+                "ot_ibm_mdf": (st, [P, i32, P, P, P, P, P, i64, C.c_float, C.c_float, i32, P, P, P, P, C.c_size_t, P]),
                 "ot_batch_run": (st, [P, P]),
                 "ot_batch_destroy": (st, [P]),
                 "ot_advect_ab2": (st, [P, P, P, P, P, i64, C.c_float, C.c_float, C.c_float, i32, i32, P]),
@@ -393,6 +395,25 @@ def ot_batch_autotune(tree: Octree, groups, field, search: int = OT_BINARY, tune
                                   search, int(tune_map_level), reps, _stream(stream), C.byref(r)))
     return {"launch": {"block": r.launch.block, "tile": r.launch.tile, "blocks_per_sm": r.launch.blocks_per_sm},
             "map_level": r.map_level, "ms": r.ms, "tried": r.tried}
+
+
+def ot_ibm_mdf(tree: Octree, kernel: int, x, y, z, U, u, rho: float, dt: float, n_iter: int, dV=None,
+               slip: bool = False, stream=None):
+    """Multi-direct forcing in place on u ((N, 4) float32: u* in, corrected u out); returns
+    (f (N, 4) total force, slip (n_iter + 1,) float32 tensor or None)."""
+    torch = _torch()
+    n, px, py, pz = _xyz(x, y, z)
+    nl = ot_octree_info(tree)[0]
+    b = C.c_size_t()
+    _check(_L().ot_ibm_mdf_workspace_size(tree.handle, kernel, n, n_iter, C.byref(b)))
+    ws = torch.empty(b.value + 256, dtype=torch.uint8, device=u.device)
+    off = (-ws.data_ptr()) % 256
+    f = torch.empty((nl, 4), dtype=torch.float32, device=u.device)
+    sl = torch.empty(n_iter + 1, dtype=torch.float32, device=u.device) if slip else None
+    _check(_L().ot_ibm_mdf(tree.handle, kernel, px, py, pz, _dptr(U, torch.float32, "U"),
+                           _dptr(dV, torch.float32, "dV"), n, rho, dt, n_iter, _dptr(u, torch.float32, "u"),
+                           _dptr(f), _dptr(sl), C.c_void_p(ws.data_ptr() + off), b.value, _stream(stream)))
+    return f, sl
 
 
 def ot_batch_run(batch: Batch, stream=None):

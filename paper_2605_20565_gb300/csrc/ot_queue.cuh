@@ -215,6 +215,17 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
     T wt[8];
     int a[8], gi[8];
     unsigned self_m = 1u, sib_m = 0u;
+    // per axis the level-mate index (the host's, or the neighbour's clamped into the cube) and
+    // its Morton bits: each corner's anchor is the OR of three of these six
+    int nb[3];
+    uint64_t dil[3][2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        nb[d] = c[d] + sg[d];
+        if (nb[d] < 0 || nb[d] >= ncell) nb[d] = c[d];
+        dil[d][0] = (part1by2((uint32_t)c[d]) << d) << (3 * sh);
+        dil[d][1] = (part1by2((uint32_t)nb[d]) << d) << (3 * sh);
+    }
 #pragma unroll
     for (int corner = 0; corner < 8; ++corner) {
         int m[3];
@@ -223,15 +234,14 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const int off = (corner >> d) & 1;
-            int v = c[d] + off * sg[d];
-            if (v < 0 || v >= ncell) v = c[d];
+            const int v = off ? nb[d] : c[d];
             m[d] = v;
             self = self && (v == c[d]);
             sib = sib && ((v >> 1) == (c[d] >> 1));
             wc *= off ? at[d] : T(1) - at[d];
         }
         wt[corner] = wc;
-        anc[corner] = morton3((uint32_t)m[0] << sh, (uint32_t)m[1] << sh, (uint32_t)m[2] << sh);
+        anc[corner] = dil[0][corner & 1] | dil[1][(corner >> 1) & 1] | dil[2][(corner >> 2) & 1];
         a[corner] = h;
         gi[corner] = min(max(h + ((m[0] & 1) | ((m[1] & 1) << 1) | ((m[2] & 1) << 2)) -
                                  ((c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2)),

@@ -499,3 +499,39 @@ def test_deep_tree_trilinear(ot, deep, map_level, torch_mod):
         ot.ot_batch_run(b)
         assert rel_err(ub.cpu().numpy(), ref32) <= TOL32
     assert ot.ot_last_error(t) & (ot.OT_DEV_OUTSIDE | ot.OT_DEV_STENCIL) == 0
+
+
+# ---------------------------------------------------------------------------------------
+# Multi-direct forcing (Sec. 2.2)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kernel", [2, 3])
+@pytest.mark.parametrize("with_dv", [False, True])
+def test_mdf_matches_oracle(ot, tiny, tiny_fields, kernel, with_dv, torch_mod):
+    torch = torch_mod
+    w, ko, lo, tree = tiny
+    rng = np.random.default_rng(31)
+    X = w.markers
+    nm = X.shape[1]
+    u_star = tiny_fields["sin"].astype(np.float32)
+    U = (0.3 * rng.normal(size=(3, nm))).astype(np.float32)
+    h3 = 2.0 ** (-3 * w.lmax)
+    dV = (rng.uniform(0.5, 2.0, nm) * h3).astype(np.float32) if with_dv else None
+    rho, dt, n_iter = 1.3, 0.7, 4
+    u_ref, f_ref, slip_ref, bad = oracle.ibm_mdf(ko, lo, w.lmax, kernel, u_star.astype(np.float64), X,
+                                                 U.astype(np.float64), rho, dt, n_iter,
+                                                 dV=None if dV is None else dV.astype(np.float64))
+    assert bad == 0
+    u = dev(u_star)
+    f, slip = ot.ot_ibm_mdf(tree, kernel, *pts(X), dev(U), u, rho, dt, n_iter,
+                            dV=None if dV is None else dev(dV), slip=True)
+    torch.cuda.synchronize()
+    assert rel_err(u.cpu().numpy()[:, :3], u_ref[:, :3]) <= TOL32
+    assert np.array_equal(u.cpu().numpy()[:, 3], u_star[:, 3])
+    assert rel_err(f.cpu().numpy()[:, :3], f_ref[:, :3]) <= TOL32
+    assert np.abs(slip.cpu().numpy() - slip_ref).max() <= 1e-5 * slip_ref.max()
+    assert np.all(np.diff(slip_ref) < 0)
+    # deterministic: a second run gives the same bits
+    u2 = dev(u_star)
+    f2, _ = ot.ot_ibm_mdf(tree, kernel, *pts(X), dev(U), u2, rho, dt, n_iter, dV=None if dV is None else dev(dV))
+    assert torch.equal(u, u2) and torch.equal(f, f2)
