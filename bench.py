@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--map-level", type=int, default=None, help="level of the level map (default: autotuned)")
     p.add_argument("--no-autotune", action="store_true", help="default launch shape and level map")
     p.add_argument("--no-nomap", action="store_true", help="skip the forms without a level map")
+    p.add_argument("--no-mdf", action="store_true", help="skip the multi-direct forcing measurement")
     return p.parse_args()
 
 
@@ -458,6 +459,25 @@ def run_ours(args):
         e2e = {"value": job_value(npts, world, e2e_ms), "unit": "points/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": k_e2e}
 
+    # multi-direct forcing (Sec. 2.2) on the same markers: 3 rounds towards a body at rest
+    mdf = None
+    if not args.no_mdf and n_m > 0:
+        U0 = torch.zeros((3, n_m), dtype=torch.float32, device=dev)
+        um_ = field.clone()
+        ot.ot_ibm_mdf(tree, ot.OT_PESKIN4, mx, my, mz, U0, um_, 1.0, 1.0, 3)
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        um_.copy_(field)
+        a_.record(stream)
+        _, slip_ = ot.ot_ibm_mdf(tree, ot.OT_PESKIN4, mx, my, mz, U0, um_, 1.0, 1.0, 3, slip=True)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        mdf_ms = a_.elapsed_time(b_)
+        sl = slip_.cpu().numpy()
+        mdf = {"rounds": 3, "ms": mdf_ms, "markers_per_s": n_m / (mdf_ms / 1e3),
+               "slip_reduction": float(sl[-1] / sl[0]) if sl[0] > 0 else None,
+               "note": "workspace allocation included; field sweeps over all leaves per round"}
+        del um_, U0
+
     # the other forms, same steps (the chosen form's level map is restored afterwards)
     forms = {chosen: {"step_ms": ms_step, "locate_interpolate_ms": batch_ms, "spread_ms": spread_ms}}
     groups_t = {}
@@ -557,6 +577,7 @@ def run_ours(args):
            "breakdown_ms": {"locate_interpolate": batch_ms, "spread": spread_ms, "step": ms_step},
            "locate_interpolate_points_per_s": world * npts / (batch_ms / 1e3),
            "forms": forms, "learned_vs_plain": learned_vs_plain, "groups_ms": groups_t, "autotune": tune,
+           "mdf": mdf,
            "index": {"n_mid": n_mid, "n_leaf": n_leaf, "mean_window": istats["mean_window"], "max_window": istats["max_window"],
                      "empty_models": istats["empty_models"], "fallbacks_timed": fb,
                      "mean_probes": istats["mean_probes"],
