@@ -113,6 +113,16 @@ __device__ __forceinline__ bool visit_stencil(const TreeView& t, const int i0[3]
     return ok_all;
 }
 
+// w[i] for a run-time stencil index i (0 <= i < W) by register selects, not an indexed (local
+// memory) load.
+template <int W, typename T>
+__device__ __forceinline__ T sel_w(const T (&w)[W], int i) {
+    T r = w[0];
+#pragma unroll
+    for (int k = 1; k < W; ++k) r = i == k ? w[k] : r;
+    return r;
+}
+
 // Delta-kernel interpolation at one marker (Sec. 2.2, Eq. ibm_interpolate).  Returns the host
 // leaf (-1 outside the cube).
 template <typename T, int K, bool LEARNED>
@@ -135,7 +145,7 @@ __device__ __forceinline__ int delta_point(const TreeView& t, const T* __restric
     int host = -1;
     T a0 = T(0), a1 = T(0), a2 = T(0);
     const bool ok = visit_stencil<K, LEARNED>(t, i0, [&](int leaf, int ax, int ay, int az) {
-        const T wt = w[0][ax] * w[1][ay] * w[2][az];
+        const T wt = sel_w<W>(w[0], ax) * sel_w<W>(w[1], ay) * sel_w<W>(w[2], az);
         const auto f = V::load(field, leaf);
         a0 += wt * f.x;
         a1 += wt * f.y;
