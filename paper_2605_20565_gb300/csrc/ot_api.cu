@@ -201,6 +201,7 @@ ot_status ot_octree_destroy(ot_octree* t) {
     if (t->d_pmap) cudaFree(t->d_pmap);
     if (t->d_nodes) cudaFree(t->d_nodes);
     if (t->d_desc) cudaFree(t->d_desc);
+    if (t->d_lmap_lv) cudaFree(t->d_lmap_lv);
     if (t->d_models) cudaFree(t->d_models);
     if (t->d_mids) cudaFree(t->d_mids);
     if (t->d_root) cudaFree(t->d_root);

@@ -505,6 +505,11 @@ __global__ void k_desc(const uint64_t* __restrict__ key, const uint8_t* __restri
     }
 }
 
+__global__ void k_lmap_lv(const uint32_t* __restrict__ lmap, const uint8_t* __restrict__ level, int64_t ncell,
+                          uint8_t* __restrict__ out) {
+    GRID_STRIDE(c, ncell) out[c] = level[lmap[c]];
+}
+
 ot_status finish_tree(ot_octree* t, cudaStream_t s, int map_level) {
     const int L = map_level >= 0 ? std::min(map_level, t->lmax) : std::min(t->lmax, 7);
     const int Lp = std::min(t->lmax, 7);
@@ -528,6 +533,13 @@ ot_status finish_tree(ot_octree* t, cudaStream_t s, int map_level) {
         count_launch();
     }
     t->lmap_level = L;
+    if (t->d_lmap_lv) cudaFree(t->d_lmap_lv);
+    {
+        const int64_t ncell = (int64_t)1 << (3 * L);
+        OT_CUDA(cudaMalloc(&t->d_lmap_lv, ncell));
+        k_lmap_lv<<<grid1d(ncell, 256), 256, 0, s>>>(t->d_lmap, t->d_level, ncell, t->d_lmap_lv);
+        count_launch();
+    }
     if (t->d_desc) cudaFree(t->d_desc);
     t->d_desc = nullptr;
     if (L + 1 <= t->lmax && L + 1 < MAXLEVEL) {
@@ -556,6 +568,7 @@ TreeView tree_view(const ot_octree* t) {
     v.lmap = t->d_lmap;
     v.lmap_level = t->lmap_level;
     v.desc = t->d_desc;
+    v.lmap_lv = t->d_lmap_lv;
     v.pyr_level = t->pyr_level;
     v.root = t->d_root;
     v.models = t->d_models;

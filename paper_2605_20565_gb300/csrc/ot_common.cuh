@@ -141,6 +141,7 @@ struct TreeView {
     // per level-map cell, the shape of its subtree when it is at most 3 levels deep (see
     // desc_leaf); null when not built
     const uint4* __restrict__ desc;
+    const uint8_t* __restrict__ lmap_lv;  // level of leaf lmap[c]
     int pyr_level;  // deepest level of the pyramid of cell means (refined trilinear level-mates)
     // learned search: root -> (optional mid models) -> leaf models
     const RootModel* __restrict__ root;  // device copy
@@ -185,17 +186,23 @@ __device__ __forceinline__ void map_range(const TreeView& t, uint64_t q, int& a,
 // m2 byte) leaves, so the leaves before child c1 number c1 + 7 popc(m1 below c1) + 7 popc(m2
 // bytes below c1); inside a refined child the same count one level down, and inside a refined
 // grandchild the great-grandchild's index.
-__device__ __forceinline__ int desc_leaf(uint4 d, int L, uint64_t q, int a) {
+// The leaf's level comes with it: L+1, L+2 or L+3 by the depth reached.
+__device__ __forceinline__ int desc_leaf(uint4 d, int L, uint64_t q, int a, int& lv) {
     const uint32_t m1 = d.z & 0xFFu;
     const uint64_t m2 = ((uint64_t)d.y << 32) | d.x;
     const int c1 = (int)(q >> (3 * (MAXLEVEL - L - 1))) & 7;
     const uint64_t low = c1 ? (~0ULL >> (64 - 8 * c1)) : 0ULL;
     int idx = a + c1 + 7 * __popc(m1 & ((1u << c1) - 1u)) + 7 * __popcll(m2 & low);
+    lv = L + 1;
     if ((m1 >> c1) & 1u) {
         const int c2 = (int)(q >> (3 * (MAXLEVEL - L - 2))) & 7;
         const uint32_t g = (uint32_t)(m2 >> (8 * c1)) & 0xFFu;
         idx += c2 + 7 * __popc(g & ((1u << c2) - 1u));
-        if ((g >> c2) & 1u) idx += (int)(q >> (3 * (MAXLEVEL - L - 3))) & 7;
+        lv = L + 2;
+        if ((g >> c2) & 1u) {
+            idx += (int)(q >> (3 * (MAXLEVEL - L - 3))) & 7;
+            lv = L + 3;
+        }
     }
     return idx;
 }
@@ -208,7 +215,8 @@ __device__ __forceinline__ int search_plain(const TreeView& t, uint64_t q) {
     const int e = (c + 1 < (1u << (3 * t.lmap_level))) ? (int)t.lmap[c + 1] : t.n;
     const uint4 d = t.desc ? __ldg(t.desc + c) : make_uint4(0u, 0u, 0u, 0u);
     if (e - a <= 1) return a;
-    if (d.z & DESC_VALID) return desc_leaf(d, t.lmap_level, q, a);
+    int lv;
+    if (d.z & DESC_VALID) return desc_leaf(d, t.lmap_level, q, a, lv);
     return search_range(t.key, a, e - a, q);
 }
 

@@ -24,6 +24,7 @@ struct WarpQueue {
     uint64_t q[QCAP];
     int lo[QCAP];
     int len[QCAP];
+    signed char lv[QCAP];  // the answer leaf's level when the search learned it, else -1
 };
 
 // The root model of the learned index, staged in shared memory by every block that searches
@@ -42,10 +43,12 @@ __device__ __forceinline__ void stage_root(const TreeView& t, RootModel& s_root)
 // The cell is covered by one leaf -- leaf a, the answer -- exactly when e - a <= 1 (a refined
 // cell holds at least 8 leaves, its first one starting at its anchor).  Returns true with the
 // answer in a when covered, else false with the cell's leaf range [a, e) to search.
-__device__ __forceinline__ bool map_lookup(const TreeView& t, uint64_t q, int& a, int& e) {
+// lv: the level of leaf a (from the per-cell level table, in the same round trip).
+__device__ __forceinline__ bool map_lookup(const TreeView& t, uint64_t q, int& a, int& e, int& lv) {
     const uint32_t cell = (uint32_t)(q >> (3 * (MAXLEVEL - t.lmap_level)));
     a = (int)t.lmap[cell];
     e = cell < (1u << (3 * t.lmap_level)) - 1u ? (int)t.lmap[cell + 1] : t.n;
+    lv = t.lmap_lv[cell];
     return e - a <= 1;
 }
 
@@ -72,7 +75,8 @@ __device__ __forceinline__ int push_task(WarpQueue& w, int& n, bool need, uint64
 //            load and window (its prediction widened by the stored error bounds, clamped to
 //            the cell), halving probes over the window, and the check key[a] <= q < key[a+1];
 //            a window that missed is replaced by the whole cell (a counted fallback).
-// A finished task's answer (the last index in its range whose key is <= q) replaces its lo.
+// A finished task's answer (the last index in its range whose key is <= q) replaces its lo;
+// its level goes to lv when the descriptor gave it (-1 otherwise).
 // (Routing all tasks side by side before the loop was measured slower: it adds a round trip
 // and registers.)
 enum { ST_ROUTE = 0, ST_MODEL = 1, ST_PROBE = 2, ST_CHECK = 3, ST_DONE = 4, ST_DESC = 5 };
@@ -81,12 +85,15 @@ template <bool LEARNED>
 __device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& root, WarpQueue& w, int ntask,
                                           unsigned lt) {
     __syncwarp();
-    int cur = -1, lo = 0, len = 0, next = 0, st = ST_DONE, clo = 0, clen = 0, j = 0;
+    int cur = -1, lo = 0, len = 0, next = 0, st = ST_DONE, clo = 0, clen = 0, j = 0, lvr = -1;
     bool checked = false;
     uint64_t q = 0;
     for (;;) {
         const bool fin = cur >= 0 && st == ST_DONE;
-        if (fin) w.lo[cur] = lo;
+        if (fin) {
+            w.lo[cur] = lo;
+            w.lv[cur] = (signed char)lvr;
+        }
         const bool need = cur < 0 || fin;
         const unsigned m = __ballot_sync(FULL, need);
         if (need) {
@@ -99,6 +106,7 @@ __device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& ro
                 len = clen = w.len[idx];
                 st = LEARNED ? ST_ROUTE : (t.desc ? ST_DESC : ST_PROBE);
                 checked = false;
+                lvr = -1;
             }
         }
         next += __popc(m);
@@ -107,7 +115,7 @@ __device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& ro
         if (!LEARNED && st == ST_DESC) {
             const uint4 d = __ldg(t.desc + (q >> (3 * (MAXLEVEL - t.lmap_level))));
             if (d.z & DESC_VALID) {
-                lo = desc_leaf(d, t.lmap_level, q, lo);
+                lo = desc_leaf(d, t.lmap_level, q, lo, lvr);
                 st = ST_DONE;
             } else {
                 st = ST_PROBE;
@@ -178,24 +186,24 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
     const bool ok = active && fixpoint3(x, y, z, X);
     if (active && !ok) atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
 
-    // host
-    int h = host_in;
+    // host (and its level, when the lookup gives it)
+    int h = host_in, hl = -1;
     {
         const uint64_t q = morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32));
-        int ca = 0, ce = 0;
-        const bool need = ok && h < 0 && !map_lookup(t, q, ca, ce);
-        if (ok && h < 0 && !need) h = ca;
+        int ca = 0, ce = 0, clv = -1;
+        const bool need = ok && h < 0 && !map_lookup(t, q, ca, ce, clv);
+        if (ok && h < 0 && !need) h = ca, hl = clv;
         if (__any_sync(FULL, need)) {
             int n = 0;
             const int ix = push_task(w, n, need, q, ca, ce - ca, lt);
             run_tasks<LEARNED>(t, root, w, n, lt);
-            if (ix >= 0) h = w.lo[ix];
+            if (ix >= 0) h = w.lo[ix], hl = w.lv[ix];
             __syncwarp();
         }
     }
-    if (!ok) h = 0;  // keeps the lane's reads in bounds; its result is discarded
+    if (!ok) h = 0, hl = -1;  // keeps the lane's reads in bounds; its result is discarded
 
-    const int l = t.level[h];
+    const int l = hl >= 0 ? hl : (int)t.level[h];
     const int ncell = 1 << l;
     int c[3], sg[3];
     T at[3];
@@ -259,6 +267,7 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
     int ca[8], ce[8];
     {
         uint64_t gk[8];
+        int unused_lv;
 #pragma unroll
         for (int corner = 1; corner < 8; ++corner) {
             ca[corner] = 0;
@@ -267,7 +276,7 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
             if ((sib_m >> corner) & 1u) {
                 gk[corner] = ldg_key(t.key + gi[corner]);
             } else if ((pend_m >> corner) & 1u) {
-                if (map_lookup(t, anc[corner], ca[corner], ce[corner])) {
+                if (map_lookup(t, anc[corner], ca[corner], ce[corner], unused_lv)) {
                     a[corner] = ca[corner];
                     pend_m &= ~(1u << corner);
                 }
@@ -276,7 +285,7 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
 #pragma unroll
         for (int corner = 1; corner < 8; ++corner) {
             if (!((sib_m >> corner) & 1u)) continue;
-            if (gk[corner] == anc[corner] || map_lookup(t, anc[corner], ca[corner], ce[corner])) {
+            if (gk[corner] == anc[corner] || map_lookup(t, anc[corner], ca[corner], ce[corner], unused_lv)) {
                 a[corner] = gk[corner] == anc[corner] ? gi[corner] : ca[corner];
                 pend_m &= ~(1u << corner);
             }
@@ -298,7 +307,8 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
         out[0] = out[1] = out[2] = qnan<T>();
         return -1;
     }
-    // Stage 6: levels of the level-mates' leaves; stage 7: their values.
+    // Stage 6: the levels of the level-mates' leaves (carrying them along from the lookups was
+    // measured slower: registers); stage 7: the values.
     int lvl[8];
 #pragma unroll
     for (int corner = 0; corner < 8; ++corner) lvl[corner] = ((self_m >> corner) & 1u) ? l : (int)t.level[a[corner]];
