@@ -321,6 +321,28 @@ ot_status ot_batch_autotune(ot_octree* t, const ot_group* groups, int n_groups, 
                             int tune_map_level, int reps, void* stream, ot_tune_result* out);
 
 /* ---------------------------------------------------------------------------------------
+ * Analytic field on the leaves (not in the paper; the synthetic stand-in for the fluid
+ * solver's velocity): d_field[leaf] = (sum_m A_m cos(2 pi n_m . c + phi_m), 0) at each leaf
+ * centre c, FP32.  h_wave: 3 x n_modes integer wave vectors (|component| <= 4096); h_amp:
+ * 3 x n_modes amplitudes; h_phase: n_modes phases (radians).  n_modes <= 64.  The argument
+ * is reduced modulo one turn exactly (integer fixed point, phase rounded to 2^-32 turns);
+ * only the cosine is FP32.  Asynchronous on `stream`.
+ * -------------------------------------------------------------------------------------*/
+ot_status ot_field_fourier(const ot_octree* t, int n_modes, const int32_t* h_wave, const double* h_amp,
+                           const double* h_phase, float* d_field, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Morton order of a point set (not in the paper's API; its ranks keep their Lagrangian points
+ * grouped by cell, Sec. 3.2): d_perm[i] = the index of the i-th point along the Z curve of
+ * the finest cells (stable; points outside [0,1)^3 last).  Storing points in this order lets
+ * a warp's points share their host leaves and level-mates.  n < 2^31.  d_workspace:
+ * ot_points_order_workspace_size bytes, 16-byte aligned.  Asynchronous on `stream`.
+ * -------------------------------------------------------------------------------------*/
+ot_status ot_points_order_workspace_size(int64_t n, size_t* bytes);
+ot_status ot_points_morton_order(const double* d_x, const double* d_y, const double* d_z, int64_t n, int32_t* d_perm,
+                                 void* d_workspace, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Point-particle advection (Sec. 2.3.2, Eq. PointParticle, gravity off): per particle
  *   a = f_p (u - v)/tau, f_p = 1 + 0.15 (re_coef |u - v|)^0.687 (re_coef = 0: f_p = 1),
  *   v += dt (3/2 a - 1/2 a_prev), x += dt (3/2 v_old - 1/2 v_prev); Euler when first != 0.

@@ -21,7 +21,7 @@ __all__ = [
     "OtError", "Octree", "Batch", "library_path", "ot_octree_build", "ot_octree_from_leaves", "ot_octree_info",
     "ot_octree_copy_leaves", "ot_octree_set_map_level", "ot_octree_get_map_level", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats",
     "ot_index_mlp_grad", "ot_locate", "ot_interpolate", "ot_interpolate_f64", "ot_spread_workspace_size",
-    "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_ibm_mdf", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
+    "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_ibm_mdf", "ot_points_morton_order", "ot_field_fourier", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
     "ot_last_error", "ot_launch_count",
 ]
 
@@ -111,6 +111,9 @@ def _L():
                 "ot_batch_create": (st, [P, P, i32, P, i32, P, P, P]),
                 "ot_batch_autotune": (st, [P, P, i32, P, i32, i32, i32, P, P]),
                 "ot_ibm_mdf_workspace_size": (st, [P, i32, i64, i32, P]),
+                "ot_points_order_workspace_size": (st, [i64, P]),
+                "ot_field_fourier": (st, [P, i32, P, P, P, P, P]),
+                "ot_points_morton_order": (st, [P, P, P, i64, P, P, C.c_size_t, P]),
                 "ot_ibm_mdf": (st, [P, i32, P, P, P, P, P, i64, C.c_float, C.c_float, i32, P, P, P, P, C.c_size_t, P]),
                 "ot_batch_run": (st, [P, P]),
                 "ot_batch_destroy": (st, [P]),
@@ -414,6 +417,33 @@ def ot_ibm_mdf(tree: Octree, kernel: int, x, y, z, U, u, rho: float, dt: float, 
                            _dptr(dV, torch.float32, "dV"), n, rho, dt, n_iter, _dptr(u, torch.float32, "u"),
                            _dptr(f), _dptr(sl), C.c_void_p(ws.data_ptr() + off), b.value, _stream(stream)))
     return f, sl
+
+
+def ot_field_fourier(tree: Octree, wave, amp, phase, field=None, stream=None):
+    """(N, 4) float32 field sum_m amp_m cos(2 pi wave_m . c + phase_m) at the leaf centres c.
+    wave: (M, 3) integers; amp: (M, 3); phase: (M,) radians."""
+    import numpy as np
+    torch = _torch()
+    w = np.ascontiguousarray(np.asarray(wave).reshape(-1, 3), dtype=np.int32)
+    a = np.ascontiguousarray(np.asarray(amp, dtype=np.float64).reshape(-1, 3))
+    p = np.ascontiguousarray(np.asarray(phase, dtype=np.float64).reshape(-1))
+    if field is None:
+        field = torch.empty((ot_octree_info(tree)[0], 4), dtype=torch.float32, device="cuda")
+    _check(_L().ot_field_fourier(tree.handle, w.shape[0], w.ctypes.data_as(C.c_void_p), a.ctypes.data_as(C.c_void_p),
+                                 p.ctypes.data_as(C.c_void_p), _dptr(field, torch.float32, "field"), _stream(stream)))
+    return field
+
+
+def ot_points_morton_order(x, y, z, stream=None):
+    """int32 permutation putting the points in Morton (Z-curve) order of their finest cells."""
+    torch = _torch()
+    n, px, py, pz = _xyz(x, y, z)
+    b = C.c_size_t()
+    _check(_L().ot_points_order_workspace_size(n, C.byref(b)))
+    ws = torch.empty(max(1, b.value), dtype=torch.uint8, device=x.device)
+    perm = torch.empty(n, dtype=torch.int32, device=x.device)
+    _check(_L().ot_points_morton_order(px, py, pz, n, _dptr(perm), _dptr(ws), b.value, _stream(stream)))
+    return perm
 
 
 def ot_batch_run(batch: Batch, stream=None):

@@ -11,8 +11,10 @@ Every step, through the C ABI:
   4. the bubbles translate at constant velocities carrying their markers.
 Every ``rebuild_every`` steps the octree is rebuilt around the moved bubbles
 (``ot_octree_build``), the learned index is retrained on the device (``ot_index_train``), the
-velocity field is re-sampled at the new leaf centres, and the batch graph is re-captured:
-the single-GPU form of re-locating every point after a mesh change.
+velocity field is re-sampled at the new leaf centres, the particles are re-stored in Morton
+order of their cells (``ot_points_morton_order``; ``ids`` keeps each one's original index),
+and the batch graph is re-captured: the single-GPU form of re-locating every point after a
+mesh change.
 
 The time step keeps particle motion below one finest cell per step: dt = h_lmax / max|u|.
 """
@@ -27,7 +29,8 @@ from . import synth
 
 class Tracker:
     def __init__(self, w: synth.Workload, search: int = 1, rebuild_every: int = 10, tau_steps: float = 10.0,
-                 re_coef: float = 0.0, n_leaf_models: int = 1 << 18, n_mid_models: int = 4096, device=None):
+                 re_coef: float = 0.0, n_leaf_models: int = 1 << 18, n_mid_models: int = 4096, device=None,
+                 sort_points: bool = True):
         import torch
         from . import OT_PESKIN4, OT_SORTED, OT_TRILINEAR
         self.torch = torch
@@ -48,6 +51,8 @@ class Tracker:
         dev = self.dev
         self.x = T.as_tensor(np.ascontiguousarray(w.particles), device=dev)            # (3, n) FP64
         n = self.x.shape[1]
+        self.sort_points = sort_points
+        self.ids = T.arange(n, device=dev)  # original index of each stored particle
         self.v = T.zeros((3, n), dtype=T.float32, device=dev)
         self.a_prev = T.zeros_like(self.v)
         self.v_prev = T.zeros_like(self.v)
@@ -76,19 +81,41 @@ class Tracker:
         c = self.torch.as_tensor(self.centres0 + self.vel * self.t, device=self.dev)  # (B, 3)
         self.mx.copy_(c[self.m_grp].T + self.m_off)
 
+    def _reorder(self):
+        """Store the particles in Morton order of their cells (neighbouring particles share host
+        leaves and level-mates in a warp); every per-particle array follows."""
+        import paper_2605_20565_gb300 as ot
+        perm = ot.ot_points_morton_order(self.x[0], self.x[1], self.x[2]).long()
+        for name in ("x", "v", "a_prev", "v_prev", "u", "ids"):
+            a = getattr(self, name)
+            setattr(self, name, a.index_select(a.dim() - 1, perm).contiguous())
+
     def _rebuild(self):
         import paper_2605_20565_gb300 as ot
         T = self.torch
         t0 = time.time()
         w = self.w
+        parts = self.timings.setdefault("rebuild_parts_s", {})
+
+        def mark(name, t_prev):
+            T.cuda.synchronize()
+            now = time.time()
+            parts[name] = parts.get(name, 0.0) + now - t_prev
+            return now
+
+        t = t0
+        if self.sort_points:
+            self._reorder()
+            t = mark("reorder", t)
         self.tree = ot.ot_octree_build(self.spheres_now(), w.lmin, w.lmax)
+        t = mark("octree_build", t)
         ot.ot_index_train(self.tree, root=ot.OT_ROOT_MLP, n_leaf_models=self.n_leaf_models,
                           n_mid_models=self.n_mid_models, epochs=2, batch=65536, lr=1e-3, seed=self.step_no)
+        t = mark("index_train", t)
         n_leaves = ot.ot_octree_info(self.tree)[0]
-        cen = ot.ot_octree_centres(self.tree)
-        self.field = synth.fourier_field(w.modes, cen.T.contiguous()).to(T.float32).contiguous()
-        del cen
+        self.field = ot.ot_field_fourier(self.tree, w.modes.n, w.modes.amp, w.modes.phase)
         self.f = T.zeros((n_leaves, 4), dtype=T.float32, device=self.dev)
+        t = mark("field", t)
         mx, my, mz = self.mx[0], self.mx[1], self.mx[2]
         px, py, pz = self.x[0], self.x[1], self.x[2]
         K_P4, _, K_TRI = self.kinds
@@ -98,7 +125,7 @@ class Tracker:
         need = ot.ot_spread_workspace_size(self.tree, K_P4, self.mx.shape[1])
         if self.ws.numel() < need:
             self.ws = T.empty(need, dtype=T.uint8, device=self.dev)
-        T.cuda.synchronize()
+        mark("batch", t)
         self.timings["rebuild_s"] += time.time() - t0
         self.timings["rebuilds"] += 1
 

@@ -535,3 +535,38 @@ def test_mdf_matches_oracle(ot, tiny, tiny_fields, kernel, with_dv, torch_mod):
     u2 = dev(u_star)
     f2, _ = ot.ot_ibm_mdf(tree, kernel, *pts(X), dev(U), u2, rho, dt, n_iter, dV=None if dV is None else dev(dV))
     assert torch.equal(u, u2) and torch.equal(f, f2)
+
+
+@pytest.mark.parametrize("n", [1, 33, 50000])
+def test_points_morton_order(ot, n, torch_mod):
+    """The permutation equals a stable sort of the points' level-21 Morton keys, truncated to
+    the bits left beside the index (an independent bit-loop encoder here)."""
+    rng = np.random.default_rng(n)
+    P = rng.uniform(0, 1, (3, n))
+    if n > 40:
+        P[:, :5] = P[:, 5:10]           # equal keys keep their input order
+        P[0, 10] = 1.0                  # outside: last
+    perm = ot.ot_points_morton_order(*pts(P)).cpu().numpy()
+    q = np.floor(np.clip(P, 0, 1) * 2.0 ** 21).astype(np.uint64)
+    key = np.zeros(n, np.uint64)
+    for b in range(21):
+        for d in range(3):
+            key |= ((q[d] >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + d)
+    ib = max(1, int(np.ceil(np.log2(max(n, 2)))))
+    top = key >> np.uint64(ib - 1)
+    top[np.any((P < 0) | (P >= 1), axis=0)] = np.uint64((1 << (64 - ib)) - 1)
+    ref = np.argsort(top, kind="stable")
+    assert np.array_equal(perm, ref)
+
+
+def test_field_fourier_matches_modes(ot, deep):
+    """The analytic leaf field (exact fixed-point phase, FP32 cosine) against the same modes
+    evaluated in FP64 at the oracle's leaf centres."""
+    from paper_2605_20565_gb300 import synth
+    sph, ko, lo, P, _ = deep
+    t = ot.ot_octree_build(sph, 3, 9)
+    m = synth.fourier_modes(4)
+    f = ot.ot_field_fourier(t, m.n, m.amp, m.phase).cpu().numpy()
+    ref = synth.fourier_field(m, oracle.leaf_centres(ko, lo))
+    assert np.abs(f[:, :3] - ref[:, :3]).max() <= 1e-6 * np.abs(ref).max()
+    assert np.all(f[:, 3] == 0)

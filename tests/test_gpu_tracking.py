@@ -13,6 +13,16 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 
+def _morton(P):
+    """Morton keys of the finest (level 21) cells of points (3, n) in [0, 1)."""
+    q = np.floor(np.asarray(P) * 2.0 ** 21).astype(np.uint64)
+    key = np.zeros(q.shape[1], np.uint64)
+    for b in range(21):
+        for d in range(3):
+            key |= ((q[d] >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + d)
+    return key
+
+
 @pytest.fixture(scope="module")
 def env():
     torch = pytest.importorskip("torch")
@@ -63,11 +73,15 @@ def test_tracking_first_step_matches_oracle(env):
     oracle.advect_ab2(st, u_ref, tr.tau, 2.0, tr.dt, True, periodic=True)
     tr.step()
     torch.cuda.synchronize()
+    # the tracker stores its particles in Morton order; ids maps them to the input order
+    ids = tr.ids.cpu().numpy()
+    assert np.array_equal(np.sort(ids), np.arange(P.shape[1]))
+    assert np.all(np.diff(_morton(P[:, ids])) >= 0)
     scale = np.abs(f32[:, :3]).max()
-    assert np.abs(tr.u.cpu().numpy() - u_ref).max() <= 1e-5 * scale
+    assert np.abs(tr.u.cpu().numpy() - u_ref[:, ids]).max() <= 1e-5 * scale
     assert np.abs(tr.um.cpu().numpy() - um_ref).max() <= 1e-5 * scale
-    assert np.abs(tr.v.cpu().numpy() - st["v"]).max() <= 1e-5 * max(np.abs(st["v"]).max(), 1e-30)
-    dx = np.abs(tr.x.cpu().numpy() - st["x"])
+    assert np.abs(tr.v.cpu().numpy() - st["v"][:, ids]).max() <= 1e-5 * max(np.abs(st["v"]).max(), 1e-30)
+    dx = np.abs(tr.x.cpu().numpy() - st["x"][:, ids])
     dx = np.minimum(dx, 1.0 - dx)  # periodic distance
     assert dx.max() <= 1e-9
     # markers moved rigidly with their bubbles
