@@ -148,10 +148,18 @@ typedef struct {
     int batch;         /* MLP root: minibatch size                                           */
     float lr;          /* MLP root: Adam step size                                           */
     uint64_t seed;     /* MLP root: minibatch sampling                                       */
+    int steps;         /* MLP root: > 0 replaces epochs by this many Adam steps              */
+    const float* h_init; /* MLP root: nullable; 97 host floats (w1, b1, w2, b2) to start from
+                            instead of the spline initialisation (a warm start: retraining
+                            after a re-adaptation from the previous tree's network)          */
 } ot_index_params;
 
 /* Train on the device over the octree's keys; replaces a previous index.  Synchronises. */
 ot_status ot_index_train(ot_octree* t, const ot_index_params* params, void* stream);
+
+/* The trained MLP root's 97 parameters (w1[32], b1[32], w2[32], b2) into host memory;
+ * OT_ERR_NO_INDEX without an index or with a linear root. */
+ot_status ot_index_get_root_params(const ot_octree* t, float* h_params);
 
 /* Index statistics (host values): window length (mean over the stored keys, max over the
  * leaf models), number of empty models, learned-query fallbacks counted since the last reset,
@@ -334,13 +342,14 @@ ot_status ot_field_fourier(const ot_octree* t, int n_modes, const int32_t* h_wav
 /* ---------------------------------------------------------------------------------------
  * Morton order of a point set (not in the paper's API; its ranks keep their Lagrangian points
  * grouped by cell, Sec. 3.2): d_perm[i] = the index of the i-th point along the Z curve of
- * the finest cells (stable; points outside [0,1)^3 last).  Storing points in this order lets
- * a warp's points share their host leaves and level-mates.  n < 2^31.  d_workspace:
+ * the cells of `level` (1..21; stable, so points of one cell keep their order; points outside
+ * [0,1)^3 last).  Storing points in this order lets a warp's points share their host leaves
+ * and level-mates.  n < 2^31 and 3 level + ceil(log2 n) <= 64.  d_workspace:
  * ot_points_order_workspace_size bytes, 16-byte aligned.  Asynchronous on `stream`.
  * -------------------------------------------------------------------------------------*/
 ot_status ot_points_order_workspace_size(int64_t n, size_t* bytes);
-ot_status ot_points_morton_order(const double* d_x, const double* d_y, const double* d_z, int64_t n, int32_t* d_perm,
-                                 void* d_workspace, size_t ws_bytes, void* stream);
+ot_status ot_points_morton_order(const double* d_x, const double* d_y, const double* d_z, int64_t n, int level,
+                                 int32_t* d_perm, void* d_workspace, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Point-particle advection (Sec. 2.3.2, Eq. PointParticle, gravity off): per particle

@@ -19,7 +19,7 @@ __all__ = [
     "OT_TRILINEAR", "OT_PESKIN4", "OT_ROMA3", "OT_BINARY", "OT_LEARNED", "OT_SORTED", "OT_ATOMIC",
     "OT_ROOT_LINEAR", "OT_ROOT_MLP", "OT_DEV_OUTSIDE", "OT_DEV_STENCIL", "OT_DEV_REFINED_CAP", "OT_DEV_WINDOW",
     "OtError", "Octree", "Batch", "library_path", "ot_octree_build", "ot_octree_from_leaves", "ot_octree_info",
-    "ot_octree_copy_leaves", "ot_octree_set_map_level", "ot_octree_get_map_level", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats",
+    "ot_octree_copy_leaves", "ot_octree_set_map_level", "ot_octree_get_map_level", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats", "ot_index_get_root_params",
     "ot_index_mlp_grad", "ot_locate", "ot_interpolate", "ot_interpolate_f64", "ot_spread_workspace_size",
     "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_ibm_mdf", "ot_points_morton_order", "ot_field_fourier", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
     "ot_last_error", "ot_launch_count",
@@ -57,7 +57,8 @@ class _BuildParams(C.Structure):
 
 class _IndexParams(C.Structure):
     _fields_ = [("root", C.c_int), ("n_leaf_models", C.c_int), ("n_mid_models", C.c_int), ("epochs", C.c_int),
-                ("batch", C.c_int), ("lr", C.c_float), ("seed", C.c_uint64)]
+                ("batch", C.c_int), ("lr", C.c_float), ("seed", C.c_uint64), ("steps", C.c_int),
+                ("h_init", C.c_void_p)]
 
 
 class _IndexStats(C.Structure):
@@ -101,6 +102,7 @@ def _L():
                 "ot_octree_destroy": (st, [P]),
                 "ot_index_train": (st, [P, P, P]),
                 "ot_index_get_stats": (st, [P, P, i32]),
+                "ot_index_get_root_params": (st, [P, P]),
                 "ot_index_mlp_grad": (st, [P, P, P, i64, P, P, P]),
                 "ot_locate": (st, [P, P, P, P, i64, i32, P, P, P]),
                 "ot_interpolate": (st, [P, i32, P, P, P, i64, P, i32, P, P, P, P]),
@@ -113,7 +115,7 @@ def _L():
                 "ot_ibm_mdf_workspace_size": (st, [P, i32, i64, i32, P]),
                 "ot_points_order_workspace_size": (st, [i64, P]),
                 "ot_field_fourier": (st, [P, i32, P, P, P, P, P]),
-                "ot_points_morton_order": (st, [P, P, P, i64, P, P, C.c_size_t, P]),
+                "ot_points_morton_order": (st, [P, P, P, i64, i32, P, P, C.c_size_t, P]),
                 "ot_ibm_mdf": (st, [P, i32, P, P, P, P, P, i64, C.c_float, C.c_float, i32, P, P, P, P, C.c_size_t, P]),
                 "ot_batch_run": (st, [P, P]),
                 "ot_batch_destroy": (st, [P]),
@@ -256,9 +258,21 @@ def ot_octree_destroy(tree: Octree):
 # --- learned index ------------------------------------------------------------------------
 
 def ot_index_train(tree: Octree, root: int = OT_ROOT_MLP, n_leaf_models: int = 4096, epochs: int = 4,
-                   batch: int = 65536, lr: float = 1e-3, seed: int = 0, n_mid_models: int = 0, stream=None):
-    prm = _IndexParams(root, n_leaf_models, n_mid_models, epochs, batch, lr, seed)
+                   batch: int = 65536, lr: float = 1e-3, seed: int = 0, n_mid_models: int = 0, steps: int = 0,
+                   init=None, stream=None):
+    """init: 97 MLP parameters to start from (e.g. ot_index_get_root_params of the previous tree)."""
+    import numpy as np
+    h = None if init is None else np.ascontiguousarray(np.asarray(init, dtype=np.float32).reshape(97))
+    prm = _IndexParams(root, n_leaf_models, n_mid_models, epochs, batch, lr, seed, steps,
+                       None if h is None else h.ctypes.data_as(C.c_void_p))
     _check(_L().ot_index_train(tree.handle, C.byref(prm), _stream(stream)))
+
+
+def ot_index_get_root_params(tree: Octree):
+    import numpy as np
+    h = np.empty(97, np.float32)
+    _check(_L().ot_index_get_root_params(tree.handle, h.ctypes.data_as(C.c_void_p)))
+    return h
 
 
 def ot_index_get_stats(tree: Octree, reset: bool = False) -> dict:
@@ -434,15 +448,15 @@ def ot_field_fourier(tree: Octree, wave, amp, phase, field=None, stream=None):
     return field
 
 
-def ot_points_morton_order(x, y, z, stream=None):
-    """int32 permutation putting the points in Morton (Z-curve) order of their finest cells."""
+def ot_points_morton_order(x, y, z, level: int = 8, stream=None):
+    """int32 permutation putting the points in Morton (Z-curve) order of their level cells."""
     torch = _torch()
     n, px, py, pz = _xyz(x, y, z)
     b = C.c_size_t()
     _check(_L().ot_points_order_workspace_size(n, C.byref(b)))
     ws = torch.empty(max(1, b.value), dtype=torch.uint8, device=x.device)
     perm = torch.empty(n, dtype=torch.int32, device=x.device)
-    _check(_L().ot_points_morton_order(px, py, pz, n, _dptr(perm), _dptr(ws), b.value, _stream(stream)))
+    _check(_L().ot_points_morton_order(px, py, pz, n, level, _dptr(perm), _dptr(ws), b.value, _stream(stream)))
     return perm
 
 

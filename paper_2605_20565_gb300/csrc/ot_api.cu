@@ -215,8 +215,21 @@ ot_status ot_index_train(ot_octree* t, const ot_index_params* p, void* stream) {
     if (p->root != OT_ROOT_LINEAR && p->root != OT_ROOT_MLP) return OT_ERR_ARG;
     if (p->n_leaf_models < 1 || p->n_leaf_models > (1 << 22)) return OT_ERR_ARG;
     if (p->n_mid_models < 0 || p->n_mid_models > (1 << 20)) return OT_ERR_ARG;
-    if (p->root == OT_ROOT_MLP && (p->epochs < 0 || p->batch < 1 || !(p->lr >= 0.0f))) return OT_ERR_ARG;
+    if (p->root == OT_ROOT_MLP && (p->epochs < 0 || p->steps < 0 || p->batch < 1 || !(p->lr >= 0.0f)))
+        return OT_ERR_ARG;
     return train_index(t, p, (cudaStream_t)stream);
+}
+
+ot_status ot_index_get_root_params(const ot_octree* t, float* h) {
+    if (!t || !h) return OT_ERR_ARG;
+    if (!t->has_index || t->root.kind != OT_ROOT_MLP) return OT_ERR_NO_INDEX;
+    for (int k = 0; k < MLP_H; ++k) {
+        h[k] = t->root.w1[k];
+        h[MLP_H + k] = t->root.b1[k];
+        h[2 * MLP_H + k] = t->root.w2[k];
+    }
+    h[3 * MLP_H] = t->root.b2;
+    return OT_OK;
 }
 
 ot_status ot_index_get_stats(const ot_octree* t, ot_index_stats* s, int reset) {

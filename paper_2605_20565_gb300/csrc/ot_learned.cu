@@ -425,6 +425,8 @@ ot_status train_index(ot_octree* t, const ot_index_params* prm, cudaStream_t s) 
             prev = slope;
         }
         p[3 * MLP_H] = cdf[0];
+        if (prm->h_init)
+            for (int k = 0; k < MLP_NPARAM; ++k) p[k] = prm->h_init[k];
         float* d_p = nullptr;
         Adam* d_adam = nullptr;
         float* d_loss = nullptr;
@@ -439,7 +441,7 @@ ot_status train_index(ot_octree* t, const ot_index_params* prm, cudaStream_t s) 
         OT_CUDA(cudaMemsetAsync(d_loss, 0, sizeof(float), s));
         const int batch = std::max(1, prm->batch);
         const int64_t per_epoch = std::max<int64_t>(1, std::min<int64_t>(n / batch, 512));
-        const int64_t steps = (int64_t)std::max(0, prm->epochs) * per_epoch;
+        const int64_t steps = prm->steps > 0 ? prm->steps : (int64_t)std::max(0, prm->epochs) * per_epoch;
         for (int64_t st = 0; st < steps; ++st) {
             k_mlp_step_grad<<<nb, MT, 0, s>>>(d_p, t->d_key, n, batch, prm->seed, (int)st, part);
             k_adam<<<1, 128, 0, s>>>(d_p, d_adam, part, nb, (int)st, prm->lr, d_loss);

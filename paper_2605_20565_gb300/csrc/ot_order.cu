@@ -1,5 +1,5 @@
 // ot_order.cu -- the Morton (Z-curve) order of a point set: the permutation that sorts the
-// points by the key of the finest-level cell holding them.  Points stored in this order give
+// points (stably) by the key of the level-L cell holding them.  Points stored in this order give
 // a warp neighbouring points (the same host leaf and level-mates), which is how the paper's
 // ranks keep their Lagrangian points grouped by cell (Sec. 3.2); the tracking driver reorders
 // its particles this way at every re-adaptation.
@@ -11,17 +11,17 @@ namespace ot {
 
 namespace {
 
-// (top key bits << ib) | index; a point outside the cube sorts last (key all ones).
+// (level-L cell key << ib) | index; a point outside the cube gets the all-ones key (last).
 __global__ void __launch_bounds__(256) k_point_keys(const double* __restrict__ x, const double* __restrict__ y,
-                                                   const double* __restrict__ z, int64_t n, int ib,
+                                                   const double* __restrict__ z, int64_t n, int L, int ib,
                                                    uint64_t* __restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         uint64_t X[3];
-        uint64_t key = ~0ULL;
+        uint64_t cell = (1ULL << (3 * L)) - 1;
         if (fixpoint3(x[i], y[i], z[i], X))
-            key = morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32));
-        const uint64_t top = key == ~0ULL ? ~0ULL >> ib : key >> (ib - 1);  // the top 64 - ib bits
-        out[i] = (top << ib) | (uint64_t)i;
+            cell = morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32)) >>
+                   (3 * (MAXLEVEL - L));
+        out[i] = (cell << ib) | (uint64_t)i;
     }
 }
 
@@ -56,8 +56,10 @@ extern "C" ot_status ot_points_order_workspace_size(int64_t n, size_t* bytes) {
 }
 
 extern "C" ot_status ot_points_morton_order(const double* d_x, const double* d_y, const double* d_z, int64_t n,
-                                            int32_t* d_perm, void* d_workspace, size_t ws_bytes, void* stream) {
-    if (n < 0 || n > ((int64_t)1 << 31) - 1) return OT_ERR_ARG;
+                                            int level, int32_t* d_perm, void* d_workspace, size_t ws_bytes,
+                                            void* stream) {
+    if (n < 0 || n > ((int64_t)1 << 31) - 1 || level < 1 || level > MAXLEVEL) return OT_ERR_ARG;
+    if (3 * level + index_bits(std::max<int64_t>(n, 1)) > 64) return OT_ERR_ARG;
     if (n == 0) return OT_OK;
     if (!d_x || !d_y || !d_z || !d_perm || !d_workspace || ((uintptr_t)d_workspace & 15) ||
         ws_bytes < order_ws_bytes(n))
@@ -67,10 +69,9 @@ extern "C" ot_status ot_points_morton_order(const double* d_x, const double* d_y
     uint64_t* tmp = pairs + n;
     void* rws = tmp + n;
     const int ib = index_bits(n);
-    k_point_keys<<<grid_o(n), 256, 0, s>>>(d_x, d_y, d_z, n, ib, pairs);
+    k_point_keys<<<grid_o(n), 256, 0, s>>>(d_x, d_y, d_z, n, level, ib, pairs);
     count_launch();
-    // the key keeps the top 64 - ib bits of the 63-bit Morton key: sort bits [ib, 64)
-    ot_status st = radix_sort_u64_ws(pairs, tmp, n, ib, 64, rws, s);
+    ot_status st = radix_sort_u64_ws(pairs, tmp, n, ib, ib + 3 * level, rws, s);
     if (st != OT_OK) return st;
     k_pair_index<<<grid_o(n), 256, 0, s>>>(pairs, n, ((uint64_t)1 << ib) - 1, d_perm);
     count_launch();

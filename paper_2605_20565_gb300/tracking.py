@@ -107,10 +107,14 @@ class Tracker:
         if self.sort_points:
             self._reorder()
             t = mark("reorder", t)
+        prev = ot.ot_index_get_root_params(self.tree) if getattr(self, "tree", None) is not None else None
         self.tree = ot.ot_octree_build(self.spheres_now(), w.lmin, w.lmax)
         t = mark("octree_build", t)
+        # the first index trains from the spline initialisation; later ones fine-tune the previous
+        # network (the bubbles moved by a few cells): a warm start with few steps
         ot.ot_index_train(self.tree, root=ot.OT_ROOT_MLP, n_leaf_models=self.n_leaf_models,
-                          n_mid_models=self.n_mid_models, epochs=2, batch=65536, lr=1e-3, seed=self.step_no)
+                          n_mid_models=self.n_mid_models, epochs=2, batch=65536, lr=1e-3, seed=self.step_no,
+                          steps=0 if prev is None else 64, init=prev)
         t = mark("index_train", t)
         n_leaves = ot.ot_octree_info(self.tree)[0]
         self.field = ot.ot_field_fourier(self.tree, w.modes.n, w.modes.amp, w.modes.phase)

@@ -105,3 +105,16 @@ def test_autotune_picks_a_valid_shape_and_keeps_results(ot):
     ot.ot_batch_run(b)
     torch.cuda.synchronize()
     assert torch.equal(um, ref_m) and torch.equal(up, ref_p)
+
+
+def test_warm_start_keeps_the_network_and_stays_exact(ot, clustered):
+    sph, ko, lo, P = clustered
+    tree = ot.ot_octree_build(sph, 3, 9)
+    ot.ot_index_train(tree, root=ot.OT_ROOT_MLP, n_leaf_models=4096, epochs=2, batch=16384, seed=5)
+    p0 = ot.ot_index_get_root_params(tree)
+    t2 = ot.ot_octree_build(sph, 3, 9)
+    ot.ot_index_train(t2, root=ot.OT_ROOT_MLP, n_leaf_models=4096, epochs=0, init=p0)
+    assert np.array_equal(ot.ot_index_get_root_params(t2), p0)  # no steps: the starting network
+    ot.ot_index_train(t2, root=ot.OT_ROOT_MLP, n_leaf_models=4096, steps=16, init=p0, lr=1e-4)
+    h = ot.ot_locate(t2, *pts(P.T), search=ot.OT_LEARNED)
+    assert np.array_equal(h.cpu().numpy(), oracle.locate_ub(ko, lo, *P.T))

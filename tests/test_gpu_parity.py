@@ -537,25 +537,23 @@ def test_mdf_matches_oracle(ot, tiny, tiny_fields, kernel, with_dv, torch_mod):
     assert torch.equal(u, u2) and torch.equal(f, f2)
 
 
-@pytest.mark.parametrize("n", [1, 33, 50000])
-def test_points_morton_order(ot, n, torch_mod):
-    """The permutation equals a stable sort of the points' level-21 Morton keys, truncated to
-    the bits left beside the index (an independent bit-loop encoder here)."""
-    rng = np.random.default_rng(n)
+@pytest.mark.parametrize("n,level", [(1, 8), (33, 19), (50000, 8), (50000, 5)])
+def test_points_morton_order(ot, n, level, torch_mod):
+    """The permutation equals a stable sort of the points' level-L Morton cell keys (an
+    independent bit-loop encoder here)."""
+    rng = np.random.default_rng(n + level)
     P = rng.uniform(0, 1, (3, n))
     if n > 40:
         P[:, :5] = P[:, 5:10]           # equal keys keep their input order
         P[0, 10] = 1.0                  # outside: last
-    perm = ot.ot_points_morton_order(*pts(P)).cpu().numpy()
-    q = np.floor(np.clip(P, 0, 1) * 2.0 ** 21).astype(np.uint64)
+    perm = ot.ot_points_morton_order(*pts(P), level=level).cpu().numpy()
+    q = np.floor(np.clip(P, 0, 1) * 2.0 ** level).astype(np.uint64)
     key = np.zeros(n, np.uint64)
-    for b in range(21):
+    for b in range(level):
         for d in range(3):
             key |= ((q[d] >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + d)
-    ib = max(1, int(np.ceil(np.log2(max(n, 2)))))
-    top = key >> np.uint64(ib - 1)
-    top[np.any((P < 0) | (P >= 1), axis=0)] = np.uint64((1 << (64 - ib)) - 1)
-    ref = np.argsort(top, kind="stable")
+    key[np.any((P < 0) | (P >= 1), axis=0)] = np.uint64((1 << (3 * level)) - 1)
+    ref = np.argsort(key, kind="stable")
     assert np.array_equal(perm, ref)
 
 
