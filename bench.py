@@ -611,10 +611,13 @@ def run_tracking(args):
     launches0 = ot.ot_launch_count()
     t0 = time.perf_counter()
     pts = 0
-    for _ in range(args.steps):
-        pts += tr.step()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        pts += tr.step(evs[k])
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
+    parts = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs)
+             for i, name in enumerate(("batch", "advect", "spread", "markers"))}
     clk = clocks.stop()
     out = {"metric": METRIC, "value": pts / el, "unit": "points/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
@@ -628,6 +631,7 @@ def run_tracking(args):
                       "l2": "inputs larger than L2; no flush"},
            "rebuild": {"rebuilds_timed": tr.timings["rebuilds"], "rebuild_s_timed": tr.timings["rebuild_s"],
                        "parts_s_timed": tr.timings.get("rebuild_parts_s"), "setup_s": setup_s},
+           "step_parts_ms": parts,
            "gpu_launches": int(ot.ot_launch_count() - launches0), "clocks": clk,
            "roofline": None, "cpu_baseline": None, "e2e": None}
     print(json.dumps(out), flush=True)

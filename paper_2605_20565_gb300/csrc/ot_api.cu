@@ -39,8 +39,10 @@ __global__ void k_advect(double* __restrict__ x, float* __restrict__ v, float* _
             const float am = first ? an : ap[d * n + i];
             const float vm = first ? vn : vp[d * n + i];
             v[d * n + i] = vn + dt * (1.5f * an - 0.5f * am);
-            double xn = x[d * n + i] + (double)dt * (1.5 * (double)vn - 0.5 * (double)vm);
-            if (periodic) {
+            // the displacement (well below one cell) in FP32, one FP64 add for the position:
+            // GB300's FP64 rate made the all-FP64 update the bound of this kernel
+            double xn = x[d * n + i] + (double)(dt * (1.5f * vn - 0.5f * vm));
+            if (periodic && (xn < 0.0 || xn >= 1.0)) {  // only points that crossed a wall
                 xn -= floor(xn);
                 if (xn >= 1.0) xn = 0.0;  // -tiny - floor(-tiny) rounds to 1
             }

@@ -133,18 +133,26 @@ class Tracker:
         self.timings["rebuild_s"] += time.time() - t0
         self.timings["rebuilds"] += 1
 
-    def step(self):
-        """One coupled step; returns the number of points located and interpolated."""
+    def step(self, events=None):
+        """One coupled step; returns the number of points located and interpolated.  events: an
+        optional list of 5 CUDA events recorded between the parts (batch, advect, spread,
+        markers)."""
         import paper_2605_20565_gb300 as ot
         K_P4, K_SORTED, _ = self.kinds
+        rec = (lambda k: events[k].record()) if events else (lambda k: None)
+        rec(0)
         ot.ot_batch_run(self.batch)
+        rec(1)
         ot.ot_advect_ab2(self.x, self.v, self.a_prev, self.v_prev, self.u, self.tau, self.re_coef, self.dt,
                          first=self.step_no == 0, periodic=True)
+        rec(2)
         self.f.zero_()
         ot.ot_spread(self.tree, K_P4, K_SORTED, self.mx[0], self.mx[1], self.mx[2], self.F, self.f, workspace=self.ws)
+        rec(3)
         self.step_no += 1
         self.t += self.dt
         self._place_markers()
+        rec(4)
         if self.step_no % self.rebuild_every == 0:
             self._rebuild()
         return self.x.shape[1] + self.mx.shape[1]
