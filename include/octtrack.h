@@ -299,6 +299,12 @@ typedef struct {
     int blocks_per_sm; /* resident blocks per SM, capped by occupancy (0: the occupancy max);
                           2 also selects the kernel compiled for 2 blocks per SM (more
                           registers per thread, no spills) instead of 3                    */
+    int order_level;   /* 0: points in the caller's order.  L in 1..21: each replay first sorts
+                          every trilinear group of >= 64 points by the Morton key of their
+                          level-L cells (on the device, inside the graph), interpolates them in
+                          that order (a warp's points then share host leaves and level-mates)
+                          and writes the results back in the caller's order; identical
+                          results                                                           */
 } ot_launch;
 
 /* Create a batch over groups (copied) reading d_field (float4 per leaf).  search selects
@@ -314,11 +320,11 @@ ot_status ot_batch_destroy(ot_batch* b);
 
 /* Autotuner of the batched launch (not in the paper): creates the batch for every launch
  * shape of {128, 256} threads x {1, 2, 4, 8} rows per work item x {occupancy max, 2} blocks
- * per SM and, when tune_map_level != 0, every level-map level from min(lmax, 6) to
- * min(lmax, 8); times `reps` graph replays of each (CUDA events on `stream`, after one
- * warm-up replay) and returns the fastest.  The octree is left at the chosen level-map level
+ * per SM x {caller's order, level-8 Morton order} and, when tune_map_level != 0, every
+ * level-map level from min(lmax, 6) to min(lmax, 8); times `reps` graph replays of each (CUDA
+ * events on `stream`, after one warm-up replay) and returns the fastest.  The octree is left at the chosen level-map level
  * (batches made earlier on it must be recreated).  The groups' outputs are overwritten.
- * Synchronises the stream; takes about (1 + reps) * 16 * levels replays. */
+ * Synchronises the stream; takes about (1 + reps) * 32 * levels replays. */
 typedef struct {
     ot_launch launch; /* fastest launch shape                                                */
     int map_level;    /* its level-map level                                                 */

@@ -72,7 +72,7 @@ class _Group(C.Structure):
 
 
 class _Launch(C.Structure):
-    _fields_ = [("block", C.c_int), ("tile", C.c_int), ("blocks_per_sm", C.c_int)]
+    _fields_ = [("block", C.c_int), ("tile", C.c_int), ("blocks_per_sm", C.c_int), ("order_level", C.c_int)]
 
 
 class _TuneResult(C.Structure):
@@ -393,7 +393,8 @@ def ot_batch_create(tree: Octree, groups, field, search: int = OT_BINARY, launch
     keep = [field] + list(groups)
     lp = None
     if launch:
-        lp = _Launch(launch.get("block", 0), launch.get("tile", 0), launch.get("blocks_per_sm", 0))
+        lp = _Launch(launch.get("block", 0), launch.get("tile", 0), launch.get("blocks_per_sm", 0),
+                     launch.get("order_level", 0))
     h = C.c_void_p()
     _check(_L().ot_batch_create(tree.handle, arr, len(groups), _dptr(field, torch.float32, "field"), search,
                                 C.byref(lp) if lp is not None else None, _stream(stream), C.byref(h)))
@@ -410,7 +411,8 @@ def ot_batch_autotune(tree: Octree, groups, field, search: int = OT_BINARY, tune
     r = _TuneResult()
     _check(_L().ot_batch_autotune(tree.handle, _groups(groups), len(groups), _dptr(field, torch.float32, "field"),
                                   search, int(tune_map_level), reps, _stream(stream), C.byref(r)))
-    return {"launch": {"block": r.launch.block, "tile": r.launch.tile, "blocks_per_sm": r.launch.blocks_per_sm},
+    return {"launch": {"block": r.launch.block, "tile": r.launch.tile, "blocks_per_sm": r.launch.blocks_per_sm,
+                       "order_level": r.launch.order_level},
             "map_level": r.map_level, "ms": r.ms, "tried": r.tried}
 
 

@@ -16,6 +16,7 @@
 struct ot_batch {
     const ot_octree* tree = nullptr;
     int n_groups = 0;
+    std::vector<void*> bufs;   // per ordered group: point-order workspace and the ordered copies
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned* d_counter = nullptr;
@@ -89,6 +90,36 @@ __global__ void __launch_bounds__(256, MINB) k_batch(TreeView t, BatchArgs a, co
 }
 
 
+// Ordered copies of a group's positions: the i-th ordered point is point (pairs[i] & mask).
+__global__ void __launch_bounds__(256) k_gather_points(const uint64_t* __restrict__ pairs, int64_t n, uint64_t mask,
+                                                       const double* __restrict__ x, const double* __restrict__ y,
+                                                       const double* __restrict__ z, double* __restrict__ xs,
+                                                       double* __restrict__ ys, double* __restrict__ zs) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = (int64_t)(pairs[i] & mask);
+        xs[i] = x[j];
+        ys[i] = y[j];
+        zs[i] = z[j];
+    }
+}
+
+// Results back to the caller's order.
+__global__ void __launch_bounds__(256) k_scatter_results(const uint64_t* __restrict__ pairs, int64_t n, uint64_t mask,
+                                                         const float* __restrict__ us, const int32_t* __restrict__ hs,
+                                                         float* __restrict__ u, int32_t* __restrict__ host) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = (int64_t)(pairs[i] & mask);
+        u[j] = us[i];
+        u[n + j] = us[n + i];
+        u[2 * n + j] = us[2 * n + i];
+        if (host) host[j] = hs[i];
+    }
+}
+
+unsigned grid_b(int64_t n) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8));
+}
+
 } // namespace ot
 
 using namespace ot;
@@ -101,7 +132,9 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     *out = nullptr;
     const int block = (launch && launch->block) ? launch->block : 256;
     const int tile = (launch && launch->tile) ? launch->tile : 4;
+    const int order_level = launch ? launch->order_level : 0;
     if (block < 64 || block > 256 || block % 32 || tile < 1 || tile > 64) return OT_ERR_ARG;
+    if (order_level < 0 || order_level > MAXLEVEL) return OT_ERR_ARG;
     BatchArgs a{};
     a.ng = n_groups;
     a.tile = tile;
@@ -126,6 +159,17 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     ot_batch* b = new ot_batch();
     b->tree = t;
     b->n_groups = n_groups;
+    // trilinear groups processed in Morton order of their points' level-order_level cells:
+    // per group, the sort workspace and ordered copies of positions and results
+    struct Ordered {
+        int k;                 // slot in a.g
+        GroupDev user;         // the caller's arrays
+        uint64_t* pairs;
+        double *xs, *ys, *zs;
+        float* us;
+        int32_t* hs;
+    };
+    std::vector<Ordered> ordered;
     cudaStream_t cs = nullptr;
     auto fail = [&](cudaError_t e) {
         if (cs) cudaStreamDestroy(cs);
@@ -134,12 +178,33 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     };
     cudaError_t e;
     if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned))) != cudaSuccess) return fail(e);
+    for (int k = 0; order_level > 0 && k < n_groups; ++k) {
+        GroupDev& d = a.g[k];
+        if (d.kernel != OT_TRILINEAR || d.n < 64 || !order_fits(d.n, order_level)) continue;
+        Ordered o{k, d, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        void* p = nullptr;
+        const size_t bytes = order_ws_bytes(d.n) + 3 * sizeof(double) * (size_t)d.n + 3 * sizeof(float) * (size_t)d.n +
+                             sizeof(int32_t) * (size_t)d.n + 4 * 256;
+        if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) return fail(e);
+        b->bufs.push_back(p);
+        char* c = static_cast<char*>(p);
+        auto take = [&](size_t sz) {
+            char* r = c;
+            c += (sz + 255) & ~(size_t)255;
+            return r;
+        };
+        o.pairs = reinterpret_cast<uint64_t*>(take(order_ws_bytes(d.n)));
+        o.xs = reinterpret_cast<double*>(take(sizeof(double) * d.n));
+        o.ys = reinterpret_cast<double*>(take(sizeof(double) * d.n));
+        o.zs = reinterpret_cast<double*>(take(sizeof(double) * d.n));
+        o.us = reinterpret_cast<float*>(take(3 * sizeof(float) * d.n));
+        o.hs = d.host ? reinterpret_cast<int32_t*>(take(sizeof(int32_t) * d.n)) : nullptr;
+        d.x = o.xs, d.y = o.ys, d.z = o.zs, d.u = o.us, d.host = o.hs;
+        ordered.push_back(o);
+    }
     bool has_tri = false;
     for (int k = 0; k < n_groups; ++k) has_tri = has_tri || groups[k].kernel == OT_TRILINEAR;
     if (has_tri && (e = cudaMalloc(&b->d_pyr, pyramid_bytes(t, sizeof(float)))) != cudaSuccess) return fail(e);
-    int pyr_kernels = 1 + t->pyr_level;  // base level and the coarser levels
-    for (int k = 0; k < node_levels(t); ++k) pyr_kernels += t->node_cnt[k] > 0 ? 1 : 0;
-    b->kernels = has_tri ? 1 + pyr_kernels : 1;
     TreeView v = tree_view(t);
     const size_t smem = 0;
     const bool two = launch && launch->blocks_per_sm == 2;
@@ -155,17 +220,39 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     const unsigned grid = (unsigned)(num_sms() * per_sm);
 
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    // the kernels captured below run at every replay: count them once here, as the replay's
+    const uint64_t launches0 = g_launches.load();
     if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e);
     cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), cs);
-    if (has_tri && launch_pyramid<float>(t, d_field, b->d_pyr, cs) != OT_OK) {
+    bool cap_ok = true;
+    std::vector<int> ibs;
+    for (const Ordered& o : ordered) {
+        int ib = 0;
+        cap_ok = cap_ok && launch_point_sort(o.user.x, o.user.y, o.user.z, o.user.n, order_level, o.pairs, &ib, cs) == OT_OK;
+        ibs.push_back(ib);
+        k_gather_points<<<grid_b(o.user.n), 256, 0, cs>>>(o.pairs, o.user.n, (1ULL << ib) - 1, o.user.x, o.user.y,
+                                                          o.user.z, o.xs, o.ys, o.zs);
+        count_launch();
+    }
+    if (cap_ok && has_tri) cap_ok = launch_pyramid<float>(t, d_field, b->d_pyr, cs) == OT_OK;
+    if (cap_ok) {
+        void* args[] = {&v, &a, (void*)&d_field, (void*)&b->d_pyr, &b->d_counter};
+        cap_ok = cudaLaunchKernel(kfn, dim3(grid), dim3(block), args, smem, cs) == cudaSuccess;
+        count_launch();
+    }
+    for (size_t i = 0; cap_ok && i < ordered.size(); ++i) {
+        const Ordered& o = ordered[i];
+        k_scatter_results<<<grid_b(o.user.n), 256, 0, cs>>>(o.pairs, o.user.n, (1ULL << ibs[i]) - 1, o.us, o.hs,
+                                                            o.user.u, o.user.host);
+        count_launch();
+    }
+    b->kernels = (int)(g_launches.load() - launches0);
+    g_launches.fetch_sub((uint64_t)b->kernels);
+    if (!cap_ok) {
         cudaGraph_t g = nullptr;
         cudaStreamEndCapture(cs, &g);
         if (g) cudaGraphDestroy(g);
         return fail(cudaErrorUnknown);
-    }
-    {
-        void* args[] = {&v, &a, (void*)&d_field, (void*)&b->d_pyr, &b->d_counter};
-        cudaLaunchKernel(kfn, dim3(grid), dim3(block), args, smem, cs);
     }
     e = cudaStreamEndCapture(cs, &b->graph);
     if (e != cudaSuccess) return fail(e);
@@ -189,6 +276,7 @@ extern "C" ot_status ot_batch_destroy(ot_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_pyr) cudaFree(b->d_pyr);
+    for (void* p : b->bufs) cudaFree(p);
     delete b;
     return OT_OK;
 }

@@ -119,6 +119,12 @@ ot_status build_node_lists(ot_octree* t, cudaStream_t s);
 size_t pyramid_bytes(const ot_octree* t, size_t elem);  // elem: sizeof the field type
 template <typename T> ot_status launch_pyramid(const ot_octree* t, const T* field, T* pyr, cudaStream_t s);
 
+// Morton order of points (ot_order.cu) ----------------------------------------------------------
+size_t order_ws_bytes(int64_t n);
+bool order_fits(int64_t n, int level);
+ot_status launch_point_sort(const double* x, const double* y, const double* z, int64_t n, int level,
+                            uint64_t* pairs, int* ib_out, cudaStream_t s);
+
 // spreading (ot_spread.cu) ---------------------------------------------------------------------
 size_t spread_ws_bytes(const ot_octree* t, int kernel, int64_t n);
 template <typename T>

@@ -45,6 +45,22 @@ unsigned grid_o(int64_t n) {
 
 size_t order_ws_bytes(int64_t n) { return 2 * sizeof(uint64_t) * (size_t)n + radix_ws_bytes(n) + 512; }
 
+bool order_fits(int64_t n, int level) { return level >= 1 && level <= MAXLEVEL && 3 * level + index_bits(n) <= 64; }
+
+// Sorts (cell key << ib | index) pairs of the n points into `pairs` (workspace: pairs, tmp and
+// the radix histograms, order_ws_bytes(n) bytes from `pairs`); the low ib bits of each sorted
+// pair are a point index.  Capturable in a CUDA graph.
+ot_status launch_point_sort(const double* x, const double* y, const double* z, int64_t n, int level,
+                            uint64_t* pairs, int* ib_out, cudaStream_t s) {
+    const int ib = index_bits(n);
+    *ib_out = ib;
+    uint64_t* tmp = pairs + n;
+    void* rws = tmp + n;
+    k_point_keys<<<grid_o(n), 256, 0, s>>>(x, y, z, n, level, ib, pairs);
+    count_launch();
+    return radix_sort_u64_ws(pairs, tmp, n, ib, ib + 3 * level, rws, s);
+}
+
 } // namespace ot
 
 using namespace ot;

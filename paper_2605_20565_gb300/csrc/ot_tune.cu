@@ -49,6 +49,7 @@ extern "C" ot_status ot_batch_autotune(ot_octree* t, const ot_group* groups, int
     const int blocks[] = {128, 256};
     const int tiles[] = {1, 2, 4, 8};
     const int per_sm[] = {0, 2};
+    const int orders[] = {0, 8};  // caller's order, or Morton order of level-8 cells
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     OT_CUDA(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -62,8 +63,8 @@ extern "C" ot_status ot_batch_autotune(ot_octree* t, const ot_group* groups, int
     const int start_level = t->lmap_level;
     for (int L : levels) {
         if (L != t->lmap_level && (err = ot_octree_set_map_level(t, L, stream)) != OT_OK) break;
-        for (int k = 0; k < 2 * 4 * 2 && err == OT_OK; ++k) {
-            const ot_launch lp{blocks[k / 8], tiles[(k / 2) % 4], per_sm[k % 2]};
+        for (int k = 0; k < 2 * 4 * 2 * 2 && err == OT_OK; ++k) {
+            const ot_launch lp{blocks[(k / 8) % 2], tiles[(k / 2) % 4], per_sm[k % 2], orders[k / 16]};
             const float ms = time_shape(t, groups, n_groups, d_field, search, lp, reps, s, e0, e1, &err);
             if (err != OT_OK || ms < 0.0f) continue;
             ++best.tried;

@@ -98,9 +98,10 @@ def test_autotune_picks_a_valid_shape_and_keeps_results(ot):
     ref_m = ot.ot_interpolate(tree, ot.OT_PESKIN4, mx, my, mz, field)
     ref_p = ot.ot_interpolate(tree, ot.OT_TRILINEAR, px, py, pz, field)
     r = ot.ot_batch_autotune(tree, groups, field, search=ot.OT_BINARY, tune_map_level=True, reps=1)
-    assert r["tried"] == 16  # lmax 5: one level-map level, 16 launch shapes
+    assert r["tried"] == 32  # lmax 5: one level-map level, 32 launch shapes (16 with the points ordered)
     assert r["map_level"] == 5 and r["ms"] > 0
     assert r["launch"]["block"] in (128, 256) and r["launch"]["tile"] in (1, 2, 4, 8)
+    assert r["launch"]["order_level"] in (0, 8)
     b = ot.ot_batch_create(tree, groups, field, search=ot.OT_BINARY, launch=r["launch"])
     ot.ot_batch_run(b)
     torch.cuda.synchronize()

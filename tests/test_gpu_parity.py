@@ -434,6 +434,29 @@ def test_batch_matches_single_ops(ot, tiny, tiny_fields, search, torch_mod):
     assert np.array_equal(hp.cpu().numpy(), oracle.locate_ub(ko, lo, *P))
 
 
+@pytest.mark.parametrize("order_level", [5, 8])
+def test_ordered_batch_gives_identical_results(ot, deep, order_level, torch_mod):
+    """Points interpolated in Morton order of their cells inside the graph, results written
+    back in the caller's order: the same values and hosts bit for bit."""
+    torch = torch_mod
+    sph, ko, lo, P, field = deep
+    t = ot.ot_octree_build(sph, 3, 9)
+    f32 = dev(field.astype(np.float32))
+    x, y, z = pts(P.T)
+    outs = []
+    for lv in (0, order_level):
+        u = torch.full((3, P.shape[0]), 7.0, device="cuda")
+        h = torch.full((P.shape[0],), -5, dtype=torch.int32, device="cuda")
+        b = ot.ot_batch_create(t, [dict(kernel=ot.OT_TRILINEAR, x=x, y=y, z=z, u=u, host=h)], f32,
+                               launch=dict(order_level=lv))
+        ot.ot_batch_run(b)
+        ot.ot_batch_run(b)
+        torch.cuda.synchronize()
+        outs.append((u, h))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[1][1].cpu().numpy(), oracle.locate_ub(ko, lo, *P.T))
+
+
 # ---------------------------------------------------------------------------------------
 # Advection step
 # ---------------------------------------------------------------------------------------
