@@ -67,6 +67,7 @@ def _L():
                 "or_mlp_loss_grad": (dbl, [P, P, P, i64, P]),
                 "or_advect_ab2": (None, [P, P, P, P, P, i64, dbl, dbl, dbl, i32, i32]),
                 "or_ibm_mdf": (i64, [P, P, i64, i32, i32, P, P, P, P, P, P, i64, dbl, dbl, i32, P, P, P]),
+                "or_body_sums": (None, [P, P, P, P, P, dbl, i64, P, i32, P, dbl, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -220,6 +221,25 @@ def ibm_mdf(keys, levels, lmax, kernel, u_star, X, U, rho, dt, n_iter, dV=None):
     bad = _L().or_ibm_mdf(_p(k), _p(l), k.size, lmax, kernel, _p(us), _p(x), _p(y), _p(z), _p(Uc), dvp, x.size,
                           rho, dt, n_iter, _p(u), _p(f), _p(slip))
     return u, f, slip, int(bad)
+
+
+def body_sums(X, v, start, xb, scale, dV=None, w=1.0):
+    """Per-body (lin, ang), each (nb, 3): scale * sum v w and scale * sum (X - x_b) x v w over
+    the markers start[b] .. start[b+1]-1 (Sec. 2.3)."""
+    x, y, z = _pts(*np.asarray(X, np.float64))
+    vv = _c(v, np.float64).reshape(3, -1)
+    st = _c(start, np.int64)
+    xbc = _c(xb, np.float64).reshape(-1, 3)
+    nb = xbc.shape[0]
+    dvp = None
+    if dV is not None:
+        dV = _c(dV, np.float64)
+        dvp = _p(dV)
+    lin = np.empty((nb, 3))
+    ang = np.empty((nb, 3))
+    _L().or_body_sums(_p(x), _p(y), _p(z), _p(vv), dvp, float(w), x.size, _p(st), nb, _p(xbc), float(scale),
+                      _p(lin), _p(ang))
+    return lin, ang
 
 
 # --- Learned-index root network (1 -> 32 ReLU -> 1) ------------------------------------

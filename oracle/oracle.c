@@ -30,6 +30,9 @@
  *                                       level-mates beyond constant-field reproduction
  *   or_mlp_loss_grad .................. pinned (central finite differences)
  *   or_advect_ab2 ..................... pinned (closed-form relaxation of a constant field)
+ *   or_body_sums ...................... pinned (uniform translation gives P = rho V u; a rigid
+ *                                       rotation gives L = rho I Omega with I from the tensor
+ *                                       form; torque of a force through the centre vanishes)
  *   or_ibm_mdf ........................ pinned (slip recursion s' = s - A s / rho against a
  *                                       brute-force interpolation-spreading matrix A, monotone
  *                                       slip decrease, force conservation, zero-slip fixed point)
@@ -556,6 +559,36 @@ int64_t or_ibm_mdf(const uint64_t *key, const uint8_t *level, int64_t n, int lma
     free(Fk);
     free(F);
     return nbad;
+}
+
+/* Per-body linear and angular sums of a marker quantity (Sec. 2.3, rigid bodies):
+ *   lin_b = scale * sum_{k in b} v_k w_k,   ang_b = scale * sum_{k in b} (X_k - x_b) x v_k w_k,
+ * with w_k = dV[k] (or w when dV is NULL).  With v = u at the internal markers and
+ * scale = rho_f these are the internal fluid's linear momentum P and angular momentum L; with
+ * v = F_k at the surface markers and scale = -1, the IBM force and torque -sum F_k dV_k and
+ * -sum (X_k - x_b) x F_k dV_k.  The printed formulas swap the names P and L against the
+ * text (linear momentum P, angular momentum L) and drop rho_f from the discrete sums; read
+ * with the text and the integrals.  Markers of body b are start[b] .. start[b+1]-1.
+ * v: 3 planes of n; xb: nb x 3; lin, ang: nb x 3. */
+void or_body_sums(const double *x, const double *y, const double *z, const double *v, const double *dV, double w,
+                  int64_t n, const int64_t *start, int nb, const double *xb, double scale, double *lin,
+                  double *ang) {
+    for (int b = 0; b < nb; ++b) {
+        double l[3] = {0.0, 0.0, 0.0}, a[3] = {0.0, 0.0, 0.0};
+        for (int64_t k = start[b]; k < start[b + 1]; ++k) {
+            double wk = dV ? dV[k] : w;
+            double vv[3] = {v[k] * wk, v[n + k] * wk, v[2 * n + k] * wk};
+            double r[3] = {x[k] - xb[3 * b], y[k] - xb[3 * b + 1], z[k] - xb[3 * b + 2]};
+            for (int d = 0; d < 3; ++d) l[d] += vv[d];
+            a[0] += r[1] * vv[2] - r[2] * vv[1];
+            a[1] += r[2] * vv[0] - r[0] * vv[2];
+            a[2] += r[0] * vv[1] - r[1] * vv[0];
+        }
+        for (int d = 0; d < 3; ++d) {
+            lin[3 * b + d] = scale * l[d];
+            ang[3 * b + d] = scale * a[d];
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------------------ */

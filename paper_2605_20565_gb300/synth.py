@@ -257,6 +257,27 @@ def _markers_on(centres, diams, counts, seed):
     return np.concatenate(pos, 1), np.concatenate(nrm, 1), np.concatenate(grp)
 
 
+def internal_markers(centres, diameters, h: float):
+    """Lagrangian points inside each body on a cubic lattice of spacing h centred on the body
+    (the internal markers of Sec. 2.3, spacing the finest cell): the points c + h (i, j, k)
+    with |h (i, j, k)| < r - h/2.  Returns positions (3, n) grouped by body and the offsets
+    start (nb + 1,) of each body's markers."""
+    centres = np.asarray(centres, np.float64).reshape(-1, 3)
+    diameters = np.asarray(diameters, np.float64).reshape(-1)
+    pts, start = [], [0]
+    for c, d in zip(centres, diameters):
+        r = 0.5 * d
+        m = int(np.floor(r / h))
+        g = np.arange(-m, m + 1, dtype=np.float64) * h
+        gx, gy, gz = np.meshgrid(g, g, g, indexing="ij")
+        off = np.stack([gx.ravel(), gy.ravel(), gz.ravel()])
+        keep = (off ** 2).sum(0) < (r - 0.5 * h) ** 2
+        pts.append(c[:, None] + off[:, keep])
+        start.append(start[-1] + int(keep.sum()))
+    X = np.concatenate(pts, axis=1) if pts else np.zeros((3, 0))
+    return np.ascontiguousarray(X), np.asarray(start, np.int64)
+
+
 def tiny(seed: int = 0) -> Workload:
     """Levels 3-5 refined to 5 within 0.1 of the sphere c = (.5,.5,.5), r = 0.2; 1,000
     Fibonacci markers with F = outward unit normal; 10,000 uniform particles."""

@@ -402,6 +402,45 @@ def test_mdf_slip_decreases_and_fixed_point(tiny_tree, tiny_workload):
 
 
 # ---------------------------------------------------------------------------------------
+# Rigid bodies: internal-marker momenta and IBM force / torque sums (Sec. 2.3)
+# ---------------------------------------------------------------------------------------
+
+def test_body_sums_closed_forms():
+    rng = np.random.default_rng(3)
+    cs = np.array([[0.3, 0.4, 0.5], [0.7, 0.6, 0.35]])
+    ds = np.array([0.1, 0.06])
+    h = 1.0 / 256
+    X, start = synth.internal_markers(cs, ds, h)
+    w = h ** 3
+    rho = 1.3
+    xb = cs
+    body = np.repeat(np.arange(2), np.diff(start))
+    r = X - cs[body].T
+    # uniform translation: P = rho V U, and no angular momentum (the lattice is symmetric)
+    U0 = np.array([0.2, -0.1, 0.35])
+    v = np.tile(U0[:, None], (1, X.shape[1]))
+    lin, ang = oracle.body_sums(X, v, start, xb, rho, w=w)
+    for b in range(2):
+        nb = start[b + 1] - start[b]
+        assert np.allclose(lin[b], rho * nb * w * U0, rtol=1e-12)
+        assert np.abs(ang[b]).max() < 1e-12 * nb * w
+    # rigid rotation u = Omega x r: L = rho I Omega with I = sum w (|r|^2 1 - r r^T) (tensor form)
+    Om = rng.normal(size=3)
+    v = np.cross(Om[:, None], r, axis=0)
+    lin, ang = oracle.body_sums(X, v, start, xb, rho, dV=np.full(X.shape[1], w))
+    for b in range(2):
+        rb = r[:, start[b]:start[b + 1]]
+        I = w * ((rb ** 2).sum() * np.eye(3) - rb @ rb.T)
+        assert np.allclose(ang[b], rho * I @ Om, rtol=1e-10)
+        assert np.abs(lin[b]).max() < 1e-12
+    # IBM force through the centre (F parallel to r): no torque; total force summed with sign
+    F = r * rng.uniform(0.5, 2.0, X.shape[1])
+    lin, ang = oracle.body_sums(X, F, start, xb, -1.0, w=w)
+    assert np.abs(ang).max() < 1e-14
+    assert np.allclose(lin[0], -w * F[:, :start[1]].sum(1), rtol=1e-12, atol=1e-16)
+
+
+# ---------------------------------------------------------------------------------------
 # Trilinear interpolation of point particles (Sec. 2.3.2)
 # ---------------------------------------------------------------------------------------
 
