@@ -477,6 +477,32 @@ def run_ours(args):
                "note": "workspace allocation included; field sweeps over all leaves per round"}
         del um_, U0
 
+    # internal-fluid momenta of the bodies (Sec. 2.3): trilinear velocity at the internal markers
+    # (a lattice of the finest cell inside each bubble), then the per-body sums
+    bodies = None
+    if not args.no_mdf and w.extra and "centres" in w.extra:
+        hmin = 2.0 ** -w.lmax
+        Xi, st_i = synth.internal_markers(w.extra["centres"], w.extra["diameters"], hmin)
+        xi, yi, zi = to_dev(Xi)
+        d_start = torch.as_tensor(st_i, device=dev)
+        xb = torch.as_tensor(np.ascontiguousarray(w.extra["centres"]), device=dev)
+        ui = torch.empty((3, Xi.shape[1]), dtype=torch.float32, device=dev)
+
+        def momenta():
+            ot.ot_interpolate(tree, ot.OT_TRILINEAR, xi, yi, zi, field, u=ui)
+            return ot.ot_body_sums(xi, yi, zi, ui, d_start, xb, 1.0, w=hmin ** 3)
+
+        momenta()
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        for _ in range(3):
+            momenta()
+        b_.record(stream)
+        torch.cuda.synchronize()
+        bodies = {"bodies": int(len(st_i) - 1), "internal_markers": int(Xi.shape[1]),
+                  "ms": a_.elapsed_time(b_) / 3, "what": "trilinear u at internal markers + per-body P and L"}
+        del xi, yi, zi, ui
+
     # the other forms, same steps (the chosen form's level map is restored afterwards)
     forms = {chosen: {"step_ms": ms_step, "locate_interpolate_ms": batch_ms, "spread_ms": spread_ms}}
     groups_t = {}
@@ -576,7 +602,7 @@ def run_ours(args):
            "breakdown_ms": {"locate_interpolate": batch_ms, "spread": spread_ms, "step": ms_step},
            "locate_interpolate_points_per_s": world * npts / (batch_ms / 1e3),
            "forms": forms, "learned_vs_plain": learned_vs_plain, "groups_ms": groups_t, "autotune": tune,
-           "mdf": mdf,
+           "mdf": mdf, "body_momenta": bodies,
            "index": {"n_mid": n_mid, "n_leaf": n_leaf, "mean_window": istats["mean_window"], "max_window": istats["max_window"],
                      "empty_models": istats["empty_models"], "fallbacks_timed": fb,
                      "mean_probes": istats["mean_probes"],

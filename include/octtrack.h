@@ -279,6 +279,21 @@ ot_status ot_ibm_mdf(const ot_octree* t, int kernel, const double* d_x, const do
                      float* d_f, float* d_slip, void* d_workspace, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Rigid bodies (Sec. 2.3): per-body linear and angular sums of a marker quantity v,
+ *   d_lin[b] = scale sum_{k in b} v_k w_k,  d_ang[b] = scale sum_{k in b} (X_k - x_b) x v_k w_k,
+ * w_k = d_dV[k] (or w when d_dV is NULL).  With v = u at the internal markers (interpolated,
+ * e.g. trilinear, since the body interior need not be refined) and scale = rho_f: the internal
+ * fluid's linear momentum P and angular momentum L (the printed sums swap the two names
+ * against the text and omit rho_f); with v = F_k at the surface markers and scale = -1: the
+ * IBM force -sum F_k dV_k and torque -sum (X_k - x_b) x F_k dV_k.  The markers of body b are
+ * d_start[b] .. d_start[b+1]-1 (device int64, n_bodies + 1 entries); d_xb: n_bodies x 3 body
+ * centres; d_lin, d_ang: n_bodies x 3 doubles.  FP64 sums in a fixed order (deterministic).
+ * -------------------------------------------------------------------------------------*/
+ot_status ot_body_sums(const double* d_x, const double* d_y, const double* d_z, const float* d_v, const float* d_dV,
+                       float w, int64_t n, const int64_t* d_start, int n_bodies, const double* d_xb, double scale,
+                       double* d_lin, double* d_ang, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Batched launch: every group of points (IBM markers with a delta kernel, point particles
  * with trilinear) located and interpolated by ONE persistent kernel, captured once in a
  * CUDA graph and replayed.

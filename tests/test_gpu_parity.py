@@ -591,3 +591,38 @@ def test_field_fourier_matches_modes(ot, deep):
     ref = synth.fourier_field(m, oracle.leaf_centres(ko, lo))
     assert np.abs(f[:, :3] - ref[:, :3]).max() <= 1e-6 * np.abs(ref).max()
     assert np.all(f[:, 3] == 0)
+
+
+def test_body_sums_match_oracle(ot, deep, torch_mod):
+    """Internal-fluid momenta of each body from trilinear velocities at its internal markers,
+    and the IBM force and torque of surface-marker forces (Sec. 2.3), against the oracle."""
+    torch = torch_mod
+    from paper_2605_20565_gb300 import synth
+    sph, ko, lo, P, field = deep
+    t = ot.ot_octree_build(sph, 3, 9)
+    h = 2.0 ** -9
+    X, start = synth.internal_markers(sph[:, :3], 2.0 * sph[:, 3], h)
+    f32 = field.astype(np.float32)
+    u = ot.ot_interpolate(t, ot.OT_TRILINEAR, *pts(X), dev(f32))
+    href = oracle.locate_ub(ko, lo, *X)
+    uref = oracle.interp_trilinear(ko, lo, f32.astype(np.float64), *X, href)
+    rho = 1.2
+    d_start = torch.as_tensor(start, device="cuda")
+    xb = torch.as_tensor(np.ascontiguousarray(sph[:, :3]), device="cuda")
+    lin, ang = ot.ot_body_sums(*pts(X), u, d_start, xb, rho, w=h ** 3)
+    lref, aref = oracle.body_sums(X, uref, start, sph[:, :3], rho, w=h ** 3)
+    assert rel_err(lin.cpu().numpy(), lref) <= TOL32
+    assert rel_err(ang.cpu().numpy(), aref) <= TOL32
+    # surface forces with marker volumes
+    rng = np.random.default_rng(8)
+    Xs = np.concatenate([synth.fibonacci_sphere(500, sph[b, :3], sph[b, 3])[0] for b in range(2)], axis=1)
+    ss = np.array([0, 500, 1000])
+    F = rng.normal(size=(3, 1000)).astype(np.float32)
+    dV = rng.uniform(0.5, 1.5, 1000).astype(np.float32) * h ** 3
+    lin, ang = ot.ot_body_sums(*pts(Xs), dev(F), torch.as_tensor(ss, device="cuda"), xb, -1.0, dV=dev(dV))
+    lref, aref = oracle.body_sums(Xs, F.astype(np.float64), ss, sph[:, :3], -1.0, dV=dV.astype(np.float64))
+    assert np.allclose(lin.cpu().numpy(), lref, rtol=1e-9, atol=1e-16)
+    assert np.allclose(ang.cpu().numpy(), aref, rtol=1e-9, atol=1e-18)
+    # deterministic
+    lin2, ang2 = ot.ot_body_sums(*pts(Xs), dev(F), torch.as_tensor(ss, device="cuda"), xb, -1.0, dV=dev(dV))
+    assert torch.equal(lin, lin2) and torch.equal(ang, ang2)
