@@ -68,6 +68,10 @@ def _L():
                 "or_advect_ab2": (None, [P, P, P, P, P, i64, dbl, dbl, dbl, i32, i32]),
                 "or_ibm_mdf": (i64, [P, P, i64, i32, i32, P, P, P, P, P, P, i64, dbl, dbl, i32, P, P, P]),
                 "or_body_sums": (None, [P, P, P, P, P, dbl, i64, P, i32, P, dbl, P, P]),
+                "or_interp_delta_p": (i64, [P, P, i64, i32, i32, P, P, P, P, i64, P, i32]),
+                "or_spread_delta_p": (i64, [P, P, i64, i32, i32, P, P, P, P, P, i64, P, i32]),
+                "or_interp_trilinear_p": (None, [P, P, i64, P, P, P, P, P, i64, P, i32]),
+                "or_field_mean": (None, [P, i64, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -168,17 +172,19 @@ def phi(kernel: int, r) -> np.ndarray:
     return out
 
 
-def interp_delta(keys, levels, lmax, kernel, field, x, y, z):
-    """u (3, n) and the count of skipped stencil cells.  field: (N, 4) float64."""
+def interp_delta(keys, levels, lmax, kernel, field, x, y, z, periodic: bool = False):
+    """u (3, n) and the count of skipped stencil cells.  field: (N, 4) float64.  periodic: the
+    stencil wraps around the unit cube."""
     k, l = _c(keys, np.uint64), _c(levels, np.uint8)
     f = _c(field, np.float64).reshape(-1, 4)
     x, y, z = _pts(x, y, z)
     u = np.empty((3, x.size), np.float64)
-    bad = _L().or_interp_delta(_p(k), _p(l), k.size, lmax, kernel, _p(f), _p(x), _p(y), _p(z), x.size, _p(u))
+    bad = _L().or_interp_delta_p(_p(k), _p(l), k.size, lmax, kernel, _p(f), _p(x), _p(y), _p(z), x.size, _p(u),
+                                 int(periodic))
     return u, int(bad)
 
 
-def spread_delta(keys, levels, lmax, kernel, x, y, z, F, dV=None, f=None):
+def spread_delta(keys, levels, lmax, kernel, x, y, z, F, dV=None, f=None, periodic: bool = False):
     """f (N, 4) accumulated in place (zeros when f is None) and the skipped-cell count."""
     k, l = _c(keys, np.uint64), _c(levels, np.uint8)
     x, y, z = _pts(x, y, z)
@@ -190,18 +196,29 @@ def spread_delta(keys, levels, lmax, kernel, x, y, z, F, dV=None, f=None):
     if dV is not None:
         dV = _c(dV, np.float64)
         dvp = _p(dV)
-    bad = _L().or_spread_delta(_p(k), _p(l), k.size, lmax, kernel, _p(x), _p(y), _p(z), _p(F), dvp, x.size, _p(f))
+    bad = _L().or_spread_delta_p(_p(k), _p(l), k.size, lmax, kernel, _p(x), _p(y), _p(z), _p(F), dvp, x.size, _p(f),
+                                 int(periodic))
     return f, int(bad)
 
 
-def interp_trilinear(keys, levels, field, x, y, z, host):
+def interp_trilinear(keys, levels, field, x, y, z, host, periodic: bool = False):
     k, l = _c(keys, np.uint64), _c(levels, np.uint8)
     f = _c(field, np.float64).reshape(-1, 4)
     x, y, z = _pts(x, y, z)
     h = _c(host, np.int32)
     u = np.empty((3, x.size), np.float64)
-    _L().or_interp_trilinear(_p(k), _p(l), k.size, _p(f), _p(x), _p(y), _p(z), _p(h), x.size, _p(u))
+    _L().or_interp_trilinear_p(_p(k), _p(l), k.size, _p(f), _p(x), _p(y), _p(z), _p(h), x.size, _p(u),
+                               int(periodic))
     return u
+
+
+def field_mean(levels, field) -> np.ndarray:
+    """Volume-weighted mean over the unit cube of a cell field (N, 4): (3,)."""
+    l = _c(levels, np.uint8)
+    f = _c(field, np.float64).reshape(-1, 4)
+    m = np.empty(3, np.float64)
+    _L().or_field_mean(_p(l), l.size, _p(f), _p(m))
+    return m
 
 
 def ibm_mdf(keys, levels, lmax, kernel, u_star, X, U, rho, dt, n_iter, dV=None):

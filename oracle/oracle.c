@@ -30,6 +30,10 @@
  *                                       level-mates beyond constant-field reproduction
  *   or_mlp_loss_grad .................. pinned (central finite differences)
  *   or_advect_ab2 ..................... pinned (closed-form relaxation of a constant field)
+ *   periodic variants (_p) ............ pinned (uniform periodic trees against independent
+ *                                       numpy sums over wrapped indices and scipy trilinear on
+ *                                       a wrap-padded grid; spread conservation at the walls)
+ *   or_field_mean ..................... pinned (constant field; zero after subtraction)
  *   or_body_sums ...................... pinned (uniform translation gives P = rho V u; a rigid
  *                                       rotation gives L = rho I Omega with I from the tensor
  *                                       form; torque of a force through the centre vanishes)
@@ -436,9 +440,17 @@ static double phi(int kernel, double r) { return kernel == 2 ? or_phi_peskin4(r)
 
 /* Leaf index of the finest-level cell (i,j,k), or -1 when the cell is outside the domain or
  * is not a leaf of level lmax (IBM operations live on the finest level only, Sec. 2.4). */
-static int64_t fine_leaf(const uint64_t *key, const uint8_t *level, int64_t n, int lmax, int64_t i, int64_t j,
-                         int64_t k) {
+/* Periodic domain (Sec. 5.2's turbulence box): cell indices wrap modulo the cells per axis. */
+static int64_t wrap_index(int64_t i, int64_t nc) { return ((i % nc) + nc) % nc; }
+
+static int64_t fine_leaf_p(const uint64_t *key, const uint8_t *level, int64_t n, int lmax, int64_t i, int64_t j,
+                           int64_t k, int periodic) {
     int64_t nc = (int64_t)1 << lmax;
+    if (periodic) {
+        i = wrap_index(i, nc);
+        j = wrap_index(j, nc);
+        k = wrap_index(k, nc);
+    }
     if (i < 0 || j < 0 || k < 0 || i >= nc || j >= nc || k >= nc) return -1;
     uint64_t q = or_morton((uint32_t)(i << (OR_MAXLEVEL - lmax)), (uint32_t)(j << (OR_MAXLEVEL - lmax)),
                            (uint32_t)(k << (OR_MAXLEVEL - lmax)));
@@ -452,9 +464,9 @@ static int64_t fine_leaf(const uint64_t *key, const uint8_t *level, int64_t n, i
  * kernel: 2 = Peskin-4, 3 = Roma-3.  field: N x 4 (x, y, z, unused).  u: 3 planes of np.
  * Stencil cells that are outside the domain or not finest-level leaves are skipped and
  * counted in *n_bad (returned). */
-int64_t or_interp_delta(const uint64_t *key, const uint8_t *level, int64_t n, int lmax, int kernel,
-                        const double *field, const double *x, const double *y, const double *z, int64_t np,
-                        double *u) {
+int64_t or_interp_delta_p(const uint64_t *key, const uint8_t *level, int64_t n, int lmax, int kernel,
+                          const double *field, const double *x, const double *y, const double *z, int64_t np,
+                          double *u, int periodic) {
     int64_t nbad = 0;
     int wdt = stencil_width(kernel);
     double scale = ldexp(1.0, lmax);
@@ -467,7 +479,7 @@ int64_t or_interp_delta(const uint64_t *key, const uint8_t *level, int64_t n, in
         for (int c = 0; c < wdt; ++c)
             for (int b = 0; b < wdt; ++b)
                 for (int a = 0; a < wdt; ++a) {
-                    int64_t leaf = fine_leaf(key, level, n, lmax, i0[0] + a, i0[1] + b, i0[2] + c);
+                    int64_t leaf = fine_leaf_p(key, level, n, lmax, i0[0] + a, i0[1] + b, i0[2] + c, periodic);
                     if (leaf < 0) {
                         nbad++;
                         continue;
@@ -486,9 +498,9 @@ int64_t or_interp_delta(const uint64_t *key, const uint8_t *level, int64_t n, in
  * with dV_k = dx^3 when dV is NULL (the paper's literal form, Eq. for F(x)).
  * F: 3 planes of np.  f: N x 4, accumulated (component 3 untouched).  Sequential over
  * markers.  Returns the number of skipped stencil cells. */
-int64_t or_spread_delta(const uint64_t *key, const uint8_t *level, int64_t n, int lmax, int kernel,
-                        const double *x, const double *y, const double *z, const double *F, const double *dV,
-                        int64_t np, double *f) {
+int64_t or_spread_delta_p(const uint64_t *key, const uint8_t *level, int64_t n, int lmax, int kernel,
+                          const double *x, const double *y, const double *z, const double *F, const double *dV,
+                          int64_t np, double *f, int periodic) {
     int64_t nbad = 0;
     int wdt = stencil_width(kernel);
     double scale = ldexp(1.0, lmax);
@@ -501,7 +513,7 @@ int64_t or_spread_delta(const uint64_t *key, const uint8_t *level, int64_t n, in
         for (int c = 0; c < wdt; ++c)
             for (int b = 0; b < wdt; ++b)
                 for (int a = 0; a < wdt; ++a) {
-                    int64_t leaf = fine_leaf(key, level, n, lmax, i0[0] + a, i0[1] + b, i0[2] + c);
+                    int64_t leaf = fine_leaf_p(key, level, n, lmax, i0[0] + a, i0[1] + b, i0[2] + c, periodic);
                     if (leaf < 0) {
                         nbad++;
                         continue;
@@ -512,6 +524,27 @@ int64_t or_spread_delta(const uint64_t *key, const uint8_t *level, int64_t n, in
                 }
     }
     return nbad;
+}
+
+int64_t or_interp_delta(const uint64_t *key, const uint8_t *level, int64_t n, int lmax, int kernel,
+                        const double *field, const double *x, const double *y, const double *z, int64_t np,
+                        double *u) {
+    return or_interp_delta_p(key, level, n, lmax, kernel, field, x, y, z, np, u, 0);
+}
+
+int64_t or_spread_delta(const uint64_t *key, const uint8_t *level, int64_t n, int lmax, int kernel,
+                        const double *x, const double *y, const double *z, const double *F, const double *dV,
+                        int64_t np, double *f) {
+    return or_spread_delta_p(key, level, n, lmax, kernel, x, y, z, F, dV, np, f, 0);
+}
+
+/* Volume-weighted mean of a cell field over the unit cube, sum_c f_c 8^-level_c (the mean
+ * force removed in a periodic box, Sec. 5.2), and its subtraction from every cell. */
+void or_field_mean(const uint8_t *level, int64_t n, const double *f, double mean[3]) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t c = 0; c < n; ++c)
+        for (int d = 0; d < 3; ++d) acc[d] += f[4 * c + d] * ldexp(1.0, -3 * level[c]);
+    for (int d = 0; d < 3; ++d) mean[d] = acc[d];
 }
 
 /* Multi-direct forcing (Sec. 2.2): n_iter rounds, each
@@ -624,9 +657,9 @@ static void levelmate_value(const uint64_t *key, const uint8_t *level, int64_t n
 }
 
 /* host: leaf of each point (from a locate), -1 entries give NaN.  u: 3 planes of np. */
-void or_interp_trilinear(const uint64_t *key, const uint8_t *level, int64_t n, const double *field,
-                         const double *x, const double *y, const double *z, const int32_t *host, int64_t np,
-                         double *u) {
+void or_interp_trilinear_p(const uint64_t *key, const uint8_t *level, int64_t n, const double *field,
+                           const double *x, const double *y, const double *z, const int32_t *host, int64_t np,
+                           double *u, int periodic) {
 #pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < np; ++p) {
         if (host[p] < 0) {
@@ -653,7 +686,7 @@ void or_interp_trilinear(const uint64_t *key, const uint8_t *level, int64_t n, c
             for (int d = 0; d < 3; ++d) {
                 int off = (corner >> d) & 1;
                 m[d] = c[d] + off * sgn[d];
-                if (m[d] < 0 || m[d] >= ncell) m[d] = c[d];
+                if (m[d] < 0 || m[d] >= ncell) m[d] = periodic ? wrap_index(m[d], ncell) : c[d];
                 w *= off ? fabs(t[d]) : 1.0 - fabs(t[d]);
             }
             double v[3];
@@ -746,4 +779,10 @@ void or_advect_ab2(double *x, double *v, double *a_prev, double *v_prev, const d
 /* Vectorised delta-kernel evaluation for tests: kernel 2 = Peskin-4, 3 = Roma-3. */
 void or_phi_array(int kernel, const double *r, int64_t n, double *out) {
     for (int64_t i = 0; i < n; ++i) out[i] = phi(kernel, r[i]);
+}
+
+void or_interp_trilinear(const uint64_t *key, const uint8_t *level, int64_t n, const double *field,
+                         const double *x, const double *y, const double *z, const int32_t *host, int64_t np,
+                         double *u) {
+    or_interp_trilinear_p(key, level, n, field, x, y, z, host, np, u, 0);
 }

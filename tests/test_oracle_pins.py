@@ -402,6 +402,87 @@ def test_mdf_slip_decreases_and_fixed_point(tiny_tree, tiny_workload):
 
 
 # ---------------------------------------------------------------------------------------
+# Periodic box (Sec. 5.2): wrapped stencils and level-mates, mean force
+# ---------------------------------------------------------------------------------------
+
+def _uniform_periodic(lev, seed):
+    ko, lo = oracle.octree_build(np.zeros((0, 5)), lev, lev)
+    nc = 1 << lev
+    ii, jj, kk = np.meshgrid(np.arange(nc), np.arange(nc), np.arange(nc), indexing="ij")
+    sh = np.uint64(21 - lev)
+    keys = morton_np(ii.ravel().astype(np.uint64) << sh, jj.ravel().astype(np.uint64) << sh,
+                     kk.ravel().astype(np.uint64) << sh)
+    leaf = np.searchsorted(ko, keys).reshape(nc, nc, nc)  # leaf index of cell (i, j, k)
+    rng = np.random.default_rng(seed)
+    F = rng.normal(size=(nc, nc, nc, 3))
+    field = np.zeros((ko.size, 4))
+    field[leaf.ravel(), :3] = F.reshape(-1, 3)
+    return ko, lo, nc, F, field, rng
+
+
+@pytest.mark.parametrize("kernel,width", [(2, 4), (3, 3)])
+def test_periodic_delta_interp_wraps(kernel, width):
+    lev = 4
+    ko, lo, nc, F, field, rng = _uniform_periodic(lev, 5)
+    P = np.concatenate([rng.uniform(0, 1, (200, 3)), rng.uniform(0, 1.5 / nc, (100, 3)),
+                        1.0 - rng.uniform(0, 1.5 / nc, (100, 3))])
+    u, bad = oracle.interp_delta(ko, lo, lev, kernel, field, *P.T, periodic=True)
+    assert bad == 0
+    ref = np.zeros((3, P.shape[0]))
+    for p, x in enumerate(P):
+        s = x * nc - 0.5
+        i0 = (np.floor(s).astype(int) - 1) if kernel == 2 else (np.floor(s + 0.5).astype(int) - 1)
+        for a in range(width):
+            for b in range(width):
+                for c in range(width):
+                    w = (oracle.phi(kernel, [s[0] - (i0[0] + a)])[0] * oracle.phi(kernel, [s[1] - (i0[1] + b)])[0] *
+                         oracle.phi(kernel, [s[2] - (i0[2] + c)])[0])
+                    ref[:, p] += w * F[(i0[0] + a) % nc, (i0[1] + b) % nc, (i0[2] + c) % nc]
+    assert np.abs(u - ref).max() < 1e-12
+    # non-periodic: the same points near the walls lose stencil cells
+    _, bad_np = oracle.interp_delta(ko, lo, lev, kernel, field, *P.T)
+    assert bad_np > 0
+
+
+def test_periodic_trilinear_matches_wrapped_grid():
+    from scipy.interpolate import RegularGridInterpolator
+    lev = 4
+    ko, lo, nc, F, field, rng = _uniform_periodic(lev, 6)
+    Fp = np.pad(F, ((1, 1), (1, 1), (1, 1), (0, 0)), mode="wrap")
+    g = (np.arange(-1, nc + 1) + 0.5) / nc
+    P = np.concatenate([rng.uniform(0, 1, (300, 3)), rng.uniform(0, 0.5 / nc, (100, 3)),
+                        1.0 - rng.uniform(1e-9, 0.5 / nc, (100, 3))])
+    host = oracle.locate_ub(ko, lo, *P.T)
+    u = oracle.interp_trilinear(ko, lo, field, *P.T, host, periodic=True)
+    ref = np.stack([RegularGridInterpolator((g, g, g), Fp[..., d])(P) for d in range(3)])
+    assert np.abs(u - ref).max() < 1e-12
+
+
+def test_periodic_spread_conserves_at_walls():
+    lev = 4
+    ko, lo, nc, F, field, rng = _uniform_periodic(lev, 7)
+    X = np.concatenate([rng.uniform(0, 1.0 / nc, (50, 3)), 1.0 - rng.uniform(1e-9, 1.0 / nc, (50, 3))]).T
+    Fk = rng.normal(size=(3, X.shape[1]))
+    f, bad = oracle.spread_delta(ko, lo, lev, 2, *X, Fk, periodic=True)
+    assert bad == 0
+    h3 = 2.0 ** (-3 * lev)
+    assert np.allclose((f[:, :3] * h3).sum(0), (Fk * h3).sum(1), rtol=1e-12, atol=1e-14)
+    # adjoint with wrapping
+    Iu, _ = oracle.interp_delta(ko, lo, lev, 2, field, *X, periodic=True)
+    assert abs((Iu * Fk).sum() - (field[:, :3] * f[:, :3]).sum()) < 1e-10 * max(1.0, abs((Iu * Fk).sum()))
+
+
+def test_field_mean(tiny_tree):
+    k, l = tiny_tree
+    rng = np.random.default_rng(4)
+    c = np.tile([0.5, -2.0, 3.0, 0.0], (k.size, 1))
+    assert np.allclose(oracle.field_mean(l, c), [0.5, -2.0, 3.0], rtol=1e-13)
+    f = rng.normal(size=(k.size, 4))
+    vol = 2.0 ** (-3 * l.astype(np.float64))
+    assert np.allclose(oracle.field_mean(l, f), (f[:, :3] * vol[:, None]).sum(0), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------
 # Rigid bodies: internal-marker momenta and IBM force / torque sums (Sec. 2.3)
 # ---------------------------------------------------------------------------------------
 
