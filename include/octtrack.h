@@ -125,6 +125,12 @@ ot_status ot_octree_set_map_level(ot_octree* t, int level, void* stream);
 /* The current level-map level. */
 ot_status ot_octree_get_map_level(const ot_octree* t, int* level);
 
+/* Periodic unit cube (the turbulence box of Sec. 5.2): with periodic = 1, delta-kernel
+ * stencils (interpolation and spreading) and trilinear level-mates wrap around the cube
+ * (cell indices modulo the cells per axis) instead of dropping cells / taking the host's
+ * index.  Batches made earlier on the octree keep the setting they were made with. */
+ot_status ot_octree_set_periodic(ot_octree* t, int periodic);
+
 /* Leaf centres, FP64, written as 3 planes of N (x..., y..., z...). */
 ot_status ot_octree_centres(const ot_octree* t, double* d_xyz, void* stream);
 
@@ -359,6 +365,12 @@ ot_status ot_batch_autotune(ot_octree* t, const ot_group* groups, int n_groups, 
  * -------------------------------------------------------------------------------------*/
 ot_status ot_field_fourier(const ot_octree* t, int n_modes, const int32_t* h_wave, const double* h_amp,
                            const double* h_phase, float* d_field, void* stream);
+
+/* Mean-force removal in a periodic box (Sec. 5.2): subtracts from every leaf of d_field
+ * (float4 per leaf) its volume-weighted mean over the unit cube, sum_c f_c 8^-level_c,
+ * summed in FP64 in a fixed order (deterministic).  d_mean (nullable, device): the 3
+ * subtracted components.  Stream-ordered scratch; asynchronous on `stream`. */
+ot_status ot_field_subtract_mean(const ot_octree* t, float* d_field, double* d_mean, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Morton order of a point set (not in the paper's API; its ranks keep their Lagrangian points

@@ -21,7 +21,8 @@ __all__ = [
     "OtError", "Octree", "Batch", "library_path", "ot_octree_build", "ot_octree_from_leaves", "ot_octree_info",
     "ot_octree_copy_leaves", "ot_octree_set_map_level", "ot_octree_get_map_level", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats", "ot_index_get_root_params",
     "ot_index_mlp_grad", "ot_locate", "ot_interpolate", "ot_interpolate_f64", "ot_spread_workspace_size",
-    "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_ibm_mdf", "ot_points_morton_order", "ot_field_fourier", "ot_body_sums", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
+    "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_ibm_mdf", "ot_points_morton_order", "ot_field_fourier", "ot_body_sums", "ot_octree_set_periodic",
+    "ot_field_subtract_mean", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
     "ot_last_error", "ot_launch_count",
 ]
 
@@ -116,6 +117,8 @@ def _L():
                 "ot_points_order_workspace_size": (st, [i64, P]),
                 "ot_field_fourier": (st, [P, i32, P, P, P, P, P]),
                 "ot_body_sums": (st, [P, P, P, P, P, C.c_float, i64, P, i32, P, C.c_double, P, P, P]),
+                "ot_octree_set_periodic": (st, [P, i32]),
+                "ot_field_subtract_mean": (st, [P, P, P, P]),
                 "ot_points_morton_order": (st, [P, P, P, i64, i32, P, P, C.c_size_t, P]),
                 "ot_ibm_mdf": (st, [P, i32, P, P, P, P, P, i64, C.c_float, C.c_float, i32, P, P, P, P, C.c_size_t, P]),
                 "ot_batch_run": (st, [P, P]),
@@ -449,6 +452,19 @@ def ot_field_fourier(tree: Octree, wave, amp, phase, field=None, stream=None):
     _check(_L().ot_field_fourier(tree.handle, w.shape[0], w.ctypes.data_as(C.c_void_p), a.ctypes.data_as(C.c_void_p),
                                  p.ctypes.data_as(C.c_void_p), _dptr(field, torch.float32, "field"), _stream(stream)))
     return field
+
+
+def ot_octree_set_periodic(tree: Octree, periodic: bool = True):
+    _check(_L().ot_octree_set_periodic(tree.handle, int(periodic)))
+
+
+def ot_field_subtract_mean(tree: Octree, field, stream=None):
+    """Subtracts the volume-weighted mean of field ((N, 4) float32, in place); returns the mean."""
+    torch = _torch()
+    mean = torch.empty(3, dtype=torch.float64, device=field.device)
+    _check(_L().ot_field_subtract_mean(tree.handle, _dptr(field, torch.float32, "field"), _dptr(mean),
+                                       _stream(stream)))
+    return mean
 
 
 def ot_body_sums(x, y, z, v, start, xb, scale: float, dV=None, w: float = 1.0, stream=None):

@@ -179,6 +179,12 @@ ot_status ot_octree_copy_leaves(const ot_octree* t, uint64_t* d_keys, uint8_t* d
     return OT_OK;
 }
 
+ot_status ot_octree_set_periodic(ot_octree* t, int periodic) {
+    if (!t || (periodic != 0 && periodic != 1)) return OT_ERR_ARG;
+    t->periodic = periodic;
+    return OT_OK;
+}
+
 ot_status ot_octree_get_map_level(const ot_octree* t, int* level) {
     if (!t || !level) return OT_ERR_ARG;
     *level = t->lmap_level;

@@ -143,6 +143,7 @@ struct TreeView {
     const uint4* __restrict__ desc;
     const uint8_t* __restrict__ lmap_lv;  // level of leaf lmap[c]
     int pyr_level;  // deepest level of the pyramid of cell means (refined trilinear level-mates)
+    int periodic;   // the unit cube is periodic: stencils and level-mates wrap around
     // learned search: root -> (optional mid models) -> leaf models
     const RootModel* __restrict__ root;  // device copy
     const LeafModel* __restrict__ models;

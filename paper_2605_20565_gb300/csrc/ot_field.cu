@@ -45,11 +45,68 @@ __global__ void __launch_bounds__(256) k_field_fourier(const uint64_t* __restric
     }
 }
 
+// Volume-weighted field sums, FP64: block b adds the leaves of its stride in a fixed order,
+// then a fixed tree; a single block then adds the block partials in order.
+constexpr int MT = 256;
+
+__global__ void __launch_bounds__(MT) k_field_sum(const uint8_t* __restrict__ level, int64_t n,
+                                                  const float4* __restrict__ f, double* __restrict__ part) {
+    __shared__ double s[3][MT];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)MT + threadIdx.x; i < n; i += (int64_t)gridDim.x * MT) {
+        const double vol = __longlong_as_double((long long)(1023 - 3 * (int)level[i]) << 52);  // 8^-level
+        const float4 v = f[i];
+        a0 += vol * v.x, a1 += vol * v.y, a2 += vol * v.z;
+    }
+    s[0][threadIdx.x] = a0, s[1][threadIdx.x] = a1, s[2][threadIdx.x] = a2;
+    __syncthreads();
+    for (int o = MT / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int c = 0; c < 3; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) part[3 * blockIdx.x + threadIdx.x] = s[threadIdx.x][0];
+}
+
+__global__ void k_field_mean_finish(const double* __restrict__ part, int nb, double* __restrict__ mean) {
+    if (threadIdx.x < 3) {
+        double a = 0.0;
+        for (int b = 0; b < nb; ++b) a += part[3 * b + threadIdx.x];
+        mean[threadIdx.x] = a;  // the unit cube's volume is 1
+    }
+}
+
+__global__ void __launch_bounds__(MT) k_field_sub(float4* __restrict__ f, int64_t n, const double* __restrict__ mean) {
+    const float m0 = (float)mean[0], m1 = (float)mean[1], m2 = (float)mean[2];
+    for (int64_t i = blockIdx.x * (int64_t)MT + threadIdx.x; i < n; i += (int64_t)gridDim.x * MT) {
+        float4 v = f[i];
+        v.x -= m0, v.y -= m1, v.z -= m2;
+        f[i] = v;
+    }
+}
+
 } // namespace
 
 } // namespace ot
 
 using namespace ot;
+
+extern "C" ot_status ot_field_subtract_mean(const ot_octree* t, float* d_field, double* d_mean, void* stream) {
+    if (!t || !d_field) return OT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((t->n + MT - 1) / MT, (int64_t)num_sms() * 4));
+    double* part = nullptr;
+    OT_CUDA(cudaMallocAsync(&part, sizeof(double) * (3 * (size_t)nb + 3), s));
+    double* mean = part + 3 * nb;
+    k_field_sum<<<nb, MT, 0, s>>>(t->d_level, t->n, reinterpret_cast<const float4*>(d_field), part);
+    k_field_mean_finish<<<1, 32, 0, s>>>(part, nb, mean);
+    k_field_sub<<<nb, MT, 0, s>>>(reinterpret_cast<float4*>(d_field), t->n, mean);
+    count_launch(3);
+    if (d_mean) OT_CUDA(cudaMemcpyAsync(d_mean, mean, sizeof(double) * 3, cudaMemcpyDeviceToDevice, s));
+    OT_CUDA(cudaFreeAsync(part, s));
+    OT_CUDA(cudaGetLastError());
+    return OT_OK;
+}
 
 extern "C" ot_status ot_field_fourier(const ot_octree* t, int n_modes, const int32_t* h_wave, const double* h_amp,
                                       const double* h_phase, float* d_field, void* stream) {

@@ -19,6 +19,7 @@ struct ot_octree {
     uint32_t* d_lmap = nullptr;
     int lmap_level = 0;
     uint4* d_desc = nullptr;  // subtree descriptor of every level-map cell
+    int periodic = 0;         // stencils and level-mates wrap around the unit cube
     uint8_t* d_lmap_lv = nullptr;  // level of leaf lmap[c]
     // the same table at the pyramid level min(lmax, 7), fixed for the octree's life (it is
     // d_lmap when the two levels agree): leaf ranges of the cells of the pyramid of means

@@ -47,7 +47,7 @@ __device__ __forceinline__ T stencil_weight_1d(int lmax, uint64_t X, int a) {
 // consecutive leaves.  A parent in the same grandparent as the last one found is usually 8
 // leaves per child-number step away, which one key comparison proves.  The visitor gets
 // (a0, bx, by, bz, P) with a0 the first child's index, or -1 when the parent is outside the
-// cube or not refined to the finest level.
+// cube (a periodic cube wraps it instead) or not refined to the finest level.
 template <int K, bool LEARNED, typename PVisit>
 __device__ __forceinline__ void visit_parents(const TreeView& t, const int i0[3], PVisit&& pvisit) {
     constexpr int W = Stencil<K>::W;
@@ -65,23 +65,29 @@ __device__ __forceinline__ void visit_parents(const TreeView& t, const int i0[3]
         for (int by = 0; by < pn[1]; ++by)
             for (int bx = 0; bx < pn[0]; ++bx) {
                 const int P[3] = {p0[0] + bx, p0[1] + by, p0[2] + bz};
-                const bool inside = P[0] >= 0 && P[1] >= 0 && P[2] >= 0 && P[0] < np_cells && P[1] < np_cells &&
-                                    P[2] < np_cells;
+                // the parent's own index (wrapped around a periodic cube); P stays unwrapped for
+                // the stencil offsets the visitor computes
+                int Q[3] = {P[0], P[1], P[2]};
+                if (t.periodic)
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) Q[d] = (Q[d] + np_cells) & (np_cells - 1);
+                const bool inside = Q[0] >= 0 && Q[1] >= 0 && Q[2] >= 0 && Q[0] < np_cells && Q[1] < np_cells &&
+                                    Q[2] < np_cells;
                 int a0 = -1;
                 if (inside) {
                     const uint64_t anchor =
-                        morton3((uint32_t)P[0] << shp, (uint32_t)P[1] << shp, (uint32_t)P[2] << shp);
+                        morton3((uint32_t)Q[0] << shp, (uint32_t)Q[1] << shp, (uint32_t)Q[2] << shp);
                     int a = -1;
-                    if (prev_a0 >= 0 && (P[0] >> 1) == (prevP[0] >> 1) && (P[1] >> 1) == (prevP[1] >> 1) &&
-                        (P[2] >> 1) == (prevP[2] >> 1)) {
-                        const int g = prev_a0 + 8 * (((P[0] & 1) | ((P[1] & 1) << 1) | ((P[2] & 1) << 2)) -
+                    if (prev_a0 >= 0 && (Q[0] >> 1) == (prevP[0] >> 1) && (Q[1] >> 1) == (prevP[1] >> 1) &&
+                        (Q[2] >> 1) == (prevP[2] >> 1)) {
+                        const int g = prev_a0 + 8 * (((Q[0] & 1) | ((Q[1] & 1) << 1) | ((Q[2] & 1) << 2)) -
                                                      ((prevP[0] & 1) | ((prevP[1] & 1) << 1) | ((prevP[2] & 1) << 2)));
                         if (g >= 0 && g < t.n && ldg_key(t.key + g) == anchor) a = g;
                     }
                     if (a < 0) a = search<LEARNED>(t, anchor);
                     if (ldg_key(t.key + a) == anchor && t.level[a] == t.lmax) {
                         a0 = a;
-                        prevP[0] = P[0], prevP[1] = P[1], prevP[2] = P[2];
+                        prevP[0] = Q[0], prevP[1] = Q[1], prevP[2] = Q[2];
                         prev_a0 = a;
                     }
                 }

@@ -173,7 +173,7 @@ __device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& ro
 //   level-mate value: leaf of level l -> its value; inside a coarser leaf -> that leaf's
 //   value; refined -> volume-weighted mean of its leaves, one load: from the dense pyramid of
 //   cell means for l <= the pyramid level, else from the node means of level l (both in pyr);
-//   outside the cube -> the host's index on that axis.
+//   outside the cube -> the host's index on that axis, or the wrapped index when periodic.
 // Lanes with active == false take part in the warp's steps only.  host_in >= 0 gives the host.
 // Returns the host leaf (-1 when inactive or outside the cube, out = NaN).
 template <typename T, bool LEARNED>
@@ -230,7 +230,7 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         nb[d] = c[d] + sg[d];
-        if (nb[d] < 0 || nb[d] >= ncell) nb[d] = c[d];
+        if (nb[d] < 0 || nb[d] >= ncell) nb[d] = t.periodic ? (nb[d] + ncell) & (ncell - 1) : c[d];
         dil[d][0] = (part1by2((uint32_t)c[d]) << d) << (3 * sh);
         dil[d][1] = (part1by2((uint32_t)nb[d]) << d) << (3 * sh);
     }

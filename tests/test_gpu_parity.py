@@ -626,3 +626,76 @@ def test_body_sums_match_oracle(ot, deep, torch_mod):
     # deterministic
     lin2, ang2 = ot.ot_body_sums(*pts(Xs), dev(F), torch.as_tensor(ss, device="cuda"), xb, -1.0, dV=dev(dV))
     assert torch.equal(lin, lin2) and torch.equal(ang, ang2)
+
+
+# ---------------------------------------------------------------------------------------
+# Periodic box (Sec. 5.2)
+# ---------------------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def uniform6(ot):
+    ko, lo = oracle.octree_build(np.zeros((0, 5)), 6, 6)
+    t = ot.ot_octree_build(np.zeros((0, 5)), 6, 6)
+    ot.ot_octree_set_periodic(t, True)
+    rng = np.random.default_rng(17)
+    nc = 64
+    P = np.concatenate([rng.uniform(0, 1, (3000, 3)), rng.uniform(0, 1.5 / nc, (1000, 3)),
+                        1.0 - rng.uniform(1e-9, 1.5 / nc, (1000, 3))])
+    field = np.zeros((ko.size, 4))
+    field[:, :3] = rng.normal(size=(ko.size, 3))
+    return ko, lo, t, P, field
+
+
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_periodic_delta_interp_and_spread(ot, uniform6, kernel, torch_mod):
+    torch = torch_mod
+    ko, lo, t, P, field = uniform6
+    f32 = field.astype(np.float32)
+    u = ot.ot_interpolate(t, kernel, *pts(P.T), dev(f32)).cpu().numpy()
+    ref, bad = oracle.interp_delta(ko, lo, 6, kernel, f32.astype(np.float64), *P.T, periodic=True)
+    assert bad == 0
+    assert rel_err(u, ref) <= TOL32
+    rng = np.random.default_rng(3)
+    F = rng.normal(size=(3, P.shape[0])).astype(np.float32)
+    fref, bad = oracle.spread_delta(ko, lo, 6, kernel, *P.T, F.astype(np.float64), periodic=True)
+    assert bad == 0
+    for mode in (ot.OT_SORTED, ot.OT_ATOMIC):
+        f = torch.zeros((ko.size, 4), dtype=torch.float32, device="cuda")
+        ot.ot_spread(t, kernel, mode, *pts(P.T), dev(F), f)
+        assert rel_err(f.cpu().numpy()[:, :3], fref[:, :3]) <= TOL32
+    assert ot.ot_last_error(t) & ot.OT_DEV_STENCIL == 0
+
+
+def test_periodic_trilinear(ot, tiny, tiny_fields):
+    w, ko, lo, _ = tiny
+    t = ot.ot_octree_build(w.spheres, w.lmin, w.lmax)
+    ot.ot_octree_set_periodic(t, True)
+    rng = np.random.default_rng(21)
+    P = np.concatenate([rng.uniform(0, 1, (2000, 3)), rng.uniform(0, 0.02, (500, 3)),
+                        1.0 - rng.uniform(1e-9, 0.02, (500, 3))])
+    f32 = tiny_fields["sin"].astype(np.float32)
+    u = ot.ot_interpolate(t, ot.OT_TRILINEAR, *pts(P.T), dev(f32)).cpu().numpy()
+    host = oracle.locate_ub(ko, lo, *P.T)
+    ref = oracle.interp_trilinear(ko, lo, f32.astype(np.float64), *P.T, host, periodic=True)
+    assert rel_err(u, ref) <= TOL32
+    # the batched form keeps the setting
+    import torch
+    ub = torch.empty((3, P.shape[0]), device="cuda")
+    x, y, z = pts(P.T)
+    b = ot.ot_batch_create(t, [dict(kernel=ot.OT_TRILINEAR, x=x, y=y, z=z, u=ub)], dev(f32))
+    ot.ot_batch_run(b)
+    assert rel_err(ub.cpu().numpy(), ref) <= TOL32
+
+
+def test_field_subtract_mean(ot, tiny, torch_mod):
+    w, ko, lo, tree = tiny
+    rng = np.random.default_rng(9)
+    f = rng.normal(size=(ko.size, 4)).astype(np.float32)
+    ref = oracle.field_mean(lo, f.astype(np.float64))
+    d = dev(f)
+    m = ot.ot_field_subtract_mean(tree, d).cpu().numpy()
+    assert np.abs(m - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+    out = d.cpu().numpy()
+    assert np.abs(out[:, :3] - (f[:, :3] - ref.astype(np.float32))).max() <= 1e-6
+    assert np.array_equal(out[:, 3], f[:, 3])
+    assert np.abs(oracle.field_mean(lo, out.astype(np.float64))).max() <= 1e-6
