@@ -57,11 +57,24 @@ class Tracker:
         self.a_prev = T.zeros_like(self.v)
         self.v_prev = T.zeros_like(self.v)
         self.u = T.empty_like(self.v)
-        # markers: offsets from their bubble centre (moved rigidly), forces = outward normals
-        self.m_grp = T.as_tensor(w.marker_group.astype(np.int64), device=dev)
-        self.m_off = T.as_tensor(w.markers - self.centres0[w.marker_group].T, device=dev)
+        # markers: offsets from their bubble centre (moved rigidly), forces = outward normals.
+        # Stored bubble by bubble in Morton order of their initial positions (a rigid motion
+        # keeps neighbours neighbours), so a warp's markers share parent blocks; m_ids maps
+        # each stored marker to its input index.
+        m_ids = np.arange(w.markers.shape[1])
+        if sort_points and w.markers.shape[1] > 0:
+            q = np.floor(np.clip(w.markers, 0.0, np.nextafter(1.0, 0.0)) * 1024.0).astype(np.uint64)
+            key = np.zeros(q.shape[1], np.uint64)
+            for b in range(10):
+                for d in range(3):
+                    key |= ((q[d] >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + d)
+            m_ids = np.lexsort((key, w.marker_group))
+        self.m_ids = T.as_tensor(m_ids, device=dev)
+        self.m_grp = T.as_tensor(w.marker_group[m_ids].astype(np.int64), device=dev)
+        self.m_off = T.as_tensor(np.ascontiguousarray((w.markers - self.centres0[w.marker_group].T)[:, m_ids]),
+                                 device=dev)
         self.mx = T.empty((3, w.markers.shape[1]), dtype=T.float64, device=dev)
-        self.F = T.as_tensor(np.ascontiguousarray(w.forces, dtype=np.float32), device=dev)
+        self.F = T.as_tensor(np.ascontiguousarray(w.forces[:, m_ids], dtype=np.float32), device=dev)
         self.um = T.empty((3, w.markers.shape[1]), dtype=T.float32, device=dev)
         self._place_markers()
         self.h = 2.0 ** -w.lmax
