@@ -42,7 +42,10 @@ __global__ void k_advect(double* __restrict__ x, float* __restrict__ v, float* _
             // the displacement (well below one cell) in FP32, one FP64 add for the position:
             // GB300's FP64 rate made the all-FP64 update the bound of this kernel
             double xn = x[d * n + i] + (double)(dt * (1.5f * vn - 0.5f * vm));
-            if (periodic && (xn < 0.0 || xn >= 1.0)) {  // only points that crossed a wall
+            // outside [0, 1) <=> the bit pattern, read as a signed integer, is negative (sign
+            // set, or -0.0 excluded below) or at least that of 1.0: integer compares, not FP64
+            const long long xb = __double_as_longlong(xn);
+            if (periodic && (xb < 0 || xb >= 0x3FF0000000000000LL) && xb != (long long)0x8000000000000000ULL) {
                 xn -= floor(xn);
                 if (xn >= 1.0) xn = 0.0;  // -tiny - floor(-tiny) rounds to 1
             }
