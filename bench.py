@@ -55,11 +55,13 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--launch", default="", help="block,tile,blocks_per_sm")
+    p.add_argument("--launch", default="", help="block,tile,blocks_per_sm[,order_level[,tri_tile,tri_blocks_per_sm]]")
     p.add_argument("--map-level", type=int, default=None, help="level of the level map (default: autotuned)")
     p.add_argument("--no-autotune", action="store_true", help="default launch shape and level map")
     p.add_argument("--no-nomap", action="store_true", help="skip the forms without a level map")
     p.add_argument("--no-mdf", action="store_true", help="skip the multi-direct forcing measurement")
+    p.add_argument("--no-mates", action="store_true",
+                   help="search the trilinear level-mates per query instead of reading the level-mate table")
     return p.parse_args()
 
 
@@ -296,6 +298,12 @@ def run_ours(args):
     n_leaves = ot.ot_octree_info(tree)[0]
     if args.map_level is not None:
         ot.ot_octree_set_map_level(tree, args.map_level)
+    mates_s = None
+    if not args.no_mates:
+        t0 = time.time()
+        ot.ot_octree_build_mates(tree, True)
+        torch.cuda.synchronize()
+        mates_s = time.time() - t0
     t0 = time.time()
     root = ot.OT_ROOT_LINEAR if args.index == "linear2" else ot.OT_ROOT_MLP
     n_leaf, n_mid = (1 << 18, 4096) if args.index == "mlp3" else (4096, 0)
@@ -332,32 +340,42 @@ def run_ours(args):
     ws = torch.empty(max(1, ws_bytes), dtype=torch.uint8, device=dev)
     launch = None
     if args.launch:
-        b, t, s = [int(v) for v in args.launch.split(",")]
-        launch = dict(block=b, tile=t, blocks_per_sm=s)
+        vals = [int(v) for v in args.launch.split(",")]
+        launch = dict(zip(("block", "tile", "blocks_per_sm", "order_level", "tri_tile", "tri_blocks_per_sm"), vals))
     groups = [dict(kernel=ot.OT_PESKIN4, x=mx, y=my, z=mz, u=um), dict(kernel=ot.OT_TRILINEAR, x=px, y=py, z=pz, u=up)]
     stream = torch.cuda.current_stream()
 
-    # search forms over the same groups: (search, level-map level, launch shape).  "plain" and
-    # "learned" are autotuned (launch shape and level-map level) unless a launch or map level is
-    # given; the "_nomap" forms search the whole key array (level map of one cell), the plain
-    # one being Algorithm 1's binary search and the learned one the index without any map.
+    # search forms over the same groups: (search, level-map level, launch shape, level-mate
+    # table).  "plain" and "learned" are autotuned (launch shape and level-map level) unless a
+    # launch or map level is given; the "_nomap" forms search the whole key array (level map of
+    # one cell), the plain one being Algorithm 1's binary search and the learned one the index
+    # without any map; "plain_search" searches every trilinear level-mate per query.
     base_level = ot.ot_octree_get_map_level(tree)
+    use_mates = not args.no_mates
     forms_cfg, tune = {}, {}
     for name, sv in (("plain", ot.OT_BINARY), ("learned", ot.OT_LEARNED)):
         if launch is None and not args.no_autotune:
             r = ot.ot_batch_autotune(tree, groups, field, search=sv, tune_map_level=args.map_level is None, reps=2)
             tune[name] = r
-            forms_cfg[name] = (sv, r["map_level"], r["launch"])
+            forms_cfg[name] = (sv, r["map_level"], r["launch"], use_mates)
         else:
-            forms_cfg[name] = (sv, base_level, launch)
+            forms_cfg[name] = (sv, base_level, launch, use_mates)
+    if use_mates:
+        forms_cfg["plain_search"] = (ot.OT_BINARY,) + forms_cfg["plain"][1:3] + (False,)
     if not args.no_nomap:
-        forms_cfg["plain_nomap"] = (ot.OT_BINARY, 0, launch)
-        forms_cfg["learned_nomap"] = (ot.OT_LEARNED, 0, launch)
+        forms_cfg["plain_nomap"] = (ot.OT_BINARY, 0, launch, use_mates)
+        forms_cfg["learned_nomap"] = (ot.OT_LEARNED, 0, launch, use_mates)
 
-    def make_batch(name):
-        sv, lvl, lp = forms_cfg[name]
+    def set_form(name):
+        sv, lvl, lp, mt = forms_cfg[name]
         if ot.ot_octree_get_map_level(tree) != lvl:
             ot.ot_octree_set_map_level(tree, lvl)
+        if ot.ot_octree_has_mates(tree) != mt:
+            ot.ot_octree_build_mates(tree, mt)
+        return sv, lp
+
+    def make_batch(name):
+        sv, lp = set_form(name)
         return ot.ot_batch_create(tree, groups, field, search=sv, launch=lp)
 
     def step(batch, ev=None):
@@ -519,10 +537,8 @@ def run_ours(args):
             forms[name] = time_steps(bb, args.steps)
             del bb
         # per-group timing (markers only, particles only) at the form's settings
-        sv, lvl, lp = forms_cfg[name]
         for gname, gsel in (("markers", groups[:1]), ("particles", groups[1:])):
-            if ot.ot_octree_get_map_level(tree) != lvl:
-                ot.ot_octree_set_map_level(tree, lvl)
+            sv, lp = set_form(name)
             bb = ot.ot_batch_create(tree, gsel, field, search=sv, launch=lp)
             for _ in range(2):
                 ot.ot_batch_run(bb)
@@ -540,6 +556,7 @@ def run_ours(args):
         v_["search"] = "learned" if forms_cfg[name][0] == ot.OT_LEARNED else "binary"
         v_["map_level"] = forms_cfg[name][1]
         v_["launch"] = forms_cfg[name][2]
+        v_["level_mates"] = "table" if forms_cfg[name][3] else "searched per query"
     learned_vs_plain = {
         "with_level_map": {
             "locate_interpolate": forms["plain"]["locate_interpolate_ms"] / forms["learned"]["locate_interpolate_ms"],
@@ -555,9 +572,9 @@ def run_ours(args):
             "locate_interpolate": forms["plain_nomap"]["locate_interpolate_ms"] /
             forms["learned_nomap"]["locate_interpolate_ms"],
             "step": forms["plain_nomap"]["step_ms"] / forms["learned_nomap"]["step_ms"]}
-    lvl_c = forms_cfg[chosen][1]
-    if ot.ot_octree_get_map_level(tree) != lvl_c:
-        ot.ot_octree_set_map_level(tree, lvl_c)
+    if "plain_search" in forms:
+        learned_vs_plain["table_vs_search_plain_step"] = forms["plain_search"]["step_ms"] / forms["plain"]["step_ms"]
+    set_form(chosen)
 
     if rank != 0:
         if dist:
@@ -612,7 +629,7 @@ def run_ours(args):
                      "empty_models": istats["empty_models"], "fallbacks_timed": fb,
                      "mean_probes": istats["mean_probes"],
                      "final_loss": istats["final_loss"], "train_s": train_s},
-           "setup_s": {"octree_build": build_s, "index_train": train_s},
+           "setup_s": {"octree_build": build_s, "index_train": train_s, "level_mate_table": mates_s},
            "parity": parity}
     print(json.dumps(out), flush=True)
     if dist:

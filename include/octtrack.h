@@ -131,6 +131,23 @@ ot_status ot_octree_get_map_level(const ot_octree* t, int* level);
  * index.  Batches made earlier on the octree keep the setting they were made with. */
 ot_status ot_octree_set_periodic(ot_octree* t, int periodic);
 
+/* Level-mate table (the trilinear level-mate rule of Sec. 2.3.2, resolved once per octree):
+ * for every leaf h and octant o of its cell (bit d of o set when the point lies in the upper
+ * half on axis d), the 8 level-mates c + {0, s_d} of the trilinear stencil, each as a value
+ * slot -- the leaf whose value it takes (a leaf of the host's level, or the coarser leaf that
+ * covers it) or its cell-mean entry when it is refined.  With the table built, trilinear
+ * interpolation (ot_interpolate and batches created afterwards) finds its host leaf and reads
+ * one 32-byte row instead of searching for the 7 level-mates; the results are bit-identical.
+ * enable = 1 builds (or rebuilds) it: 256 bytes of device memory per leaf, OT_ERR_LIMIT when
+ * the leaf count or the cell-mean count reaches 2^31, OT_ERR_OOM when the memory is not there
+ * (the octree is then left without a table).  enable = 0 frees it.  Batches made while a table
+ * existed hold its pointer: recreate them after rebuilding or freeing it.  The octree's
+ * periodic setting is part of the table: ot_octree_set_periodic rebuilds it (on the legacy
+ * default stream).  Synchronises the stream. */
+ot_status ot_octree_build_mates(ot_octree* t, int enable, void* stream);
+/* *has = 1 when the level-mate table is built. */
+ot_status ot_octree_has_mates(const ot_octree* t, int* has);
+
 /* Leaf centres, FP64, written as 3 planes of N (x..., y..., z...). */
 ot_status ot_octree_centres(const ot_octree* t, double* d_xyz, void* stream);
 
@@ -317,15 +334,23 @@ typedef struct {
 typedef struct {
     int block;       /* threads per block: 64 .. 256, multiple of 32 (default 256)          */
     int tile;        /* 32-point rows per work item taken from the queue: 1 .. 64 (default 4) */
-    int blocks_per_sm; /* resident blocks per SM, capped by occupancy (0: the occupancy max);
-                          2 also selects the kernel compiled for 2 blocks per SM (more
-                          registers per thread, no spills) instead of 3                    */
+    int blocks_per_sm; /* resident blocks per SM of every launch of the batch, capped by
+                          occupancy (0: the occupancy max); 2 also selects the delta-kernel
+                          code compiled for 2 blocks per SM (more registers per thread, no
+                          spills) instead of 3.  With the octree's level-mate table built, the
+                          delta-kernel groups and the trilinear groups run as two launches  */
     int order_level;   /* 0: points in the caller's order.  L in 1..21: each replay first sorts
                           every trilinear group of >= 64 points by the Morton key of their
                           level-L cells (on the device, inside the graph), interpolates them in
                           that order (a warp's points then share host leaves and level-mates)
                           and writes the results back in the caller's order; identical
                           results                                                           */
+    int tri_tile;      /* with the level-mate table, the trilinear launch's rows per work item
+                          (0: tile)                                                          */
+    int tri_blocks_per_sm; /* with the level-mate table, the trilinear launch's resident blocks
+                          per SM, capped by occupancy (0: 2, which measured fastest: its loads
+                          are latency-bound and fewer warps keep more of each SM's cache
+                          per warp)                                                          */
 } ot_launch;
 
 /* Create a batch over groups (copied) reading d_field (float4 per leaf).  search selects
@@ -343,9 +368,13 @@ ot_status ot_batch_destroy(ot_batch* b);
  * shape of {128, 256} threads x {1, 2, 4, 8} rows per work item x {occupancy max, 2} blocks
  * per SM x {caller's order, level-8 Morton order} and, when tune_map_level != 0, every
  * level-map level from min(lmax, 6) to min(lmax, 8); times `reps` graph replays of each (CUDA
- * events on `stream`, after one warm-up replay) and returns the fastest.  The octree is left at the chosen level-map level
- * (batches made earlier on it must be recreated).  The groups' outputs are overwritten.
- * Synchronises the stream; takes about (1 + reps) * 32 * levels replays. */
+ * events on `stream`, after one warm-up replay) and returns the fastest.  With the level-mate
+ * table built the two launches are tuned one after the other: the delta-kernel groups alone
+ * over threads x rows x blocks per SM (16 shapes), then the trilinear groups alone over
+ * tri_tile {2, 4, 8} x tri_blocks_per_sm {1, 2, 3, 4} x order (24 shapes), and the pair is
+ * timed together.  The octree is left at the chosen level-map level (batches made earlier on
+ * it must be recreated).  The groups' outputs are overwritten.  Synchronises the stream; takes
+ * about (1 + reps) * 32 (or 41) * levels replays. */
 typedef struct {
     ot_launch launch; /* fastest launch shape                                                */
     int map_level;    /* its level-map level                                                 */

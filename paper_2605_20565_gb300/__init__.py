@@ -22,7 +22,7 @@ __all__ = [
     "ot_octree_copy_leaves", "ot_octree_set_map_level", "ot_octree_get_map_level", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats", "ot_index_get_root_params",
     "ot_index_mlp_grad", "ot_locate", "ot_interpolate", "ot_interpolate_f64", "ot_spread_workspace_size",
     "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_ibm_mdf", "ot_points_morton_order", "ot_field_fourier", "ot_body_sums", "ot_octree_set_periodic",
-    "ot_field_subtract_mean", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
+    "ot_octree_build_mates", "ot_octree_has_mates", "ot_field_subtract_mean", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
     "ot_last_error", "ot_launch_count",
 ]
 
@@ -73,7 +73,17 @@ class _Group(C.Structure):
 
 
 class _Launch(C.Structure):
-    _fields_ = [("block", C.c_int), ("tile", C.c_int), ("blocks_per_sm", C.c_int), ("order_level", C.c_int)]
+    _fields_ = [("block", C.c_int), ("tile", C.c_int), ("blocks_per_sm", C.c_int), ("order_level", C.c_int),
+                ("tri_tile", C.c_int), ("tri_blocks_per_sm", C.c_int)]
+
+    _names = ("block", "tile", "blocks_per_sm", "order_level", "tri_tile", "tri_blocks_per_sm")
+
+    @classmethod
+    def of(cls, d: dict):
+        return cls(*(int(d.get(k, 0)) for k in cls._names))
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k in self._names}
 
 
 class _TuneResult(C.Structure):
@@ -118,6 +128,8 @@ def _L():
                 "ot_field_fourier": (st, [P, i32, P, P, P, P, P]),
                 "ot_body_sums": (st, [P, P, P, P, P, C.c_float, i64, P, i32, P, C.c_double, P, P, P]),
                 "ot_octree_set_periodic": (st, [P, i32]),
+                "ot_octree_build_mates": (st, [P, i32, P]),
+                "ot_octree_has_mates": (st, [P, P]),
                 "ot_field_subtract_mean": (st, [P, P, P, P]),
                 "ot_points_morton_order": (st, [P, P, P, i64, i32, P, P, C.c_size_t, P]),
                 "ot_ibm_mdf": (st, [P, i32, P, P, P, P, P, i64, C.c_float, C.c_float, i32, P, P, P, P, C.c_size_t, P]),
@@ -397,8 +409,7 @@ def ot_batch_create(tree: Octree, groups, field, search: int = OT_BINARY, launch
     keep = [field] + list(groups)
     lp = None
     if launch:
-        lp = _Launch(launch.get("block", 0), launch.get("tile", 0), launch.get("blocks_per_sm", 0),
-                     launch.get("order_level", 0))
+        lp = _Launch.of(launch)
     h = C.c_void_p()
     _check(_L().ot_batch_create(tree.handle, arr, len(groups), _dptr(field, torch.float32, "field"), search,
                                 C.byref(lp) if lp is not None else None, _stream(stream), C.byref(h)))
@@ -409,15 +420,13 @@ def ot_batch_create(tree: Octree, groups, field, search: int = OT_BINARY, launch
 def ot_batch_autotune(tree: Octree, groups, field, search: int = OT_BINARY, tune_map_level: bool = True,
                       reps: int = 3, stream=None) -> dict:
     """Fastest launch shape (and level-map level) for a batch over these groups; the octree is
-    left at the chosen level map.  Returns {launch: {block, tile, blocks_per_sm}, map_level, ms,
-    tried}."""
+    left at the chosen level map.  Returns {launch: {block, tile, blocks_per_sm, order_level,
+    tri_tile, tri_blocks_per_sm}, map_level, ms, tried}."""
     torch = _torch()
     r = _TuneResult()
     _check(_L().ot_batch_autotune(tree.handle, _groups(groups), len(groups), _dptr(field, torch.float32, "field"),
                                   search, int(tune_map_level), reps, _stream(stream), C.byref(r)))
-    return {"launch": {"block": r.launch.block, "tile": r.launch.tile, "blocks_per_sm": r.launch.blocks_per_sm,
-                       "order_level": r.launch.order_level},
-            "map_level": r.map_level, "ms": r.ms, "tried": r.tried}
+    return {"launch": r.launch.as_dict(), "map_level": r.map_level, "ms": r.ms, "tried": r.tried}
 
 
 def ot_ibm_mdf(tree: Octree, kernel: int, x, y, z, U, u, rho: float, dt: float, n_iter: int, dV=None,
@@ -456,6 +465,19 @@ def ot_field_fourier(tree: Octree, wave, amp, phase, field=None, stream=None):
 
 def ot_octree_set_periodic(tree: Octree, periodic: bool = True):
     _check(_L().ot_octree_set_periodic(tree.handle, int(periodic)))
+
+
+def ot_octree_build_mates(tree: Octree, enable: bool = True, stream=None):
+    """Builds (or, with enable=False, frees) the octree's level-mate table: 256 bytes per leaf
+    of device memory; trilinear queries and batches made afterwards read their level-mates
+    from it (bit-identical results)."""
+    _check(_L().ot_octree_build_mates(tree.handle, int(enable), _stream(stream)))
+
+
+def ot_octree_has_mates(tree: Octree) -> bool:
+    v = C.c_int()
+    _check(_L().ot_octree_has_mates(tree.handle, C.byref(v)))
+    return bool(v.value)
 
 
 def ot_field_subtract_mean(tree: Octree, field, stream=None):

@@ -184,7 +184,14 @@ ot_status ot_octree_copy_leaves(const ot_octree* t, uint64_t* d_keys, uint8_t* d
 
 ot_status ot_octree_set_periodic(ot_octree* t, int periodic) {
     if (!t || (periodic != 0 && periodic != 1)) return OT_ERR_ARG;
+    if (t->periodic == periodic) return OT_OK;
     t->periodic = periodic;
+    // the level-mate table wraps or clamps at the faces: rebuilt for the new setting
+    if (t->d_mates) {
+        const ot_status st = build_mates(t, nullptr);
+        if (st != OT_OK) return st;
+        OT_CUDA(cudaStreamSynchronize(nullptr));
+    }
     return OT_OK;
 }
 
@@ -213,6 +220,7 @@ ot_status ot_octree_destroy(ot_octree* t) {
     if (t->d_nodes) cudaFree(t->d_nodes);
     if (t->d_desc) cudaFree(t->d_desc);
     if (t->d_lmap_lv) cudaFree(t->d_lmap_lv);
+    if (t->d_mates) cudaFree(t->d_mates);
     if (t->d_models) cudaFree(t->d_models);
     if (t->d_mids) cudaFree(t->d_mids);
     if (t->d_root) cudaFree(t->d_root);

@@ -7,6 +7,7 @@
 // balance across the SMs without a host round trip.  The counter is reset by a memset node
 // captured in the same graph.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "ot_internal.h"
@@ -27,6 +28,7 @@ struct ot_batch {
 namespace ot {
 
 constexpr int MAX_GROUPS = 16;
+constexpr int TRI_MINB = 4;  // register budget of the trilinear-only launch (level-mate table)
 
 struct GroupDev {
     int kernel;
@@ -46,12 +48,20 @@ struct BatchArgs {
 
 // MINB: the register budget (blocks of 256 resident per SM it is compiled for); 3 is the
 // default, 2 trades occupancy for no register spills and is picked with blocks_per_sm = 2.
-template <bool LEARNED, int MINB>
+// MATES: trilinear level-mates read from the octree's level-mate table instead of searched.
+// KINDS: the group kinds the instance serves -- K_ALL, K_DELTA (delta-kernel groups only) or
+// K_TRI (trilinear groups only: with the table it needs far fewer registers than the delta
+// path, so it runs as its own launch at a higher occupancy).
+enum { K_ALL = 0, K_DELTA = 1, K_TRI = 2 };
+template <bool LEARNED, int MINB, bool MATES, int KINDS = K_ALL>
 __global__ void __launch_bounds__(256, MINB) k_batch(TreeView t, BatchArgs a, const float* __restrict__ field,
                                                const float* __restrict__ pyr, unsigned* __restrict__ counter) {
-    __shared__ WarpQueue s_queue[256 / 32];
+    // with the table a trilinear-only launch searches hosts only: a 32-task list per warp
+    // (more of the SM's memory left to the L1 cache)
+    using Q = typename std::conditional<MATES && KINDS == K_TRI, HostQueue, WarpQueue>::type;
+    __shared__ Q s_queue[256 / 32];
     __shared__ RootModel s_root;
-    WarpQueue& wq = s_queue[threadIdx.x >> 5];
+    Q& wq = s_queue[threadIdx.x >> 5];
     stage_root<LEARNED>(t, s_root);
     const int lane = threadIdx.x & 31;
     const int64_t tile_pts = 32 * (int64_t)a.tile;
@@ -71,14 +81,18 @@ __global__ void __launch_bounds__(256, MINB) k_batch(TreeView t, BatchArgs a, co
             float o[3];
             int h;
             const double x = active ? gr.x[i] : 0.0, y = active ? gr.y[i] : 0.0, z = active ? gr.z[i] : 0.0;
-            if (gr.kernel == OT_TRILINEAR)
-                h = trilinear_queued<float, LEARNED>(t, s_root, field, pyr, wq, active, x, y, z, -1, o);
-            else if (!active)
+            if (KINDS != K_DELTA && (KINDS == K_TRI || gr.kernel == OT_TRILINEAR)) {
+                if constexpr (MATES)
+                    h = trilinear_mates<float, LEARNED>(t, s_root, field, pyr, wq, active, x, y, z, -1, o);
+                else
+                    h = trilinear_queued<float, LEARNED>(t, s_root, field, pyr, wq, active, x, y, z, -1, o);
+            } else if (!active) {
                 h = -1;
-            else if (gr.kernel == OT_PESKIN4)
+            } else if (gr.kernel == OT_PESKIN4) {
                 h = delta_point<float, OT_PESKIN4, LEARNED>(t, field, x, y, z, gr.host != nullptr, o);
-            else
+            } else {
                 h = delta_point<float, OT_ROMA3, LEARNED>(t, field, x, y, z, gr.host != nullptr, o);
+            }
             if (active) {
                 gr.u[i] = o[0];
                 gr.u[gr.n + i] = o[1];
@@ -133,7 +147,10 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     const int block = (launch && launch->block) ? launch->block : 256;
     const int tile = (launch && launch->tile) ? launch->tile : 4;
     const int order_level = launch ? launch->order_level : 0;
+    const int tri_tile = (launch && launch->tri_tile) ? launch->tri_tile : tile;
+    const int tri_per_sm = (launch && launch->tri_blocks_per_sm) ? launch->tri_blocks_per_sm : 2;
     if (block < 64 || block > 256 || block % 32 || tile < 1 || tile > 64) return OT_ERR_ARG;
+    if (tri_tile < 1 || tri_tile > 64 || tri_per_sm < 1 || (launch && launch->blocks_per_sm < 0)) return OT_ERR_ARG;
     if (order_level < 0 || order_level > MAXLEVEL) return OT_ERR_ARG;
     BatchArgs a{};
     a.ng = n_groups;
@@ -208,22 +225,64 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     TreeView v = tree_view(t);
     const size_t smem = 0;
     const bool two = launch && launch->blocks_per_sm == 2;
-    void* kfn = search == OT_LEARNED ? (two ? (void*)k_batch<true, 2> : (void*)k_batch<true, 3>)
-                                     : (two ? (void*)k_batch<false, 2> : (void*)k_batch<false, 3>);
-    if (smem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return fail(e);
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, block, smem)) != cudaSuccess) return fail(e);
-    if (launch && launch->blocks_per_sm > 0) per_sm = std::min(per_sm, launch->blocks_per_sm);
-    per_sm = std::max(per_sm, 1);
-    const unsigned grid = (unsigned)(num_sms() * per_sm);
+    const bool learned = search == OT_LEARNED;
+    // The launches of one replay: without the level-mate table, one kernel over every group;
+    // with it, the delta-kernel groups and the trilinear groups as two launches (the trilinear
+    // one at its own, higher, occupancy), each over its own tile range and counter.
+    struct Launch {
+        void* fn;
+        BatchArgs args;
+        unsigned grid;
+    };
+    std::vector<Launch> launches;
+    auto add_launch = [&](void* fn, const BatchArgs& args, int cap) -> cudaError_t {
+        int per_sm = 0;
+        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
+        if (err != cudaSuccess) return err;
+        if (cap > 0) per_sm = std::min(per_sm, cap);
+        per_sm = std::max(per_sm, 1);
+        launches.push_back(Launch{fn, args, (unsigned)(num_sms() * per_sm)});
+        return cudaSuccess;
+    };
+    if (!t->d_mates) {
+        void* fn = learned ? (two ? (void*)k_batch<true, 2, false> : (void*)k_batch<true, 3, false>)
+                           : (two ? (void*)k_batch<false, 2, false> : (void*)k_batch<false, 3, false>);
+        if ((e = add_launch(fn, a, launch ? launch->blocks_per_sm : 0)) != cudaSuccess) return fail(e);
+    } else {
+        BatchArgs part[2] = {};
+        for (int k = 0; k < a.ng; ++k) {
+            BatchArgs& p = part[a.g[k].kernel == OT_TRILINEAR ? 1 : 0];
+            GroupDev d = a.g[k];
+            d.tile0 = p.ntiles;
+            p.tile = a.g[k].kernel == OT_TRILINEAR ? tri_tile : tile;
+            p.g[p.ng++] = d;
+            p.ntiles += (d.n + 32 * (int64_t)p.tile - 1) / (32 * (int64_t)p.tile);
+        }
+        if (part[1].ntiles >= (1LL << 32)) {
+            ot_batch_destroy(b);
+            return OT_ERR_LIMIT;
+        }
+        if (part[0].ng > 0) {
+            void* fn = learned ? (two ? (void*)k_batch<true, 2, true, K_DELTA> : (void*)k_batch<true, 3, true, K_DELTA>)
+                               : (two ? (void*)k_batch<false, 2, true, K_DELTA> : (void*)k_batch<false, 3, true, K_DELTA>);
+            if ((e = add_launch(fn, part[0], launch ? launch->blocks_per_sm : 0)) != cudaSuccess) return fail(e);
+        }
+        if (part[1].ng > 0) {
+            void* fn = learned ? (void*)k_batch<true, TRI_MINB, true, K_TRI> : (void*)k_batch<false, TRI_MINB, true, K_TRI>;
+            if ((e = add_launch(fn, part[1], tri_per_sm)) != cudaSuccess) return fail(e);
+        }
+    }
+    if (launches.size() > 1) {
+        cudaFree(b->d_counter);
+        b->d_counter = nullptr;
+        if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned) * launches.size())) != cudaSuccess) return fail(e);
+    }
 
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
     // the kernels captured below run at every replay: count them once here, as the replay's
     const uint64_t launches0 = g_launches.load();
     if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e);
-    cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), cs);
+    cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned) * launches.size(), cs);
     bool cap_ok = true;
     std::vector<int> ibs;
     for (const Ordered& o : ordered) {
@@ -235,9 +294,10 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
         count_launch();
     }
     if (cap_ok && has_tri) cap_ok = launch_pyramid<float>(t, d_field, b->d_pyr, cs) == OT_OK;
-    if (cap_ok) {
-        void* args[] = {&v, &a, (void*)&d_field, (void*)&b->d_pyr, &b->d_counter};
-        cap_ok = cudaLaunchKernel(kfn, dim3(grid), dim3(block), args, smem, cs) == cudaSuccess;
+    for (size_t i = 0; cap_ok && i < launches.size(); ++i) {
+        unsigned* ctr = b->d_counter + i;
+        void* args[] = {&v, &launches[i].args, (void*)&d_field, (void*)&b->d_pyr, &ctr};
+        cap_ok = cudaLaunchKernel(launches[i].fn, dim3(launches[i].grid), dim3(block), args, smem, cs) == cudaSuccess;
         count_launch();
     }
     for (size_t i = 0; cap_ok && i < ordered.size(); ++i) {

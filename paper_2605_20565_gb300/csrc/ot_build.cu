@@ -571,6 +571,7 @@ TreeView tree_view(const ot_octree* t) {
     v.lmap_lv = t->d_lmap_lv;
     v.pyr_level = t->pyr_level;
     v.periodic = t->periodic;
+    v.mates = reinterpret_cast<const uint4*>(t->d_mates);
     v.root = t->d_root;
     v.models = t->d_models;
     v.mids = t->d_mids;

@@ -144,6 +144,9 @@ struct TreeView {
     const uint8_t* __restrict__ lmap_lv;  // level of leaf lmap[c]
     int pyr_level;  // deepest level of the pyramid of cell means (refined trilinear level-mates)
     int periodic;   // the unit cube is periodic: stencils and level-mates wrap around
+    // level-mate table: for leaf h and octant o, the 8 value slots of its trilinear
+    // level-mates at mates[2 (8h + o)], two uint4 (null when not built)
+    const uint4* __restrict__ mates;
     // learned search: root -> (optional mid models) -> leaf models
     const RootModel* __restrict__ root;  // device copy
     const LeafModel* __restrict__ models;

@@ -1,6 +1,7 @@
 // ot_interp.cu -- single-op kernels: locate, trilinear and delta-kernel interpolation.
 // Persistent grid-stride launches (a few blocks per SM).
 #include <algorithm>
+#include <type_traits>
 
 #include "ot_internal.h"
 #include "ot_points.cuh"
@@ -31,7 +32,7 @@ __global__ void __launch_bounds__(256) k_locate(TreeView t, const double* __rest
     }
 }
 
-template <typename T, bool LEARNED>
+template <typename T, bool LEARNED, bool MATES>
 __global__ void __launch_bounds__(256) k_trilinear(TreeView t, const double* __restrict__ x,
                                                    const double* __restrict__ y, const double* __restrict__ z,
                                                    int64_t n, const int32_t* __restrict__ host_in,
@@ -39,9 +40,10 @@ __global__ void __launch_bounds__(256) k_trilinear(TreeView t, const double* __r
                                                    T* __restrict__ u, int32_t* __restrict__ host_out) {
     // warp-aligned iteration: every lane of a warp runs the same trip count (the trilinear
     // routine is warp-cooperative)
-    __shared__ WarpQueue s_queue[256 / 32];
+    using Q = typename std::conditional<MATES, HostQueue, WarpQueue>::type;
+    __shared__ Q s_queue[256 / 32];
     __shared__ RootModel s_root;
-    WarpQueue& wq = s_queue[threadIdx.x >> 5];
+    Q& wq = s_queue[threadIdx.x >> 5];
     stage_root<LEARNED>(t, s_root);
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -60,8 +62,12 @@ __global__ void __launch_bounds__(256) k_trilinear(TreeView t, const double* __r
                 active = false;
             }
         }
-        const int h = trilinear_queued<T, LEARNED>(t, s_root, field, pyr, wq, active, inr ? x[i] : 0.0, inr ? y[i] : 0.0,
-                                                  inr ? z[i] : 0.0, hin, o);
+        const double xi = inr ? x[i] : 0.0, yi = inr ? y[i] : 0.0, zi = inr ? z[i] : 0.0;
+        int h;
+        if constexpr (MATES)
+            h = trilinear_mates<T, LEARNED>(t, s_root, field, pyr, wq, active, xi, yi, zi, hin, o);
+        else
+            h = trilinear_queued<T, LEARNED>(t, s_root, field, pyr, wq, active, xi, yi, zi, hin, o);
         if (inr) {
             u[i] = o[0];
             u[n + i] = o[1];
@@ -151,10 +157,14 @@ ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const d
             cudaFreeAsync(pws, s);
             return st;
         }
-        if (learned)
-            OT_LAUNCH((k_trilinear<T, true>), v, x, y, z, n, host_in, field, pyr, u, host_out);
+        if (t->d_mates && learned)
+            OT_LAUNCH((k_trilinear<T, true, true>), v, x, y, z, n, host_in, field, pyr, u, host_out);
+        else if (t->d_mates)
+            OT_LAUNCH((k_trilinear<T, false, true>), v, x, y, z, n, host_in, field, pyr, u, host_out);
+        else if (learned)
+            OT_LAUNCH((k_trilinear<T, true, false>), v, x, y, z, n, host_in, field, pyr, u, host_out);
         else
-            OT_LAUNCH((k_trilinear<T, false>), v, x, y, z, n, host_in, field, pyr, u, host_out);
+            OT_LAUNCH((k_trilinear<T, false, false>), v, x, y, z, n, host_in, field, pyr, u, host_out);
         cudaFreeAsync(pws, s);
     } else if (kernel == OT_PESKIN4) {
         if (learned)

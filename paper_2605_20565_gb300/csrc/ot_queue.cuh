@@ -19,13 +19,18 @@ constexpr int QCAP = 7 * 32;  // level-mate searches of a warp's 32 points (the 
 constexpr unsigned FULL = 0xffffffffu;
 
 // A warp's task list: key searched, and the range to search (the uncovered level-map cell);
-// lo holds the answer once the task has run.
-struct WarpQueue {
-    uint64_t q[QCAP];
-    int lo[QCAP];
-    int len[QCAP];
-    signed char lv[QCAP];  // the answer leaf's level when the search learned it, else -1
+// lo holds the answer once the task has run.  CAP tasks: QCAP for the level-mate searches, 32
+// where only the hosts are searched (the level-mate table gives the rest).
+template <int CAP>
+struct WarpQueueN {
+    static constexpr int cap = CAP;
+    uint64_t q[CAP];
+    int lo[CAP];
+    int len[CAP];
+    signed char lv[CAP];  // the answer leaf's level when the search learned it, else -1
 };
+using WarpQueue = WarpQueueN<QCAP>;
+using HostQueue = WarpQueueN<32>;
 
 // The root model of the learned index, staged in shared memory by every block that searches
 // with it (block-wide call; a no-op for the plain form).
@@ -54,7 +59,8 @@ __device__ __forceinline__ bool map_lookup(const TreeView& t, uint64_t q, int& a
 
 // Appends a task for every lane with need set (warp-wide call); returns the lane's task index
 // or -1.  n is the warp-uniform task count.
-__device__ __forceinline__ int push_task(WarpQueue& w, int& n, bool need, uint64_t q, int lo, int len, unsigned lt) {
+template <typename Q>
+__device__ __forceinline__ int push_task(Q& w, int& n, bool need, uint64_t q, int lo, int len, unsigned lt) {
     const unsigned m = __ballot_sync(FULL, need);
     const int idx = n + __popc(m & lt);
     n += __popc(m);
@@ -81,8 +87,8 @@ __device__ __forceinline__ int push_task(WarpQueue& w, int& n, bool need, uint64
 // and registers.)
 enum { ST_ROUTE = 0, ST_MODEL = 1, ST_PROBE = 2, ST_CHECK = 3, ST_DONE = 4, ST_DESC = 5 };
 
-template <bool LEARNED>
-__device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& root, WarpQueue& w, int ntask,
+template <bool LEARNED, typename Q>
+__device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& root, Q& w, int ntask,
                                           unsigned lt) {
     __syncwarp();
     int cur = -1, lo = 0, len = 0, next = 0, st = ST_DONE, clo = 0, clen = 0, j = 0, lvr = -1;
@@ -166,6 +172,27 @@ __device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& ro
     __syncwarp();
 }
 
+// Host leaf of the point with fixed-point coordinates X, for the lanes with ok set and no host
+// given (h < 0) (warp-wide call): the level-map lookup, then the warp's task list for the lanes
+// whose cell is not covered.  hl receives the leaf's level when the lookup or the descriptor
+// gave it, else stays -1.
+template <bool LEARNED, typename Q>
+__device__ __forceinline__ void host_queued(const TreeView& t, const RootModel& root, Q& w, bool ok,
+                                            const uint64_t X[3], int& h, int& hl) {
+    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+    const uint64_t q = morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32));
+    int ca = 0, ce = 0, clv = -1;
+    const bool need = ok && h < 0 && !map_lookup(t, q, ca, ce, clv);
+    if (ok && h < 0 && !need) h = ca, hl = clv;
+    if (__any_sync(FULL, need)) {
+        int n = 0;
+        const int ix = push_task(w, n, need, q, ca, ce - ca, lt);
+        run_tasks<LEARNED>(t, root, w, n, lt);
+        if (ix >= 0) h = w.lo[ix], hl = w.lv[ix];
+        __syncwarp();
+    }
+}
+
 // Trilinear interpolation at one point per lane (warp-wide call; Sec. 2.3.2 with the
 // level-mate rule):
 //   host leaf of level l, cell c; t_d = offset from the cell centre; s_d = +1 if t_d >= 0;
@@ -188,19 +215,7 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
 
     // host (and its level, when the lookup gives it)
     int h = host_in, hl = -1;
-    {
-        const uint64_t q = morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32));
-        int ca = 0, ce = 0, clv = -1;
-        const bool need = ok && h < 0 && !map_lookup(t, q, ca, ce, clv);
-        if (ok && h < 0 && !need) h = ca, hl = clv;
-        if (__any_sync(FULL, need)) {
-            int n = 0;
-            const int ix = push_task(w, n, need, q, ca, ce - ca, lt);
-            run_tasks<LEARNED>(t, root, w, n, lt);
-            if (ix >= 0) h = w.lo[ix], hl = w.lv[ix];
-            __syncwarp();
-        }
-    }
+    host_queued<LEARNED>(t, root, w, ok, X, h, hl);
     if (!ok) h = 0, hl = -1;  // keeps the lane's reads in bounds; its result is discarded
 
     const int l = hl >= 0 ? hl : (int)t.level[h];
@@ -323,6 +338,61 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
         const bool refined = lvl[corner] > l;
         const long long ri = in_pyr ? (long long)(anc[corner] >> (3 * sh)) : (long long)a[corner];
         const auto f = V::load(refined ? rbase : field, refined ? ri : (long long)a[corner]);
+        v[corner][0] = f.x, v[corner][1] = f.y, v[corner][2] = f.z;
+    }
+    T acc0 = T(0), acc1 = T(0), acc2 = T(0);
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+        acc0 += wt[corner] * v[corner][0];
+        acc1 += wt[corner] * v[corner][1];
+        acc2 += wt[corner] * v[corner][2];
+    }
+    out[0] = acc0;
+    out[1] = acc1;
+    out[2] = acc2;
+    return h;
+}
+
+// The same interpolation with the level-mates read from the octree's level-mate table (built
+// by ot_octree_build_mates): host leaf h of level l, octant o of its cell (bit d: the upper
+// half on axis d), then row 8h + o gives the 8 value slots -- a leaf index, or (top bit set)
+// an index into the cell means in pyr.  The weights, values and summation order are those of
+// trilinear_queued: the results are bit-identical.  Warp-wide call (the host search).
+template <typename T, bool LEARNED, typename Q>
+__device__ __forceinline__ int trilinear_mates(const TreeView& t, const RootModel& root, const T* __restrict__ field,
+                                               const T* __restrict__ pyr, Q& w, bool active, double x,
+                                               double y, double z, int host_in, T out[3]) {
+    using V = Vec4<T>;
+    uint64_t X[3] = {0, 0, 0};
+    const bool ok = active && fixpoint3(x, y, z, X);
+    if (active && !ok) atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
+    int h = host_in, hl = -1;
+    host_queued<LEARNED>(t, root, w, ok, X, h, hl);
+    if (!ok) {
+        out[0] = out[1] = out[2] = qnan<T>();
+        return -1;
+    }
+    const int l = hl >= 0 ? hl : (int)t.level[h];
+    int o = 0;
+    T at[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        o |= (fix_upper_half(X[d], l) ? 1 : 0) << d;
+        const T td = fix_offset<T>(X[d], l);
+        at[d] = td < T(0) ? -td : td;
+    }
+    const uint4* row = t.mates + 2 * (8 * (long long)h + o);
+    const uint4 r0 = __ldg(row), r1 = __ldg(row + 1);
+    const uint32_t sl[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+    T v[8][3], wt[8];
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+        T wc = T(1);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) wc *= ((corner >> d) & 1) ? at[d] : T(1) - at[d];
+        wt[corner] = wc;
+        const uint32_t sv = sl[corner];
+        const auto f = V::load((sv >> 31) ? pyr : field, (long long)(sv & 0x7FFFFFFFu));
         v[corner][0] = f.x, v[corner][1] = f.y, v[corner][2] = f.z;
     }
     T acc0 = T(0), acc1 = T(0), acc2 = T(0);

@@ -1,5 +1,6 @@
 // ot_tune.cu -- autotuner of the batched launch: times graph replays of the batch over a grid
-// of launch shapes (threads per block, 32-point rows per work item, resident blocks per SM)
+// of launch shapes (threads per block, 32-point rows per work item, resident blocks per SM,
+// point order; with the level-mate table, the trilinear launch's own rows and blocks per SM)
 // and, optionally, of level-map levels (the staging depth of the top tree levels), and keeps
 // the fastest.  Timing is by CUDA events on the caller's stream, after one warm-up replay.
 #include <algorithm>
@@ -61,16 +62,56 @@ extern "C" ot_status ot_batch_autotune(ot_octree* t, const ot_group* groups, int
     best.ms = -1.0f;
     best.map_level = t->lmap_level;
     const int start_level = t->lmap_level;
+    // with the level-mate table the delta-kernel and trilinear groups run as two launches: each
+    // part is tuned on its own groups, then the pair is timed together
+    std::vector<ot_group> delta_g, tri_g;
+    for (int g = 0; g < n_groups; ++g) (groups[g].kernel == OT_TRILINEAR ? tri_g : delta_g).push_back(groups[g]);
+    const bool split = t->d_mates != nullptr;
+    const int tri_tiles[] = {2, 4, 8};
+    const int tri_per_sm[] = {1, 2, 3, 4};
     for (int L : levels) {
         if (L != t->lmap_level && (err = ot_octree_set_map_level(t, L, stream)) != OT_OK) break;
-        for (int k = 0; k < 2 * 4 * 2 * 2 && err == OT_OK; ++k) {
-            const ot_launch lp{blocks[(k / 8) % 2], tiles[(k / 2) % 4], per_sm[k % 2], orders[k / 16]};
-            const float ms = time_shape(t, groups, n_groups, d_field, search, lp, reps, s, e0, e1, &err);
-            if (err != OT_OK || ms < 0.0f) continue;
-            ++best.tried;
-            if (best.ms < 0.0f || ms < best.ms) {
+        if (!split) {
+            for (int k = 0; k < 2 * 4 * 2 * 2 && err == OT_OK; ++k) {
+                const ot_launch lp{blocks[(k / 8) % 2], tiles[(k / 2) % 4], per_sm[k % 2], orders[k / 16], 0, 0};
+                const float ms = time_shape(t, groups, n_groups, d_field, search, lp, reps, s, e0, e1, &err);
+                if (err != OT_OK || ms < 0.0f) continue;
+                ++best.tried;
+                if (best.ms < 0.0f || ms < best.ms) {
+                    best.ms = ms;
+                    best.launch = lp;
+                    best.map_level = L;
+                }
+            }
+        } else {
+            ot_launch lp{256, 4, 0, 0, 0, 0};
+            float part_ms = -1.0f;
+            for (int k = 0; !delta_g.empty() && k < 2 * 4 * 2 && err == OT_OK; ++k) {
+                const ot_launch c{blocks[(k / 8) % 2], tiles[(k / 2) % 4], per_sm[k % 2], 0, 0, 0};
+                const float ms = time_shape(t, delta_g.data(), (int)delta_g.size(), d_field, search, c, reps, s, e0,
+                                            e1, &err);
+                if (err != OT_OK || ms < 0.0f) continue;
+                ++best.tried;
+                if (part_ms < 0.0f || ms < part_ms) part_ms = ms, lp = c;
+            }
+            part_ms = -1.0f;
+            ot_launch tri_best = lp;
+            for (int k = 0; !tri_g.empty() && k < 3 * 4 * 2 && err == OT_OK; ++k) {
+                ot_launch c = lp;
+                c.tri_tile = tri_tiles[k % 3];
+                c.tri_blocks_per_sm = tri_per_sm[(k / 3) % 4];
+                c.order_level = orders[k / 12];
+                const float ms = time_shape(t, tri_g.data(), (int)tri_g.size(), d_field, search, c, reps, s, e0, e1,
+                                            &err);
+                if (err != OT_OK || ms < 0.0f) continue;
+                ++best.tried;
+                if (part_ms < 0.0f || ms < part_ms) part_ms = ms, tri_best = c;
+            }
+            if (err != OT_OK) break;
+            const float ms = time_shape(t, groups, n_groups, d_field, search, tri_best, reps, s, e0, e1, &err);
+            if (err == OT_OK && ms >= 0.0f && (best.ms < 0.0f || ms < best.ms)) {
                 best.ms = ms;
-                best.launch = lp;
+                best.launch = tri_best;
                 best.map_level = L;
             }
         }

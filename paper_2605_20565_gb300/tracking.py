@@ -10,7 +10,7 @@ Every step, through the C ABI:
      (``ot_spread``);
   4. the bubbles translate at constant velocities carrying their markers.
 Every ``rebuild_every`` steps the octree is rebuilt around the moved bubbles
-(``ot_octree_build``), the learned index is retrained on the device (``ot_index_train``), the
+(``ot_octree_build``) with its level-mate table (``ot_octree_build_mates``), the learned index is retrained on the device (``ot_index_train``), the
 velocity field is re-sampled at the new leaf centres, the particles are re-stored in Morton
 order of their cells (``ot_points_morton_order``; ``ids`` keeps each one's original index),
 and the batch graph is re-captured: the single-GPU form of re-locating every point after a
@@ -30,7 +30,7 @@ from . import synth
 class Tracker:
     def __init__(self, w: synth.Workload, search: int = 1, rebuild_every: int = 10, tau_steps: float = 10.0,
                  re_coef: float = 0.0, n_leaf_models: int = 1 << 18, n_mid_models: int = 4096, device=None,
-                 sort_points: bool = True):
+                 sort_points: bool = True, mates: bool = True):
         import torch
         from . import OT_PESKIN4, OT_SORTED, OT_TRILINEAR
         self.torch = torch
@@ -52,6 +52,7 @@ class Tracker:
         self.x = T.as_tensor(np.ascontiguousarray(w.particles), device=dev)            # (3, n) FP64
         n = self.x.shape[1]
         self.sort_points = sort_points
+        self.mates = mates  # level-mate table built with every octree
         self.ids = T.arange(n, device=dev)  # original index of each stored particle
         self.v = T.zeros((3, n), dtype=T.float32, device=dev)
         self.a_prev = T.zeros_like(self.v)
@@ -123,6 +124,9 @@ class Tracker:
         prev = ot.ot_index_get_root_params(self.tree) if getattr(self, "tree", None) is not None else None
         self.tree = ot.ot_octree_build(self.spheres_now(), w.lmin, w.lmax)
         t = mark("octree_build", t)
+        if self.mates:
+            ot.ot_octree_build_mates(self.tree, True)
+            t = mark("level_mate_table", t)
         # the first index trains from the spline initialisation; later ones fine-tune the previous
         # network (the bubbles moved by a few cells): a warm start with few steps
         ot.ot_index_train(self.tree, root=ot.OT_ROOT_MLP, n_leaf_models=self.n_leaf_models,
