@@ -648,7 +648,7 @@ def run_tracking(args):
     w = synth.tracking(n_particles=int(200_000_000 * args.scale))
     search = ot.OT_LEARNED if args.search == "learned" else ot.OT_BINARY
     t0 = time.time()
-    tr = tracking.Tracker(w, search=search, rebuild_every=10)
+    tr = tracking.Tracker(w, search=search, rebuild_every=10, mates=not args.no_mates, map_level=args.map_level)
     setup_s = time.time() - t0
     n_leaves = ot.ot_octree_info(tr.tree)[0]
     for _ in range(args.warmup):
@@ -674,6 +674,8 @@ def run_tracking(args):
                       "leaves": int(n_leaves), "markers_peskin4": int(w.markers.shape[1]),
                       "particles_trilinear": int(w.particles.shape[1]),
                       "search": "learned" if search == ot.OT_LEARNED else "binary",
+                      "level_mates": "searched per query" if args.no_mates else "table",
+                      "map_level": ot.ot_octree_get_map_level(tr.tree),
                       "step": "locate+interpolate all points, AB2 advect particles, sorted spread of markers; "
                               "octree rebuild + index retrain + field resample every 10 steps",
                       "l2": "inputs larger than L2; no flush"},

@@ -120,7 +120,8 @@ ot_status ot_octree_copy_leaves(const ot_octree* t, uint64_t* d_keys, uint8_t* d
  * each cell of that level the map holds the leaf at the cell's anchor, so a point in a cell
  * covered by one leaf is located with one table read, and any other point is searched only
  * among its cell's leaves.  8^level * 4 bytes of device memory.  Octrees are created with
- * min(lmax, 7).  Synchronises the stream. */
+ * min(lmax, 7), or 8 when lmax > 10 (a level-map cell's subtree descriptor resolves leaves up
+ * to 3 levels below it).  Synchronises the stream. */
 ot_status ot_octree_set_map_level(ot_octree* t, int level, void* stream);
 /* The current level-map level. */
 ot_status ot_octree_get_map_level(const ot_octree* t, int* level);
@@ -145,6 +146,15 @@ ot_status ot_octree_set_periodic(ot_octree* t, int periodic);
  * periodic setting is part of the table: ot_octree_set_periodic rebuilds it (on the legacy
  * default stream).  Synchronises the stream. */
 ot_status ot_octree_build_mates(ot_octree* t, int enable, void* stream);
+/* *bytes = the table's size, 256 bytes per leaf. */
+ot_status ot_octree_mates_bytes(const ot_octree* t, size_t* bytes);
+/* Builds the table in caller memory (d_buffer: 16-byte aligned, at least ot_octree_mates_bytes
+ * bytes; the caller keeps ownership and must keep it allocated and untouched while the octree
+ * or a batch made on it is used).  A table the library held before is freed.  Lets a caller
+ * that rebuilds octrees reuse one buffer instead of allocating a table per octree.  Errors as
+ * ot_octree_build_mates (OT_ERR_ARG for a short or misaligned buffer).  Synchronises the
+ * stream. */
+ot_status ot_octree_build_mates_in(ot_octree* t, void* d_buffer, size_t bytes, void* stream);
 /* *has = 1 when the level-mate table is built. */
 ot_status ot_octree_has_mates(const ot_octree* t, int* has);
 

@@ -22,7 +22,7 @@ __all__ = [
     "ot_octree_copy_leaves", "ot_octree_set_map_level", "ot_octree_get_map_level", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats", "ot_index_get_root_params",
     "ot_index_mlp_grad", "ot_locate", "ot_interpolate", "ot_interpolate_f64", "ot_spread_workspace_size",
     "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_ibm_mdf", "ot_points_morton_order", "ot_field_fourier", "ot_body_sums", "ot_octree_set_periodic",
-    "ot_octree_build_mates", "ot_octree_has_mates", "ot_field_subtract_mean", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
+    "ot_octree_build_mates", "ot_octree_has_mates", "ot_octree_mates_bytes", "ot_octree_build_mates_in", "ot_field_subtract_mean", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
     "ot_last_error", "ot_launch_count",
 ]
 
@@ -130,6 +130,8 @@ def _L():
                 "ot_octree_set_periodic": (st, [P, i32]),
                 "ot_octree_build_mates": (st, [P, i32, P]),
                 "ot_octree_has_mates": (st, [P, P]),
+                "ot_octree_mates_bytes": (st, [P, P]),
+                "ot_octree_build_mates_in": (st, [P, P, C.c_size_t, P]),
                 "ot_field_subtract_mean": (st, [P, P, P, P]),
                 "ot_points_morton_order": (st, [P, P, P, i64, i32, P, P, C.c_size_t, P]),
                 "ot_ibm_mdf": (st, [P, i32, P, P, P, P, P, i64, C.c_float, C.c_float, i32, P, P, P, P, C.c_size_t, P]),
@@ -472,6 +474,24 @@ def ot_octree_build_mates(tree: Octree, enable: bool = True, stream=None):
     of device memory; trilinear queries and batches made afterwards read their level-mates
     from it (bit-identical results)."""
     _check(_L().ot_octree_build_mates(tree.handle, int(enable), _stream(stream)))
+
+
+def ot_octree_mates_bytes(tree: Octree) -> int:
+    v = C.c_size_t()
+    _check(_L().ot_octree_mates_bytes(tree.handle, C.byref(v)))
+    return v.value
+
+
+def ot_octree_build_mates_in(tree: Octree, buffer, stream=None):
+    """Builds the level-mate table in the caller's buffer (a CUDA uint8 tensor of at least
+    ot_octree_mates_bytes(tree) bytes), which the octree then references (kept alive here)."""
+    torch = _torch()
+    if not (isinstance(buffer, torch.Tensor) and buffer.is_cuda and buffer.dtype == torch.uint8
+            and buffer.is_contiguous()):
+        raise OtError("buffer must be a contiguous CUDA uint8 tensor")
+    _check(_L().ot_octree_build_mates_in(tree.handle, C.c_void_p(buffer.data_ptr()), buffer.numel(),
+                                         _stream(stream)))
+    tree.keep_mates = buffer
 
 
 def ot_octree_has_mates(tree: Octree) -> bool:

@@ -186,8 +186,9 @@ ot_status ot_octree_set_periodic(ot_octree* t, int periodic) {
     if (!t || (periodic != 0 && periodic != 1)) return OT_ERR_ARG;
     if (t->periodic == periodic) return OT_OK;
     t->periodic = periodic;
-    // the level-mate table wraps or clamps at the faces: rebuilt for the new setting
+    // the level-mate table wraps or clamps at the faces: refilled for the new setting
     if (t->d_mates) {
+        OT_CUDA(cudaDeviceSynchronize());
         const ot_status st = build_mates(t, nullptr);
         if (st != OT_OK) return st;
         OT_CUDA(cudaStreamSynchronize(nullptr));
@@ -220,7 +221,7 @@ ot_status ot_octree_destroy(ot_octree* t) {
     if (t->d_nodes) cudaFree(t->d_nodes);
     if (t->d_desc) cudaFree(t->d_desc);
     if (t->d_lmap_lv) cudaFree(t->d_lmap_lv);
-    if (t->d_mates) cudaFree(t->d_mates);
+    if (t->d_mates && t->mates_owned) cudaFree(t->d_mates);
     if (t->d_models) cudaFree(t->d_models);
     if (t->d_mids) cudaFree(t->d_mids);
     if (t->d_root) cudaFree(t->d_root);

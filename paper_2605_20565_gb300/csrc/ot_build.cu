@@ -511,7 +511,9 @@ __global__ void k_lmap_lv(const uint32_t* __restrict__ lmap, const uint8_t* __re
 }
 
 ot_status finish_tree(ot_octree* t, cudaStream_t s, int map_level) {
-    const int L = map_level >= 0 ? std::min(map_level, t->lmax) : std::min(t->lmax, 7);
+    // default: level 7, or 8 for trees deeper than 10 levels (the descriptors then reach lmax)
+    const int L = map_level >= 0 ? std::min(map_level, t->lmax)
+                                 : std::min(t->lmax, std::max(7, std::min(8, t->lmax - 3)));
     const int Lp = std::min(t->lmax, 7);
     if (!t->d_pmap) {
         const int64_t np = (int64_t)1 << (3 * Lp);

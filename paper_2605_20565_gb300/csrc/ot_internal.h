@@ -30,8 +30,10 @@ struct ot_octree {
     int* d_nodes = nullptr;
     int64_t node_off[ot::MAXLEVEL] = {};
     int64_t node_cnt[ot::MAXLEVEL] = {};
-    // level-mate table (null until built): 8 value slots per leaf and octant of its cell
+    // level-mate table (null until built): 8 value slots per leaf and octant of its cell, in
+    // library memory (mates_owned) or the caller's
     uint32_t* d_mates = nullptr;
+    bool mates_owned = false;
     // learned index
     bool has_index = false;
     ot::RootModel root{};
@@ -122,8 +124,10 @@ ot_status build_node_lists(ot_octree* t, cudaStream_t s);
 size_t pyramid_bytes(const ot_octree* t, size_t elem);  // elem: sizeof the field type
 template <typename T> ot_status launch_pyramid(const ot_octree* t, const T* field, T* pyr, cudaStream_t s);
 
-// level-mate table (ot_mates.cu): (re)builds t->d_mates on stream s -------------------------
+// level-mate table (ot_mates.cu): fills t->d_mates (mates_bytes(t) bytes) on stream s -----
 ot_status build_mates(ot_octree* t, cudaStream_t s);
+size_t mates_bytes(const ot_octree* t);
+bool mates_fit(const ot_octree* t);
 
 // Morton order of points (ot_order.cu) ----------------------------------------------------------
 size_t order_ws_bytes(int64_t n);

@@ -16,7 +16,9 @@ template <> __device__ __forceinline__ double qnan<double>() { return __longlong
 
 
 // First cell of level l in the pyramid of cell means: sum_{k<l} 8^k = (8^l - 1) / 7.
-__device__ __forceinline__ long long pyr_offset(int l) { return ((1LL << (3 * l)) - 1) / 7; }
+// sum_{k<l} 8^k = (8^l - 1) / 7: the octal number 11...1 of l digits, i.e. the top l of the 21
+// octal ones of 0x1249249249249249 (no 64-bit division).
+__device__ __forceinline__ long long pyr_offset(int l) { return (long long)(0x1249249249249249ULL >> (3 * (21 - l))); }
 
 // Stencil origin and per-axis weights of a point with fixed-point coordinates X on the
 // finest level lmax (Sec. 2.2: W(x) = prod phi(x_d/dx)/dx).

@@ -30,7 +30,7 @@ from . import synth
 class Tracker:
     def __init__(self, w: synth.Workload, search: int = 1, rebuild_every: int = 10, tau_steps: float = 10.0,
                  re_coef: float = 0.0, n_leaf_models: int = 1 << 18, n_mid_models: int = 4096, device=None,
-                 sort_points: bool = True, mates: bool = True):
+                 sort_points: bool = True, mates: bool = True, map_level: int | None = None):
         import torch
         from . import OT_PESKIN4, OT_SORTED, OT_TRILINEAR
         self.torch = torch
@@ -53,6 +53,7 @@ class Tracker:
         n = self.x.shape[1]
         self.sort_points = sort_points
         self.mates = mates  # level-mate table built with every octree
+        self.map_level = map_level  # level-map level of every octree (None: the library's default)
         self.ids = T.arange(n, device=dev)  # original index of each stored particle
         self.v = T.zeros((3, n), dtype=T.float32, device=dev)
         self.a_prev = T.zeros_like(self.v)
@@ -123,9 +124,18 @@ class Tracker:
             t = mark("reorder", t)
         prev = ot.ot_index_get_root_params(self.tree) if getattr(self, "tree", None) is not None else None
         self.tree = ot.ot_octree_build(self.spheres_now(), w.lmin, w.lmax)
+        if self.map_level is not None:
+            ot.ot_octree_set_map_level(self.tree, self.map_level)
         t = mark("octree_build", t)
         if self.mates:
-            ot.ot_octree_build_mates(self.tree, True)
+            # one table buffer for every octree (grown with 10% headroom when a tree outgrows it):
+            # no allocation and release of ~256 bytes per leaf at every re-adaptation
+            need = ot.ot_octree_mates_bytes(self.tree)
+            buf = getattr(self, "_mates_buf", None)
+            if buf is None or buf.numel() < need:
+                self._mates_buf = buf = None
+                self._mates_buf = T.empty(need + need // 10, dtype=T.uint8, device=self.dev)
+            ot.ot_octree_build_mates_in(self.tree, self._mates_buf)
             t = mark("level_mate_table", t)
         # the first index trains from the spline initialisation; later ones fine-tune the previous
         # network (the bubbles moved by a few cells): a warm start with few steps

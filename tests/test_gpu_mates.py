@@ -244,3 +244,32 @@ def test_autotune_with_table(ot):
     ot.ot_batch_run(b)
     torch.cuda.synchronize()
     assert torch.equal(um, ref_m) and torch.equal(up, ref_p)
+
+
+def test_table_in_caller_buffer(ot, deep):
+    """The table built in a caller buffer gives the same results; the buffer outlives the octree
+    and serves the next one; short or misaligned buffers are refused."""
+    import torch
+    sph, ko, lo, P, field = deep
+    f32 = dev(field.astype(np.float32))
+    x, y, z = pts(P.T)
+    t = ot.ot_octree_build(sph, 3, 9)
+    ref = ot.ot_interpolate(t, ot.OT_TRILINEAR, x, y, z, f32)
+    need = ot.ot_octree_mates_bytes(t)
+    assert need == 256 * ko.size
+    buf = torch.empty(need + 64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ot.OtError):
+        ot.ot_octree_build_mates_in(t, buf[: need - 16])
+    with pytest.raises(ot.OtError):
+        ot.ot_octree_build_mates_in(t, buf[8: need + 8])
+    assert not ot.ot_octree_has_mates(t)
+    ot.ot_octree_build_mates_in(t, buf)
+    assert ot.ot_octree_has_mates(t)
+    assert torch.equal(ot.ot_interpolate(t, ot.OT_TRILINEAR, x, y, z, f32), ref)
+    del t  # the caller's buffer stays allocated
+    t2 = ot.ot_octree_build(sph, 3, 9)
+    ot.ot_octree_build_mates(t2, True)  # a library-owned table first, then replaced
+    ot.ot_octree_build_mates_in(t2, buf)
+    assert torch.equal(ot.ot_interpolate(t2, ot.OT_TRILINEAR, x, y, z, f32), ref)
+    ot.ot_octree_build_mates(t2, False)
+    assert not ot.ot_octree_has_mates(t2)
