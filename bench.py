@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-autotune", action="store_true", help="default launch shape and level map")
     p.add_argument("--no-nomap", action="store_true", help="skip the forms without a level map")
     p.add_argument("--no-mdf", action="store_true", help="skip the multi-direct forcing measurement")
+    p.add_argument("--markers-as-generated", action="store_true",
+                   help="keep the markers in generation order (default: per bubble, Morton order)")
     p.add_argument("--no-mates", action="store_true",
                    help="search the trilinear level-mates per query instead of reading the level-mate table")
     return p.parse_args()
@@ -107,7 +109,8 @@ def describe(w, n_leaves, search):
         "index": search,
         "spread": "Peskin-4 sorted deterministic",
         "level_map": "top levels staged as a dense level map (level autotuned over 6-8 unless given)",
-        "l2": "inputs larger than L2 (tree+field ~0.7 GB, points 1.2 GB); no flush",
+        "l2": "inputs larger than L2 (tree + field ~0.7 GB, level-mate table 256 B/leaf, points 1.2 GB); "
+              "no flush",
     }
 
 
@@ -291,6 +294,8 @@ def run_ours(args):
             dist.barrier()
 
     w = make_workload(args.workload, args.scale, rank)
+    if not args.markers_as_generated:
+        synth.order_markers(w)  # the stored marker order: per bubble, Morton order of positions
     t0 = time.time()
     tree = ot.ot_octree_build(w.spheres, w.lmin, w.lmax)
     torch.cuda.synchronize()
@@ -618,7 +623,11 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": dict(describe(w, n_leaves, INDEX_DESC[args.index] if chosen == "learned" else
                                    "plain: level map + binary search"),
-                          form=chosen, map_level=forms_cfg[chosen][1], launch=forms_cfg[chosen][2]),
+                          form=chosen, map_level=forms_cfg[chosen][1], launch=forms_cfg[chosen][2],
+                          level_mates="table" if forms_cfg[chosen][3] else "searched per query",
+                          marker_order=("as generated (Fibonacci spiral per bubble)" if args.markers_as_generated
+                                        else "per bubble, Morton order of level-10 cells"),
+                          particle_order="as generated (uniform random)"),
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": int(launches), "clocks": clk,
            "breakdown_ms": {"locate_interpolate": batch_ms, "spread": spread_ms, "step": ms_step},

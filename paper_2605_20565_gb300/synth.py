@@ -257,6 +257,30 @@ def _markers_on(centres, diams, counts, seed):
     return np.concatenate(pos, 1), np.concatenate(nrm, 1), np.concatenate(grp)
 
 
+def marker_morton_order(markers: np.ndarray, groups: np.ndarray, level: int = 10) -> np.ndarray:
+    """The permutation that stores markers bubble by bubble, each bubble's in Morton order of
+    the level-``level`` cells holding them (consecutive markers are then neighbours on the
+    surface: a warp's markers share parent blocks and stencil cells)."""
+    if markers.shape[1] == 0:
+        return np.arange(0)
+    q = np.floor(np.clip(markers, 0.0, np.nextafter(1.0, 0.0)) * float(1 << level)).astype(np.uint64)
+    key = np.zeros(q.shape[1], np.uint64)
+    for b in range(level):
+        for d in range(3):
+            key |= ((q[d] >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + d)
+    return np.lexsort((key, groups))
+
+
+def order_markers(w: Workload) -> np.ndarray:
+    """Stores the workload's markers (positions, forces, groups) in marker_morton_order; returns
+    the permutation (stored marker i is input marker perm[i])."""
+    perm = marker_morton_order(w.markers, w.marker_group)
+    w.markers = np.ascontiguousarray(w.markers[:, perm])
+    w.forces = np.ascontiguousarray(w.forces[:, perm])
+    w.marker_group = np.ascontiguousarray(w.marker_group[perm])
+    return perm
+
+
 def internal_markers(centres, diameters, h: float):
     """Lagrangian points inside each body on a cubic lattice of spacing h centred on the body
     (the internal markers of Sec. 2.3, spacing the finest cell): the points c + h (i, j, k)

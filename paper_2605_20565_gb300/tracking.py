@@ -65,12 +65,7 @@ class Tracker:
         # each stored marker to its input index.
         m_ids = np.arange(w.markers.shape[1])
         if sort_points and w.markers.shape[1] > 0:
-            q = np.floor(np.clip(w.markers, 0.0, np.nextafter(1.0, 0.0)) * 1024.0).astype(np.uint64)
-            key = np.zeros(q.shape[1], np.uint64)
-            for b in range(10):
-                for d in range(3):
-                    key |= ((q[d] >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + d)
-            m_ids = np.lexsort((key, w.marker_group))
+            m_ids = synth.marker_morton_order(w.markers, w.marker_group)
         self.m_ids = T.as_tensor(m_ids, device=dev)
         self.m_grp = T.as_tensor(w.marker_group[m_ids].astype(np.int64), device=dev)
         self.m_off = T.as_tensor(np.ascontiguousarray((w.markers - self.centres0[w.marker_group].T)[:, m_ids]),
