@@ -56,6 +56,76 @@ __global__ void k_advect(double* __restrict__ x, float* __restrict__ v, float* _
     }
 }
 
+// The same step for 4 consecutive particles per thread with 16-byte loads and stores (every
+// component plane 16-byte aligned: n % 4 == 0 and aligned bases); identical arithmetic.
+__device__ __forceinline__ void advect_one(double& x, float& v, float& ap, float& vp, float rel, float fp,
+                                           float tau, float dt, int first, int periodic) {
+    const float vn = v;
+    const float an = fp * rel / tau;
+    const float am = first ? an : ap;
+    const float vm = first ? vn : vp;
+    v = vn + dt * (1.5f * an - 0.5f * am);
+    double xn = x + (double)(dt * (1.5f * vn - 0.5f * vm));
+    const long long xb = __double_as_longlong(xn);
+    if (periodic && (xb < 0 || xb >= 0x3FF0000000000000LL) && xb != (long long)0x8000000000000000ULL) {
+        xn -= floor(xn);
+        if (xn >= 1.0) xn = 0.0;
+    }
+    x = xn;
+    ap = an;
+    vp = vn;
+}
+
+__global__ void __launch_bounds__(256) k_advect4(double* __restrict__ x, float* __restrict__ v,
+                                                 float* __restrict__ ap, float* __restrict__ vp,
+                                                 const float* __restrict__ u, int64_t n, float tau, float re_coef,
+                                                 float dt, int first, int periodic) {
+    const int64_t nq = n / 4;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        float4 uu[3], vv[3], aa[3], pp[3];
+        double2 xx[3][2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            uu[d] = reinterpret_cast<const float4*>(u + d * n)[q];
+            vv[d] = reinterpret_cast<const float4*>(v + d * n)[q];
+            if (!first) {
+                aa[d] = reinterpret_cast<const float4*>(ap + d * n)[q];
+                pp[d] = reinterpret_cast<const float4*>(vp + d * n)[q];
+            }
+            xx[d][0] = reinterpret_cast<const double2*>(x + d * n)[2 * q];
+            xx[d][1] = reinterpret_cast<const double2*>(x + d * n)[2 * q + 1];
+        }
+        float* uf[3] = {&uu[0].x, &uu[1].x, &uu[2].x};
+        float* vf[3] = {&vv[0].x, &vv[1].x, &vv[2].x};
+        float* af[3] = {&aa[0].x, &aa[1].x, &aa[2].x};
+        float* pf[3] = {&pp[0].x, &pp[1].x, &pp[2].x};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float rel[3], mag2 = 0.0f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                rel[d] = uf[d][j] - vf[d][j];
+                mag2 += rel[d] * rel[d];
+            }
+            float fp = 1.0f;
+            if (re_coef > 0.0f) fp = 1.0f + 0.15f * powf(re_coef * sqrtf(mag2), 0.687f);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                double& xr = j < 2 ? (j == 0 ? xx[d][0].x : xx[d][0].y) : (j == 2 ? xx[d][1].x : xx[d][1].y);
+                advect_one(xr, vf[d][j], af[d][j], pf[d][j], rel[d], fp, tau, dt, first, periodic);
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            reinterpret_cast<float4*>(v + d * n)[q] = vv[d];
+            reinterpret_cast<float4*>(ap + d * n)[q] = aa[d];
+            reinterpret_cast<float4*>(vp + d * n)[q] = pp[d];
+            reinterpret_cast<double2*>(x + d * n)[2 * q] = xx[d][0];
+            reinterpret_cast<double2*>(x + d * n)[2 * q + 1] = xx[d][1];
+        }
+    }
+}
+
 template <typename T>
 ot_status interp_any(const ot_octree* t, int kernel, const double* x, const double* y, const double* z,
                             int64_t n, const int32_t* host_in, int search, const T* field, T* u, int32_t* host_out,
@@ -330,8 +400,17 @@ ot_status ot_advect_ab2(double* x, float* v, float* ap, float* vp, const float* 
                         float dt, int first, int periodic, void* stream) {
     if (n < 0 || (n > 0 && (!x || !v || !ap || !vp || !u)) || !(tau > 0.0f) || !(re_coef >= 0.0f)) return OT_ERR_ARG;
     if (n == 0) return OT_OK;
-    const int64_t g = std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
-    k_advect<<<(unsigned)g, 256, 0, (cudaStream_t)stream>>>(x, v, ap, vp, u, n, tau, re_coef, dt, first, periodic);
+    const bool aligned = n % 4 == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)v & 15) == 0 &&
+                         ((uintptr_t)ap & 15) == 0 && ((uintptr_t)vp & 15) == 0 && ((uintptr_t)u & 15) == 0;
+    if (aligned) {
+        const int64_t g = std::min<int64_t>((n / 4 + 255) / 256, (int64_t)num_sms() * 8);
+        k_advect4<<<(unsigned)g, 256, 0, (cudaStream_t)stream>>>(x, v, ap, vp, u, n, tau, re_coef, dt, first,
+                                                                 periodic);
+    } else {
+        const int64_t g = std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
+        k_advect<<<(unsigned)g, 256, 0, (cudaStream_t)stream>>>(x, v, ap, vp, u, n, tau, re_coef, dt, first,
+                                                                periodic);
+    }
     count_launch();
     OT_CUDA(cudaGetLastError());
     return OT_OK;

@@ -461,10 +461,10 @@ def test_ordered_batch_gives_identical_results(ot, deep, order_level, torch_mod)
 # Advection step
 # ---------------------------------------------------------------------------------------
 
-def test_advect_ab2_matches_oracle(ot, torch_mod):
+@pytest.mark.parametrize("n", [1000, 1001])  # the 4-particle vector kernel, and the scalar one
+def test_advect_ab2_matches_oracle(ot, torch_mod, n):
     torch = torch_mod
     rng = np.random.default_rng(31)
-    n = 1000
     x = rng.uniform(0.2, 0.8, (3, n))
     v = rng.normal(scale=0.1, size=(3, n)).astype(np.float32)
     u = rng.normal(scale=0.1, size=(3, n)).astype(np.float32)
@@ -476,6 +476,31 @@ def test_advect_ab2_matches_oracle(ot, torch_mod):
         ot.ot_advect_ab2(dx, dv, da, dvp, dev(u), 0.05, 2.0, 1e-3, step == 0)
     assert rel_err(dv.cpu().numpy(), st["v"]) <= TOL32
     assert np.abs(dx.cpu().numpy() - st["x"]).max() <= 1e-9
+
+
+def test_advect_vector_and_scalar_kernels_agree(ot, torch_mod):
+    """The 4-particle kernel (aligned planes) and the scalar one (planes 4 bytes off) give the
+    same bits, with the drag law on and positions wrapping at every face."""
+    torch = torch_mod
+    rng = np.random.default_rng(32)
+    n = 4096
+    x0 = np.concatenate([rng.uniform(0, 1e-4, (3, n // 2)), 1.0 - rng.uniform(1e-12, 1e-4, (3, n // 2))], 1)
+    v0 = rng.normal(scale=0.5, size=(3, n)).astype(np.float32)
+    u0 = rng.normal(scale=0.5, size=(3, n)).astype(np.float32)
+    outs = []
+    for off in (0, 1):
+        def buf(a, dtype):
+            t = torch.zeros(3 * n + off, dtype=dtype, device="cuda")
+            t[off:] = torch.as_tensor(np.ascontiguousarray(a).reshape(-1), dtype=dtype)
+            return t[off:].view(3, n)
+        x, v = buf(x0, torch.float64), buf(v0, torch.float32)
+        ap, vp, u = buf(np.zeros((3, n)), torch.float32), buf(np.zeros((3, n)), torch.float32), buf(u0, torch.float32)
+        for step in range(3):
+            ot.ot_advect_ab2(x, v, ap, vp, u, 0.05, 2.0, 1e-3, step == 0, periodic=True)
+        outs.append([t.clone() for t in (x, v, ap, vp)])
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    assert bool(((outs[0][0] >= 0) & (outs[0][0] < 1)).all())
 
 
 @pytest.fixture(scope="module")
