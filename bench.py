@@ -114,7 +114,7 @@ def describe(w, n_leaves, search):
     }
 
 
-BATCH_SOURCES = ("ot_batch.cu", "ot_queue.cuh", "ot_points.cuh", "ot_common.cuh")
+BATCH_SOURCES = ("ot_batch.cu", "ot_queue.cuh", "ot_points.cuh", "ot_common.cuh", "ot_pyramid.cu", "ot_mates.cu")
 
 
 def kernel_sources_hash() -> str:
@@ -127,9 +127,10 @@ def kernel_sources_hash() -> str:
     return h.hexdigest()
 
 
-def batch_traffic(workload: str, form: str, map_level: int):
-    """DRAM bytes of one batch launch from the committed ncu summary, when it was taken on this
-    workload, form and level map with the current kernel sources; else (None, reason)."""
+def batch_traffic(workload: str, form: str, map_level: int, mates: bool):
+    """DRAM bytes of one batch graph replay (every kernel in it) from the committed ncu summary,
+    when it was taken on this workload, form, level map and level-mate form with the current
+    kernel sources; else (None, reason)."""
     path = os.path.join(ROOT, "profiles", f"k_batch_{workload.split('_l')[0]}_traffic.txt")
     if not os.path.exists(path):
         return None, "no capture"
@@ -138,11 +139,12 @@ def batch_traffic(workload: str, form: str, map_level: int):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             d[k.strip()] = v.strip()
-    if d.get("workload") != workload or d.get("form") != form or int(d.get("map_level", -1)) != map_level:
-        return None, "capture taken on another workload, form or level map"
+    if (d.get("workload") != workload or d.get("form") != form or int(d.get("map_level", -1)) != map_level
+            or d.get("level_mates") != ("table" if mates else "searched per query")):
+        return None, "capture taken on another workload, form, level map or level-mate form"
     if d.get("kernel_sources_sha256") != kernel_sources_hash():
         return None, "kernel changed since the capture"
-    return int(d["bytes_per_launch"]), os.path.relpath(path, ROOT)
+    return int(d["bytes_per_replay"]), os.path.relpath(path, ROOT)
 
 
 def measured_peaks():
@@ -589,8 +591,10 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     alg_bytes = npts * BYTES_PER_POINT + n_leaves * BYTES_PER_LEAF
     achieved = alg_bytes / (batch_ms / 1e3) / 1e9
-    traffic, traffic_src = batch_traffic(w.name, chosen, forms_cfg[chosen][1])
-    roof = {"bound": "hbm", "kernel": "k_batch (locate + interpolate, persistent, graph)", "achieved": achieved,
+    traffic, traffic_src = batch_traffic(w.name, chosen, forms_cfg[chosen][1], forms_cfg[chosen][3])
+    roof = {"bound": "hbm", "kernel": "batch graph replay (cell means + k_batch delta-kernel launch + k_batch "
+                                      "trilinear launch): locate + interpolate of every point",
+            "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(alg_bytes),
             "bytes_rule": f"{BYTES_PER_POINT} B/point + {BYTES_PER_LEAF} B/leaf"}
