@@ -574,6 +574,9 @@ TreeView tree_view(const ot_octree* t) {
     v.pyr_level = t->pyr_level;
     v.periodic = t->periodic;
     v.mates = reinterpret_cast<const uint4*>(t->d_mates);
+    v.pnbr = (t->d_mates && t->lmax >= 1)
+                 ? reinterpret_cast<const int*>(reinterpret_cast<const char*>(t->d_mates) + (size_t)256 * t->n)
+                 : nullptr;
     v.root = t->d_root;
     v.models = t->d_models;
     v.mids = t->d_mids;

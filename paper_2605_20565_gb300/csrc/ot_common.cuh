@@ -147,6 +147,9 @@ struct TreeView {
     // level-mate table: for leaf h and octant o, the 8 value slots of its trilinear
     // level-mates at mates[2 (8h + o)], two uint4 (null when not built)
     const uint4* __restrict__ mates;
+    // parent-block table: row b = first children of the 27 blocks around the block whose first
+    // child is leaf 8b.. (32 entries per row), -1 where none (null when not built)
+    const int* __restrict__ pnbr;
     // learned search: root -> (optional mid models) -> leaf models
     const RootModel* __restrict__ root;  // device copy
     const LeafModel* __restrict__ models;

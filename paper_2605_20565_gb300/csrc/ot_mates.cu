@@ -10,6 +10,15 @@
 // A query then needs its host leaf, one 32-byte row and the 8 values: the values are those the
 // per-query search finds, so results are bit-identical either way.
 // 256 bytes per leaf; the table depends on the leaves and the periodic setting only.
+//
+// Built with it, the parent-block table of the delta kernels (Sec. 2.2 stencils on the finest
+// level): for every parent block -- a cell of level lmax-1 whose 8 children are leaves of
+// level lmax, identified by its first child's index a0 (a0 >> 3 is unique per block) -- row
+// a0 >> 3 holds the first child of each of the 27 blocks (b + {-1, 0, 1}^3, entry
+// sum (delta_d + 1) 3^d), or -1 for a block outside the cube (wrapped when periodic) or not
+// refined to the finest level; 32 entries per row (128 bytes).  A delta stencil's 2-3 blocks
+// per axis all lie within one block's neighbourhood, so a marker needs one lookup and one row
+// instead of one lookup per block (visit_parents).
 #include <algorithm>
 
 #include "ot_internal.h"
@@ -131,9 +140,52 @@ __global__ void __launch_bounds__(256, 4) k_mates(TreeView t, uint2* __restrict_
     }
 }
 
+// One warp per row slot s (leaves 8s .. 8s+7 hold at most one first child of a block): lanes
+// 0..7 find it, then lane k < 27 resolves block b + delta(k); lanes 27..31 write -1 padding.
+__global__ void __launch_bounds__(256) k_pnbr(TreeView t, int64_t nslots, int* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lp = t.lmax - 1;
+    const int sh = MAXLEVEL - lp;
+    const uint64_t pmask = key_span(lp) - 1;
+    const int ncell = 1 << lp;
+    for (int64_t sl = warp0; sl < nslots; sl += nwarps) {
+        const int64_t a = 8 * sl + lane;
+        bool first = false;
+        if (lane < 8 && a < t.n) first = (int)t.level[a] == t.lmax && (ldg_key(t.key + a) & pmask) == 0;
+        const unsigned m = __ballot_sync(0xffffffffu, first);
+        if (!m) continue;  // warp-uniform
+        const int64_t a0 = 8 * sl + (__ffs(m) - 1);
+        uint32_t b[3];
+        demorton3(ldg_key(t.key + a0) >> (3 * sh), b[0], b[1], b[2]);
+        int v = -1;
+        if (lane < 27) {
+            const int dir[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+            int q[3];
+            bool inside = true;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                q[d] = (int)b[d] + dir[d];
+                if (t.periodic) q[d] = (q[d] + ncell) & (ncell - 1);
+                inside = inside && q[d] >= 0 && q[d] < ncell;
+            }
+            if (inside) {
+                const uint64_t anchor = morton3((uint32_t)q[0], (uint32_t)q[1], (uint32_t)q[2]) << (3 * sh);
+                const int f = search_plain(t, anchor);
+                if ((int)t.level[f] == t.lmax && ldg_key(t.key + f) == anchor) v = f;
+            }
+        }
+        out[32 * sl + lane] = v;
+    }
+}
+
 } // namespace
 
-size_t mates_bytes(const ot_octree* t) { return (size_t)256 * (size_t)t->n; }
+size_t pnbr_slots(const ot_octree* t) { return t->lmax >= 1 ? (size_t)(t->n / 8 + 1) : 0; }
+
+// level-mate table, then the parent-block table
+size_t mates_bytes(const ot_octree* t) { return (size_t)256 * (size_t)t->n + 128 * pnbr_slots(t); }
 
 // Every slot must fit in 31 bits.
 bool mates_fit(const ot_octree* t) {
@@ -152,6 +204,14 @@ ot_status build_mates(ot_octree* t, cudaStream_t s) {
     const int64_t grid = std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * std::max(per_sm, 1));
     k_mates<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(v, reinterpret_cast<uint2*>(t->d_mates));
     count_launch();
+    const int64_t nslots = (int64_t)pnbr_slots(t);
+    if (nslots > 0) {
+        int* pn = reinterpret_cast<int*>(reinterpret_cast<char*>(t->d_mates) + (size_t)256 * t->n);
+        OT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pnbr, 256, 0));
+        const int64_t g2 = std::min<int64_t>((nslots + 7) / 8, (int64_t)num_sms() * std::max(per_sm, 1));
+        k_pnbr<<<(unsigned)std::max<int64_t>(g2, 1), 256, 0, s>>>(v, nslots, pn);
+        count_launch();
+    }
     OT_CUDA(cudaGetLastError());
     return OT_OK;
 }

@@ -15,9 +15,9 @@ template <> __device__ __forceinline__ float qnan<float>() { return __int_as_flo
 template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
 
 
-// First cell of level l in the pyramid of cell means: sum_{k<l} 8^k = (8^l - 1) / 7.
-// sum_{k<l} 8^k = (8^l - 1) / 7: the octal number 11...1 of l digits, i.e. the top l of the 21
-// octal ones of 0x1249249249249249 (no 64-bit division).
+// First cell of level l in the pyramid of cell means: sum_{k<l} 8^k = (8^l - 1) / 7, the octal
+// number 11...1 of l digits, i.e. the top l of the 21 octal ones of 0x1249249249249249 (no
+// 64-bit division).
 __device__ __forceinline__ long long pyr_offset(int l) { return (long long)(0x1249249249249249ULL >> (3 * (21 - l))); }
 
 // Stencil origin and per-axis weights of a point with fixed-point coordinates X on the
@@ -44,9 +44,9 @@ __device__ __forceinline__ T stencil_weight_1d(int lmax, uint64_t X, int a) {
 }
 
 // Parent blocks (2x2x2 cells of level lmax, i.e. cells of level lmax-1) overlapping the
-// delta-kernel stencil whose first cell is i0.  For each one, one search finds its first
-// child; a parent whose first child is a leaf of level lmax has all 8 children as
-// consecutive leaves.  A parent in the same grandparent as the last one found is usually 8
+// delta-kernel stencil whose first cell is i0.  With the parent-block table, the middle block's
+// row gives every block's first child; otherwise one search per block finds it.  A parent
+// whose first child is a leaf of level lmax has all 8 children as consecutive leaves.  A parent in the same grandparent as the last one found is usually 8
 // leaves per child-number step away, which one key comparison proves.  The visitor gets
 // (a0, bx, by, bz, P) with a0 the first child's index, or -1 when the parent is outside the
 // cube (a periodic cube wraps it instead) or not refined to the finest level.
@@ -61,6 +61,35 @@ __device__ __forceinline__ void visit_parents(const TreeView& t, const int i0[3]
     for (int d = 0; d < 3; ++d) {
         p0[d] = floordiv2(i0[d]);
         pn[d] = floordiv2(i0[d] + W - 1) - p0[d] + 1;
+    }
+    if (t.pnbr) {
+        // the parent-block table: every stencil block lies within one block of the middle one,
+        // whose row gives all their first children -- one lookup and one row of loads
+        int pm[3], qm[3];
+        bool inside = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            pm[d] = p0[d] + (pn[d] == 3 ? 1 : 0);
+            qm[d] = t.periodic ? (pm[d] + np_cells) & (np_cells - 1) : pm[d];
+            inside = inside && qm[d] >= 0 && qm[d] < np_cells;
+        }
+        int am = -1;
+        if (inside) {
+            const uint64_t anchor = morton3((uint32_t)qm[0] << shp, (uint32_t)qm[1] << shp, (uint32_t)qm[2] << shp);
+            const int a = search<LEARNED>(t, anchor);
+            if (ldg_key(t.key + a) == anchor && t.level[a] == t.lmax) am = a;
+        }
+        if (am >= 0) {  // else (the middle block is not refined to the finest level) the walk below
+            const int* __restrict__ row = t.pnbr + 32 * (size_t)(am >> 3);
+            for (int bz = 0; bz < pn[2]; ++bz)
+                for (int by = 0; by < pn[1]; ++by)
+                    for (int bx = 0; bx < pn[0]; ++bx) {
+                        const int P[3] = {p0[0] + bx, p0[1] + by, p0[2] + bz};
+                        const int k = (P[0] - pm[0] + 1) + 3 * (P[1] - pm[1] + 1) + 9 * (P[2] - pm[2] + 1);
+                        pvisit(__ldg(row + k), bx, by, bz, P);
+                    }
+            return;
+        }
     }
     int prevP[3] = {-1, -1, -1}, prev_a0 = -1;
     for (int bz = 0; bz < pn[2]; ++bz)

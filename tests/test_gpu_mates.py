@@ -256,7 +256,7 @@ def test_table_in_caller_buffer(ot, deep):
     t = ot.ot_octree_build(sph, 3, 9)
     ref = ot.ot_interpolate(t, ot.OT_TRILINEAR, x, y, z, f32)
     need = ot.ot_octree_mates_bytes(t)
-    assert need == 256 * ko.size
+    assert need == 256 * ko.size + 128 * (ko.size // 8 + 1)  # level-mate rows, then parent-block rows
     buf = torch.empty(need + 64, dtype=torch.uint8, device="cuda")
     with pytest.raises(ot.OtError):
         ot.ot_octree_build_mates_in(t, buf[: need - 16])
@@ -273,3 +273,46 @@ def test_table_in_caller_buffer(ot, deep):
     assert torch.equal(ot.ot_interpolate(t2, ot.OT_TRILINEAR, x, y, z, f32), ref)
     ot.ot_octree_build_mates(t2, False)
     assert not ot.ot_octree_has_mates(t2)
+
+
+@pytest.mark.parametrize("kernel", [2, 3])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_parent_block_table_delta_paths(ot, kernel, periodic):
+    """Delta-kernel interpolation and sorted spreading read the parent-block table built with
+    the level-mate table: identical bits with and without it, and the oracle's values --
+    markers on a refined sphere, across the cube's faces (periodic), and in cells whose
+    stencils leave the finest level."""
+    import torch
+    from paper_2605_20565_gb300 import synth
+    sph = np.array([[0.5, 0.5, 0.5, 0.2, 0.06], [0.05, 0.95, 0.5, 0.1, 0.06]])
+    ko, lo = oracle.octree_build(sph, 3, 7)
+    t = ot.ot_octree_build(sph, 3, 7)
+    if periodic:
+        ot.ot_octree_set_periodic(t, True)
+    rng = np.random.default_rng(8)
+    d = rng.normal(size=(3, 3000))
+    X = np.concatenate([np.array([[0.5], [0.5], [0.5]]) + 0.2 * d / np.linalg.norm(d, axis=0),
+                        np.array([[0.05], [0.95], [0.5]]) + 0.1 * d / np.linalg.norm(d, axis=0),
+                        rng.uniform(0, 1, (3, 500))], 1)
+    X = np.mod(X, 1.0)
+    X = X[:, np.all((X >= 0) & (X < 1), axis=0)]
+    field = synth.sin_field(oracle.leaf_centres(ko, lo)).astype(np.float32)
+    F = rng.normal(size=(3, X.shape[1])).astype(np.float32)
+    x, y, z = pts(X)
+
+    def run():
+        u = ot.ot_interpolate(t, kernel, x, y, z, dev(field))
+        f = torch.zeros((ko.size, 4), dtype=torch.float32, device="cuda")
+        ot.ot_spread(t, kernel, ot.OT_SORTED, x, y, z, dev(F), f)
+        fa = torch.zeros((ko.size, 4), dtype=torch.float32, device="cuda")
+        ot.ot_spread(t, kernel, ot.OT_ATOMIC, x, y, z, dev(F), fa)
+        return u, f, fa
+
+    (u, f, fa), (um, fm, fam) = both(ot, t, run)
+    assert torch.equal(u, um) and torch.equal(f, fm)
+    assert float((fa - fam).abs().max()) <= 1e-5 * float(f.abs().max())
+    ref, _ = oracle.interp_delta(ko, lo, 7, kernel, field.astype(np.float64), *X, periodic=periodic)
+    ok = ~np.isnan(ref).any(axis=0)
+    assert rel_err(um.cpu().numpy()[:, ok], ref[:, ok]) <= TOL32
+    fref, _ = oracle.spread_delta(ko, lo, 7, kernel, *X, F.astype(np.float64), periodic=periodic)
+    assert rel_err(fm.cpu().numpy()[:, :3], fref[:, :3]) <= TOL32
