@@ -661,7 +661,12 @@ def run_tracking(args):
     w = synth.tracking(n_particles=int(200_000_000 * args.scale))
     search = ot.OT_LEARNED if args.search == "learned" else ot.OT_BINARY
     t0 = time.time()
-    tr = tracking.Tracker(w, search=search, rebuild_every=10, mates=not args.no_mates, map_level=args.map_level)
+    launch = None
+    if args.launch:
+        vals = [int(v) for v in args.launch.split(",")]
+        launch = dict(zip(("block", "tile", "blocks_per_sm", "order_level", "tri_tile", "tri_blocks_per_sm"), vals))
+    tr = tracking.Tracker(w, search=search, rebuild_every=10, mates=not args.no_mates, map_level=args.map_level,
+                          launch=launch)
     setup_s = time.time() - t0
     n_leaves = ot.ot_octree_info(tr.tree)[0]
     for _ in range(args.warmup):
@@ -689,6 +694,7 @@ def run_tracking(args):
                       "search": "learned" if search == ot.OT_LEARNED else "binary",
                       "level_mates": "searched per query" if args.no_mates else "table",
                       "map_level": ot.ot_octree_get_map_level(tr.tree),
+                      "launch": tr.launch, "launch_autotuned": launch is None,
                       "step": "locate+interpolate all points, AB2 advect particles, sorted spread of markers; "
                               "octree rebuild + index retrain + field resample every 10 steps",
                       "l2": "inputs larger than L2; no flush"},

@@ -381,7 +381,8 @@ ot_status ot_batch_destroy(ot_batch* b);
  * events on `stream`, after one warm-up replay) and returns the fastest.  With the level-mate
  * table built the two launches are tuned one after the other: the delta-kernel groups alone
  * over threads x rows x blocks per SM (16 shapes), then the trilinear groups alone over
- * tri_tile {2, 4, 8} x tri_blocks_per_sm {1, 2, 3, 4} x order (24 shapes), and the pair is
+ * tri_tile {2, 4, 8} x tri_blocks_per_sm {1, 2, 3, 4} x (256 / threads) x order (24 shapes:
+ * 8 to 32 resident warps per SM at the delta launch's block size), and the pair is
  * timed together.  The octree is left at the chosen level-map level (batches made earlier on
  * it must be recreated).  The groups' outputs are overwritten.  Synchronises the stream; takes
  * about (1 + reps) * 32 (or 41) * levels replays. */

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) k_spread_emit(TreeView t, const double* _
 // one parent block, markers in index order) that starts inside its chunk, reading past the
 // chunk's end to finish its last run: balanced work, no compaction of run heads.  Each run
 // accumulates its 8 children and adds each touched child to f once.
-constexpr int RC = 32;
+constexpr int RC = 64;
 
 template <typename T, int K>
 __global__ void __launch_bounds__(256) k_spread_reduce(const uint64_t* __restrict__ pairs, int64_t npairs, int lmax,

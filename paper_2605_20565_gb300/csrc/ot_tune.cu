@@ -99,7 +99,9 @@ extern "C" ot_status ot_batch_autotune(ot_octree* t, const ot_group* groups, int
             for (int k = 0; !tri_g.empty() && k < 3 * 4 * 2 && err == OT_OK; ++k) {
                 ot_launch c = lp;
                 c.tri_tile = tri_tiles[k % 3];
-                c.tri_blocks_per_sm = tri_per_sm[(k / 3) % 4];
+                // resident warps per SM of 8, 16, 24, 32 whatever the block size the delta
+                // launch chose
+                c.tri_blocks_per_sm = tri_per_sm[(k / 3) % 4] * (256 / lp.block);
                 c.order_level = orders[k / 12];
                 const float ms = time_shape(t, tri_g.data(), (int)tri_g.size(), d_field, search, c, reps, s, e0, e1,
                                             &err);

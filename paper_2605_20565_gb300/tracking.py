@@ -30,7 +30,8 @@ from . import synth
 class Tracker:
     def __init__(self, w: synth.Workload, search: int = 1, rebuild_every: int = 10, tau_steps: float = 10.0,
                  re_coef: float = 0.0, n_leaf_models: int = 1 << 18, n_mid_models: int = 4096, device=None,
-                 sort_points: bool = True, mates: bool = True, map_level: int | None = None):
+                 sort_points: bool = True, mates: bool = True, map_level: int | None = None,
+                 launch: dict | None = None, autotune: bool = True):
         import torch
         from . import OT_PESKIN4, OT_SORTED, OT_TRILINEAR
         self.torch = torch
@@ -54,6 +55,7 @@ class Tracker:
         self.sort_points = sort_points
         self.mates = mates  # level-mate table built with every octree
         self.map_level = map_level  # level-map level of every octree (None: the library's default)
+        self.launch = launch  # launch shape of the batch (None: the library's default)
         self.ids = T.arange(n, device=dev)  # original index of each stored particle
         self.v = T.zeros((3, n), dtype=T.float32, device=dev)
         self.a_prev = T.zeros_like(self.v)
@@ -79,6 +81,19 @@ class Tracker:
         self.ws = T.empty(1, dtype=T.uint8, device=dev)  # sized at the first rebuild
         self.timings = {"rebuild_s": 0.0, "rebuilds": 0}
         self._rebuild()
+        if autotune and launch is None:
+            # the launch shape for this point order (the trilinear launch wants more resident
+            # warps for Morton-ordered particles than for random ones), tuned once on the
+            # first octree and kept for the later ones
+            import paper_2605_20565_gb300 as ot
+            K_P4, _, K_TRI = self.kinds
+            groups = [dict(kernel=K_P4, x=self.mx[0], y=self.mx[1], z=self.mx[2], u=self.um),
+                      dict(kernel=K_TRI, x=self.x[0], y=self.x[1], z=self.x[2], u=self.u)]
+            r = ot.ot_batch_autotune(self.tree, groups, self.field, search=self.search, tune_map_level=False,
+                                     reps=2)
+            self.launch = r["launch"]
+            self.tuned = r
+            self.batch = ot.ot_batch_create(self.tree, groups, self.field, search=self.search, launch=self.launch)
         umax = float(self.field[:, :3].abs().max())
         self.dt = self.h / max(umax, 1e-12)
         self.tau = tau_steps * self.dt
@@ -147,7 +162,7 @@ class Tracker:
         K_P4, _, K_TRI = self.kinds
         self.batch = ot.ot_batch_create(self.tree, [dict(kernel=K_P4, x=mx, y=my, z=mz, u=self.um),
                                                     dict(kernel=K_TRI, x=px, y=py, z=pz, u=self.u)],
-                                        self.field, search=self.search)
+                                        self.field, search=self.search, launch=self.launch)
         need = ot.ot_spread_workspace_size(self.tree, K_P4, self.mx.shape[1])
         if self.ws.numel() < need:
             self.ws = T.empty(need, dtype=T.uint8, device=self.dev)
