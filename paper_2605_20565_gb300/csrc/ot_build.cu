@@ -12,6 +12,7 @@
 //      leaf counts bottom-up and offsets top-down place every leaf at its rank without a
 //      global sort.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "ot_internal.h"
@@ -71,11 +72,16 @@ __device__ __forceinline__ bool maybe_near(const float lo[3], float h, const ot_
 }
 
 // Candidate cells of level l: the 8^l cells (parent == null, l == lmin) or the children of the
-// refined parents; flag[j] = criterion, cand[j] = key.
+// refined parents; flag[j] = criterion, cand[j] = key.  With the sphere bins (l >= Lb), only the
+// spheres listed for the cell's bin of level Lb are tested: a bin lists every sphere whose
+// centre is within (r + shell) + margin of it, a superset of those the pre-test can accept for
+// any cell inside it, so the result is the same as testing every sphere.
 __global__ void k_refine(const uint64_t* __restrict__ parent, int64_t ncand, int l, const ot_sphere* __restrict__ sph,
-                         int nsph, uint64_t* __restrict__ cand, uint32_t* __restrict__ flag) {
+                         int nsph, const int* __restrict__ bin_off, const int* __restrict__ bin_sph, int Lb,
+                         uint64_t* __restrict__ cand, uint32_t* __restrict__ flag) {
     const double h = ldexp(1.0, -l);
     const float hf = (float)h;
+    const bool binned = bin_off && l >= Lb;
     GRID_STRIDE(j, ncand) {
         uint64_t key = parent ? ((parent[j >> 3] << 3) | (uint64_t)(j & 7)) : (uint64_t)j;
         uint32_t i0, i1, i2;
@@ -83,9 +89,18 @@ __global__ void k_refine(const uint64_t* __restrict__ parent, int64_t ncand, int
         const double lo[3] = {__dmul_rn((double)i0, h), __dmul_rn((double)i1, h), __dmul_rn((double)i2, h)};
         const float lof[3] = {(float)lo[0], (float)lo[1], (float)lo[2]};
         uint32_t hit = 0;
-        for (int s = 0; s < nsph && !hit; ++s) {
-            const ot_sphere sp = sph[s];
-            if (maybe_near(lof, hf, sp) && box_near_surface(lo, h, sp)) hit = 1;
+        if (binned) {
+            const int sh = l - Lb, nb = 1 << Lb;
+            const int b = (int)(i0 >> sh) + nb * ((int)(i1 >> sh) + nb * (int)(i2 >> sh));
+            for (int k = bin_off[b]; k < bin_off[b + 1] && !hit; ++k) {
+                const ot_sphere sp = sph[bin_sph[k]];
+                if (maybe_near(lof, hf, sp) && box_near_surface(lo, h, sp)) hit = 1;
+            }
+        } else {
+            for (int s = 0; s < nsph && !hit; ++s) {
+                const ot_sphere sp = sph[s];
+                if (maybe_near(lof, hf, sp) && box_near_surface(lo, h, sp)) hit = 1;
+            }
         }
         cand[j] = key;
         flag[j] = hit;
@@ -222,6 +237,43 @@ ot_status build_tree(const ot_sphere* h_spheres, int nsph, const ot_build_params
         g.keep(d_sph);
         OT_CUDA(cudaMemcpyAsync(d_sph, h_spheres, sizeof(ot_sphere) * nsph, cudaMemcpyHostToDevice, s));
     }
+    // sphere bins: the cells of level Lb, each listing the spheres whose centre lies within
+    // (r + shell) (1 + 1e-4) + 1e-4 of the bin's box (bounding-box overlap; a superset)
+    const int Lb = std::min(lmin, 5);
+    int* d_bin_off = nullptr;
+    int* d_bin_sph = nullptr;
+    if (nsph > 0 && Lb >= 1) {
+        const int nb = 1 << Lb;
+        std::vector<std::vector<int>> bins((size_t)nb * nb * nb);
+        for (int k = 0; k < nsph; ++k) {
+            const ot_sphere& sp = h_spheres[k];
+            const double R = (sp.r + sp.shell) * 1.0001 + 1e-4;
+            int lo[3], hi[3];
+            const auto bin_of = [nb](double v) {  // clamped in FP64 before the conversion
+                return (int)std::floor(std::max(0.0, std::min((double)(nb - 1), v * nb)));
+            };
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = bin_of(sp.c[d] - R);
+                hi[d] = bin_of(sp.c[d] + R);
+            }
+            for (int z = lo[2]; z <= hi[2]; ++z)
+                for (int y = lo[1]; y <= hi[1]; ++y)
+                    for (int x = lo[0]; x <= hi[0]; ++x) bins[(size_t)x + nb * ((size_t)y + nb * (size_t)z)].push_back(k);
+        }
+        std::vector<int> off(bins.size() + 1, 0), idx;
+        for (size_t b = 0; b < bins.size(); ++b) {
+            off[b + 1] = off[b] + (int)bins[b].size();
+            idx.insert(idx.end(), bins[b].begin(), bins[b].end());
+        }
+        OT_CUDA(cudaMallocAsync(&d_bin_off, sizeof(int) * off.size(), s));
+        g.keep(d_bin_off);
+        OT_CUDA(cudaMallocAsync(&d_bin_sph, sizeof(int) * std::max<size_t>(idx.size(), 1), s));
+        g.keep(d_bin_sph);
+        OT_CUDA(cudaMemcpyAsync(d_bin_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s));
+        if (!idx.empty())
+            OT_CUDA(cudaMemcpyAsync(d_bin_sph, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
+        OT_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+    }
     const int L = lmax + 1;
     std::vector<uint64_t*> R(L, nullptr);
     std::vector<int64_t> nR(L, 0);
@@ -239,7 +291,8 @@ ot_status build_tree(const ot_sphere* h_spheres, int nsph, const ot_build_params
         g.keep(flag);
         if ((st = dalloc(&pos, ncand, s)) != OT_OK) return st;
         g.keep(pos);
-        k_refine<<<grid1d(ncand, 256), 256, 0, s>>>(l == lmin ? nullptr : R[l - 1], ncand, l, d_sph, nsph, cand, flag);
+        k_refine<<<grid1d(ncand, 256), 256, 0, s>>>(l == lmin ? nullptr : R[l - 1], ncand, l, d_sph, nsph, d_bin_off,
+                                                    d_bin_sph, Lb, cand, flag);
         count_launch();
         OT_CUDA(cudaGetLastError());
         uint64_t* out = nullptr;

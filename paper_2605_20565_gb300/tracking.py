@@ -10,8 +10,9 @@ Every step, through the C ABI:
      (``ot_spread``);
   4. the bubbles translate at constant velocities carrying their markers.
 Every ``rebuild_every`` steps the octree is rebuilt around the moved bubbles
-(``ot_octree_build``) with its level-mate table (``ot_octree_build_mates``), the learned index is retrained on the device (``ot_index_train``), the
-velocity field is re-sampled at the new leaf centres, the particles are re-stored in Morton
+(``ot_octree_build``) with its level-mate table (``ot_octree_build_mates``), the learned
+index is retrained on the device for the learned form (``ot_index_train``), the velocity
+field is re-sampled at the new leaf centres, the particles are re-stored in Morton
 order of their cells (``ot_points_morton_order``; ``ids`` keeps each one's original index),
 and the batch graph is re-captured: the single-GPU form of re-locating every point after a
 mesh change.
@@ -132,7 +133,8 @@ class Tracker:
         if self.sort_points:
             self._reorder()
             t = mark("reorder", t)
-        prev = ot.ot_index_get_root_params(self.tree) if getattr(self, "tree", None) is not None else None
+        prev = (ot.ot_index_get_root_params(self.tree)
+                if self.search == ot.OT_LEARNED and getattr(self, "tree", None) is not None else None)
         self.tree = ot.ot_octree_build(self.spheres_now(), w.lmin, w.lmax)
         if self.map_level is not None:
             ot.ot_octree_set_map_level(self.tree, self.map_level)
@@ -147,12 +149,14 @@ class Tracker:
                 self._mates_buf = T.empty(need + need // 10, dtype=T.uint8, device=self.dev)
             ot.ot_octree_build_mates_in(self.tree, self._mates_buf)
             t = mark("level_mate_table", t)
-        # the first index trains from the spline initialisation; later ones fine-tune the previous
-        # network (the bubbles moved by a few cells): a warm start with few steps
-        ot.ot_index_train(self.tree, root=ot.OT_ROOT_MLP, n_leaf_models=self.n_leaf_models,
-                          n_mid_models=self.n_mid_models, epochs=2, batch=65536, lr=1e-3, seed=self.step_no,
-                          steps=0 if prev is None else 64, init=prev)
-        t = mark("index_train", t)
+        # the learned form's index (the plain form needs none): the first trains from the spline
+        # initialisation; later ones fine-tune the previous network (the bubbles moved by a few
+        # cells): a warm start with few steps
+        if self.search == ot.OT_LEARNED:
+            ot.ot_index_train(self.tree, root=ot.OT_ROOT_MLP, n_leaf_models=self.n_leaf_models,
+                              n_mid_models=self.n_mid_models, epochs=2, batch=65536, lr=1e-3, seed=self.step_no,
+                              steps=0 if prev is None else 64, init=prev)
+            t = mark("index_train", t)
         n_leaves = ot.ot_octree_info(self.tree)[0]
         self.field = ot.ot_field_fourier(self.tree, w.modes.n, w.modes.amp, w.modes.phase)
         self.f = T.zeros((n_leaves, 4), dtype=T.float32, device=self.dev)
