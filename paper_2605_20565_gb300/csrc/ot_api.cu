@@ -291,7 +291,6 @@ ot_status ot_octree_destroy(ot_octree* t) {
     if (t->d_nodes) cudaFree(t->d_nodes);
     if (t->d_desc) cudaFree(t->d_desc);
     if (t->d_lmap_lv) cudaFree(t->d_lmap_lv);
-    if (t->d_mcell) cudaFree(t->d_mcell);
     if (t->d_mates && t->mates_owned) cudaFree(t->d_mates);
     if (t->d_models) cudaFree(t->d_models);
     if (t->d_mids) cudaFree(t->d_mids);

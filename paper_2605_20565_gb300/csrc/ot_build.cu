@@ -563,19 +563,6 @@ __global__ void k_lmap_lv(const uint32_t* __restrict__ lmap, const uint8_t* __re
     GRID_STRIDE(c, ncell) out[c] = level[lmap[c]];
 }
 
-__global__ void k_mcell(const uint32_t* __restrict__ lmap, const uint8_t* __restrict__ lmap_lv,
-                        const uint4* __restrict__ desc, int n, int64_t ncell, MapCell* __restrict__ out) {
-    GRID_STRIDE(c, ncell) {
-        MapCell m;
-        m.a = lmap[c];
-        m.e = c + 1 < ncell ? lmap[c + 1] : (uint32_t)n;
-        m.lv = lmap_lv[c];
-        m.pad = 0u;
-        m.desc = desc ? desc[c] : make_uint4(0u, 0u, 0u, 0u);
-        out[c] = m;
-    }
-}
-
 ot_status finish_tree(ot_octree* t, cudaStream_t s, int map_level) {
     // default: level 7, or 8 for trees deeper than 10 levels (the descriptors then reach lmax)
     const int L = map_level >= 0 ? std::min(map_level, t->lmax)
@@ -616,14 +603,6 @@ ot_status finish_tree(ot_octree* t, cudaStream_t s, int map_level) {
         k_desc<<<grid1d(ncell, 256), 256, 0, s>>>(t->d_key, t->d_level, (int)t->n, t->d_lmap, L, ncell, t->d_desc);
         count_launch();
     }
-    if (t->d_mcell) cudaFree(t->d_mcell);
-    t->d_mcell = nullptr;
-    {
-        const int64_t ncell = (int64_t)1 << (3 * L);
-        OT_CUDA(cudaMalloc(&t->d_mcell, sizeof(MapCell) * ncell));
-        k_mcell<<<grid1d(ncell, 256), 256, 0, s>>>(t->d_lmap, t->d_lmap_lv, t->d_desc, (int)t->n, ncell, t->d_mcell);
-        count_launch();
-    }
     if (!t->d_err) {
         OT_CUDA(cudaMalloc(&t->d_err, 64));
         OT_CUDA(cudaMemsetAsync(t->d_err, 0, 64, s));
@@ -645,7 +624,6 @@ TreeView tree_view(const ot_octree* t) {
     v.lmap_level = t->lmap_level;
     v.desc = t->d_desc;
     v.lmap_lv = t->d_lmap_lv;
-    v.mcell = t->d_mcell;
     v.pyr_level = t->pyr_level;
     v.periodic = t->periodic;
     v.mates = reinterpret_cast<const uint4*>(t->d_mates);

@@ -129,14 +129,6 @@ struct RootModel {
     float sa[MLP_H + 1], sb[MLP_H + 1];
 };
 
-// One level-map cell in one 32-byte sector: the leaf holding its anchor (a), the leaf holding
-// the next cell's anchor (e; n for the last cell), the level of leaf a, and the cell's subtree
-// descriptor (see desc_leaf; zero when not valid).
-struct __align__(32) MapCell {
-    uint32_t a, e, lv, pad;
-    uint4 desc;
-};
-
 struct TreeView {
     const uint64_t* __restrict__ key;
     const uint8_t* __restrict__ level;
@@ -150,7 +142,6 @@ struct TreeView {
     // desc_leaf); null when not built
     const uint4* __restrict__ desc;
     const uint8_t* __restrict__ lmap_lv;  // level of leaf lmap[c]
-    const MapCell* __restrict__ mcell;    // lmap, lmap_lv and desc of each cell, packed
     int pyr_level;  // deepest level of the pyramid of cell means (refined trilinear level-mates)
     int periodic;   // the unit cube is periodic: stencils and level-mates wrap around
     // level-mate table: for leaf h and octant o, the 8 value slots of its trilinear
@@ -187,20 +178,9 @@ __device__ __forceinline__ int search_range(const uint64_t* __restrict__ key, in
 // least 8 leaves, the first starting at its anchor.
 __device__ __forceinline__ void map_range(const TreeView& t, uint64_t q, int& a, int& e, bool& covered) {
     const uint32_t c = (uint32_t)(q >> (3 * (MAXLEVEL - t.lmap_level)));
-    const uint4 r = __ldg(reinterpret_cast<const uint4*>(t.mcell + c));
-    a = (int)r.x;
-    e = (int)r.y;
+    a = (int)t.lmap[c];
+    e = (c + 1 < (1u << (3 * t.lmap_level))) ? (int)t.lmap[c + 1] : t.n;
     covered = e - a <= 1;
-}
-
-// The packed level-map cell c (two 16-byte loads of one sector).
-__device__ __forceinline__ void load_cell(const TreeView& t, uint32_t c, int& a, int& e, int& lv, uint4& d) {
-    const uint4* p = reinterpret_cast<const uint4*>(t.mcell + c);
-    const uint4 r = __ldg(p);
-    d = __ldg(p + 1);
-    a = (int)r.x;
-    e = (int)r.y;
-    lv = (int)r.z;
 }
 
 // Plain host search (Algorithm 1's answer, upper bound - 1): the level map gives the leaf
@@ -235,13 +215,14 @@ __device__ __forceinline__ int desc_leaf(uint4 d, int L, uint64_t q, int a, int&
 }
 constexpr uint32_t DESC_VALID = 0x100u;
 
-// The cell's map entries and its descriptor come in one sector (one round trip).
+// The cell's map entries and its descriptor are loaded together (one round trip).
 __device__ __forceinline__ int search_plain(const TreeView& t, uint64_t q) {
     const uint32_t c = (uint32_t)(q >> (3 * (MAXLEVEL - t.lmap_level)));
-    int a, e, lv;
-    uint4 d;
-    load_cell(t, c, a, e, lv, d);
+    const int a = (int)t.lmap[c];
+    const int e = (c + 1 < (1u << (3 * t.lmap_level))) ? (int)t.lmap[c + 1] : t.n;
+    const uint4 d = t.desc ? __ldg(t.desc + c) : make_uint4(0u, 0u, 0u, 0u);
     if (e - a <= 1) return a;
+    int lv;
     if (d.z & DESC_VALID) return desc_leaf(d, t.lmap_level, q, a, lv);
     return search_range(t.key, a, e - a, q);
 }

@@ -21,7 +21,6 @@ struct ot_octree {
     uint4* d_desc = nullptr;  // subtree descriptor of every level-map cell
     int periodic = 0;         // stencils and level-mates wrap around the unit cube
     uint8_t* d_lmap_lv = nullptr;  // level of leaf lmap[c]
-    ot::MapCell* d_mcell = nullptr;  // the three, packed per cell
     // the same table at the pyramid level min(lmax, 7), fixed for the octree's life (it is
     // d_lmap when the two levels agree): leaf ranges of the cells of the pyramid of means
     uint32_t* d_pmap = nullptr;

@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(256, 4) k_mates(TreeView t, uint2* __restrict_
     const int sx = lane % 3, sy = 3 + (lane / 3) % 3, sz = 6 + (lane / 9) % 3;
     const bool is_mate = lane < 27 && lane != 13;
     const int Lsh = 3 * (MAXLEVEL - t.lmap_level);
+    const uint32_t nmap = 1u << (3 * t.lmap_level);
     // keys and levels of the warp's leaves, one lane each (then broadcast), loaded one
     // iteration ahead
     uint64_t kl = 0;
@@ -102,7 +103,10 @@ __global__ void __launch_bounds__(256, 4) k_mates(TreeView t, uint2* __restrict_
             nb[u] = is_mate && base + u < t.n && !(dx & dy & dz & SAME);
             q[u] = ((dx | dy | dz) & ~SAME) << sh3;  // the level-mate cell's anchor key
             const uint32_t c = nb[u] ? (uint32_t)(q[u] >> Lsh) : 0u;
-            load_cell(t, c, a[u], e[u], la[u], dsc[u]);
+            a[u] = (int)t.lmap[c];
+            e[u] = c + 1 < nmap ? (int)t.lmap[c + 1] : t.n;
+            la[u] = t.lmap_lv[c];
+            dsc[u] = t.desc ? __ldg(t.desc + c) : make_uint4(0u, 0u, 0u, 0u);
         }
         const int Lp = t.pyr_level;
 #pragma unroll

@@ -46,23 +46,15 @@ __device__ __forceinline__ void stage_root(const TreeView& t, RootModel& s_root)
 
 // Level-map lookup of key q: the leaf holding its cell's anchor (a) and the next cell's (e).
 // The cell is covered by one leaf -- leaf a, the answer -- exactly when e - a <= 1 (a refined
-// cell holds at least 8 leaves, its first one starting at its anchor).  With DESC (plain form
-// only) it also answers from the cell's subtree descriptor, which comes in the same sector.
-// Returns true with the answer in a and its level in lv, else false with the cell's leaf range
-// [a, e) to search (descriptor task, halving, or the learned models).
-// (The per-query level-mate search looks its 7 corners up without DESC: there, resolving the
-// descriptors inside the lookups measured slower than leaving them to the task list.)
-template <bool DESC>
+// cell holds at least 8 leaves, its first one starting at its anchor).  Returns true with the
+// answer in a when covered, else false with the cell's leaf range [a, e) to search.
+// lv: the level of leaf a (from the per-cell level table, in the same round trip).
 __device__ __forceinline__ bool map_lookup(const TreeView& t, uint64_t q, int& a, int& e, int& lv) {
     const uint32_t cell = (uint32_t)(q >> (3 * (MAXLEVEL - t.lmap_level)));
-    uint4 d;
-    load_cell(t, cell, a, e, lv, d);
-    if (e - a <= 1) return true;
-    if (DESC && (d.z & DESC_VALID)) {
-        a = desc_leaf(d, t.lmap_level, q, a, lv);
-        return true;
-    }
-    return false;
+    a = (int)t.lmap[cell];
+    e = cell < (1u << (3 * t.lmap_level)) - 1u ? (int)t.lmap[cell + 1] : t.n;
+    lv = t.lmap_lv[cell];
+    return e - a <= 1;
 }
 
 // Appends a task for every lane with need set (warp-wide call); returns the lane's task index
@@ -83,8 +75,8 @@ __device__ __forceinline__ int push_task(Q& w, int& n, bool need, uint64_t q, in
 // Runs the warp's ntask tasks (warp-wide call).  Each step, a lane without a task takes the
 // next one, and every lane with a task advances it by one step of at most one memory round
 // trip:
-//   plain:   with DESC_TASK, the cell's subtree descriptor first, which answers directly when
-//            the subtree is at most 3 levels deep; then halving probes over the cell's leaves;
+//   plain:   the cell's subtree descriptor, which answers directly when the subtree is at most
+//            3 levels deep; else halving probes over the cell's leaves;
 //   learned: route (root model from shared memory, then the middle model's load), leaf model
 //            load and window (its prediction widened by the stored error bounds, clamped to
 //            the cell), halving probes over the window, and the check key[a] <= q < key[a+1];
@@ -95,7 +87,7 @@ __device__ __forceinline__ int push_task(Q& w, int& n, bool need, uint64_t q, in
 // and registers.)
 enum { ST_ROUTE = 0, ST_MODEL = 1, ST_PROBE = 2, ST_CHECK = 3, ST_DONE = 4, ST_DESC = 5 };
 
-template <bool LEARNED, bool DESC_TASK, typename Q>
+template <bool LEARNED, typename Q>
 __device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& root, Q& w, int ntask,
                                           unsigned lt) {
     __syncwarp();
@@ -118,7 +110,7 @@ __device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& ro
                 q = w.q[idx];
                 lo = clo = w.lo[idx];
                 len = clen = w.len[idx];
-                st = LEARNED ? ST_ROUTE : (DESC_TASK ? ST_DESC : ST_PROBE);
+                st = LEARNED ? ST_ROUTE : (t.desc ? ST_DESC : ST_PROBE);
                 checked = false;
                 lvr = -1;
             }
@@ -126,8 +118,8 @@ __device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& ro
         next += __popc(m);
         if (!__any_sync(FULL, cur >= 0)) break;
         if (cur < 0) continue;
-        if (!LEARNED && DESC_TASK && st == ST_DESC) {
-            const uint4 d = __ldg(reinterpret_cast<const uint4*>(t.mcell + (q >> (3 * (MAXLEVEL - t.lmap_level)))) + 1);
+        if (!LEARNED && st == ST_DESC) {
+            const uint4 d = __ldg(t.desc + (q >> (3 * (MAXLEVEL - t.lmap_level))));
             if (d.z & DESC_VALID) {
                 lo = desc_leaf(d, t.lmap_level, q, lo, lvr);
                 st = ST_DONE;
@@ -184,19 +176,18 @@ __device__ __forceinline__ void run_tasks(const TreeView& t, const RootModel& ro
 // given (h < 0) (warp-wide call): the level-map lookup, then the warp's task list for the lanes
 // whose cell is not covered.  hl receives the leaf's level when the lookup or the descriptor
 // gave it, else stays -1.
-// DESC_LOOKUP (plain form): the descriptor answers in the lookup; otherwise in a task step.
-template <bool LEARNED, bool DESC_LOOKUP, typename Q>
+template <bool LEARNED, typename Q>
 __device__ __forceinline__ void host_queued(const TreeView& t, const RootModel& root, Q& w, bool ok,
                                             const uint64_t X[3], int& h, int& hl) {
     const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
     const uint64_t q = morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32));
     int ca = 0, ce = 0, clv = -1;
-    const bool need = ok && h < 0 && !map_lookup<!LEARNED && DESC_LOOKUP>(t, q, ca, ce, clv);
+    const bool need = ok && h < 0 && !map_lookup(t, q, ca, ce, clv);
     if (ok && h < 0 && !need) h = ca, hl = clv;
     if (__any_sync(FULL, need)) {
         int n = 0;
         const int ix = push_task(w, n, need, q, ca, ce - ca, lt);
-        run_tasks<LEARNED, !DESC_LOOKUP>(t, root, w, n, lt);
+        run_tasks<LEARNED>(t, root, w, n, lt);
         if (ix >= 0) h = w.lo[ix], hl = w.lv[ix];
         __syncwarp();
     }
@@ -224,7 +215,7 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
 
     // host (and its level, when the lookup gives it)
     int h = host_in, hl = -1;
-    host_queued<LEARNED, false>(t, root, w, ok, X, h, hl);
+    host_queued<LEARNED>(t, root, w, ok, X, h, hl);
     if (!ok) h = 0, hl = -1;  // keeps the lane's reads in bounds; its result is discarded
 
     const int l = hl >= 0 ? hl : (int)t.level[h];
@@ -300,7 +291,7 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
             if ((sib_m >> corner) & 1u) {
                 gk[corner] = ldg_key(t.key + gi[corner]);
             } else if ((pend_m >> corner) & 1u) {
-                if (map_lookup<false>(t, anc[corner], ca[corner], ce[corner], unused_lv)) {
+                if (map_lookup(t, anc[corner], ca[corner], ce[corner], unused_lv)) {
                     a[corner] = ca[corner];
                     pend_m &= ~(1u << corner);
                 }
@@ -309,7 +300,7 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
 #pragma unroll
         for (int corner = 1; corner < 8; ++corner) {
             if (!((sib_m >> corner) & 1u)) continue;
-            if (gk[corner] == anc[corner] || map_lookup<false>(t, anc[corner], ca[corner], ce[corner], unused_lv)) {
+            if (gk[corner] == anc[corner] || map_lookup(t, anc[corner], ca[corner], ce[corner], unused_lv)) {
                 a[corner] = gk[corner] == anc[corner] ? gi[corner] : ca[corner];
                 pend_m &= ~(1u << corner);
             }
@@ -321,7 +312,7 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
 #pragma unroll
         for (int corner = 1; corner < 8; ++corner)
             tix[corner] = push_task(w, n, (pend_m >> corner) & 1u, anc[corner], ca[corner], ce[corner] - ca[corner], lt);
-        run_tasks<LEARNED, true>(t, root, w, n, lt);
+        run_tasks<LEARNED>(t, root, w, n, lt);
 #pragma unroll
         for (int corner = 1; corner < 8; ++corner)
             if (tix[corner] >= 0) a[corner] = w.lo[tix[corner]];
@@ -376,7 +367,7 @@ __device__ __forceinline__ int trilinear_mates(const TreeView& t, const RootMode
     const bool ok = active && fixpoint3(x, y, z, X);
     if (active && !ok) atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
     int h = host_in, hl = -1;
-    host_queued<LEARNED, true>(t, root, w, ok, X, h, hl);
+    host_queued<LEARNED>(t, root, w, ok, X, h, hl);
     if (!ok) {
         out[0] = out[1] = out[2] = qnan<T>();
         return -1;
