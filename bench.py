@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--no-mdf", action="store_true", help="skip the multi-direct forcing measurement")
     p.add_argument("--markers-as-generated", action="store_true",
                    help="keep the markers in generation order (default: per bubble, Morton order)")
+    p.add_argument("--no-morton-form", action="store_true",
+                   help="skip the informative form with the particles stored in Morton order")
     p.add_argument("--no-mates", action="store_true",
                    help="search the trilinear level-mates per query instead of reading the level-mate table")
     return p.parse_args()
@@ -557,6 +559,25 @@ def run_ours(args):
             torch.cuda.synchronize()
             groups_t[f"{gname}_{name}_ms"] = a_.elapsed_time(b_) / 5
             del bb
+    # informative, not `value`: the plain step with the particles stored in Morton order of
+    # their level-8 cells (the order the tracking driver keeps them in; sorted once, untimed)
+    morton = None
+    if not args.no_morton_form and n_p > 0 and forms_cfg["plain"][3]:
+        set_form("plain")
+        perm = ot.ot_points_morton_order(px, py, pz).long()
+        sx, sy, sz = [a_.index_select(0, perm).contiguous() for a_ in (px, py, pz)]
+        del perm
+        up_m = torch.empty_like(up)  # its own outputs: `up` keeps the timed form's for the parity check
+        gs = [groups[0], dict(kernel=ot.OT_TRILINEAR, x=sx, y=sy, z=sz, u=up_m)]
+        lp_m = ot.ot_batch_autotune(tree, gs, field, search=ot.OT_BINARY, tune_map_level=False, reps=2)["launch"]
+        bb = ot.ot_batch_create(tree, gs, field, search=ot.OT_BINARY, launch=lp_m)
+        warm(bb)
+        morton = time_steps(bb, args.steps)
+        morton.update(points_per_s=npts / (morton["step_ms"] / 1e3),
+                      locate_interpolate_points_per_s=npts / (morton["locate_interpolate_ms"] / 1e3), launch=lp_m,
+                      map_level=forms_cfg["plain"][1], search="binary", level_mates="table",
+                      particle_order="Morton order of level-8 cells")
+        del bb, sx, sy, sz, gs, up_m
     for name, v_ in forms.items():
         v_["points_per_s"] = npts / (v_["step_ms"] / 1e3)
         v_["locate_interpolate_points_per_s"] = npts / (v_["locate_interpolate_ms"] / 1e3)
@@ -581,6 +602,8 @@ def run_ours(args):
             "step": forms["plain_nomap"]["step_ms"] / forms["learned_nomap"]["step_ms"]}
     if "plain_search" in forms:
         learned_vs_plain["table_vs_search_plain_step"] = forms["plain_search"]["step_ms"] / forms["plain"]["step_ms"]
+    if morton:
+        forms["plain_particles_morton"] = morton
     set_form(chosen)
 
     if rank != 0:
