@@ -292,6 +292,7 @@ ot_status ot_octree_destroy(ot_octree* t) {
     if (t->d_desc) cudaFree(t->d_desc);
     if (t->d_lmap_lv) cudaFree(t->d_lmap_lv);
     if (t->d_mates && t->mates_owned) cudaFree(t->d_mates);
+    if (t->d_need_flags) cudaFree(t->d_need_flags);
     if (t->d_models) cudaFree(t->d_models);
     if (t->d_mids) cudaFree(t->d_mids);
     if (t->d_root) cudaFree(t->d_root);

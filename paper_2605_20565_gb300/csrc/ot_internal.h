@@ -34,6 +34,10 @@ struct ot_octree {
     // library memory (mates_owned) or the caller's
     uint32_t* d_mates = nullptr;
     bool mates_owned = false;
+    // with the table: flags of the cell means it reads, closed under "a mean needs its
+    // children's", one byte per entry of the means array (null without the table: every mean
+    // is computed)
+    uint8_t* d_need_flags = nullptr;
     // learned index
     bool has_index = false;
     ot::RootModel root{};
@@ -121,6 +125,10 @@ int64_t pyramid_offset(int l);
 // entries (4 values each), indexed by the refined cell's first leaf.
 int node_levels(const ot_octree* t);
 ot_status build_node_lists(ot_octree* t, cudaStream_t s);
+// Flags of the means the level-mate table reads (need_flag_bytes(t) bytes, one per entry of
+// the means array, set by the table builder), closed under "a mean needs its children's".
+size_t need_flag_bytes(const ot_octree* t);
+ot_status close_need_flags(ot_octree* t, uint8_t* need, cudaStream_t s);
 size_t pyramid_bytes(const ot_octree* t, size_t elem);  // elem: sizeof the field type
 template <typename T> ot_status launch_pyramid(const ot_octree* t, const T* field, T* pyr, cudaStream_t s);
 

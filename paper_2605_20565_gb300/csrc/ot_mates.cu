@@ -37,7 +37,7 @@ namespace {
 constexpr int MATES_U = 3;
 constexpr uint64_t SAME = 1ULL << 63;
 
-__global__ void __launch_bounds__(256, 4) k_mates(TreeView t, uint2* __restrict__ out) {
+__global__ void __launch_bounds__(256, 4) k_mates(TreeView t, uint2* __restrict__ out, uint8_t* __restrict__ need) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(256, 4) k_mates(TreeView t, uint2* __restrict_
                     const long long ri = l <= Lp ? pyr_offset(l) + (long long)(q[u] >> (3 * (MAXLEVEL - l)))
                                                  : pyr_offset(Lp + 1) + (long long)(l - Lp - 1) * t.n + leaf;
                     slot = 0x80000000u | (uint32_t)ri;
+                need[ri] = 1;  // a mean the table reads
                 }
             }
             const uint32_t p0 = __shfl_sync(0xffffffffu, slot, src[0]);
@@ -202,7 +203,15 @@ ot_status build_mates(ot_octree* t, cudaStream_t s) {
     OT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mates, 256, 0));
     const int64_t warps = (t->n + MATES_U - 1) / MATES_U;
     const int64_t grid = std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * std::max(per_sm, 1));
-    k_mates<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(v, reinterpret_cast<uint2*>(t->d_mates));
+    // flags of the cell means the table reads (kept by the octree: later pyramids compute
+    // those only)
+    const size_t nbytes = std::max<size_t>(need_flag_bytes(t), 1);
+    if (t->d_need_flags) cudaFree(t->d_need_flags);
+    t->d_need_flags = nullptr;
+    uint8_t* need = nullptr;
+    OT_CUDA(cudaMalloc(&need, nbytes));
+    OT_CUDA(cudaMemsetAsync(need, 0, nbytes, s));
+    k_mates<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(v, reinterpret_cast<uint2*>(t->d_mates), need);
     count_launch();
     const int64_t nslots = (int64_t)pnbr_slots(t);
     if (nslots > 0) {
@@ -212,6 +221,13 @@ ot_status build_mates(ot_octree* t, cudaStream_t s) {
         k_pnbr<<<(unsigned)std::max<int64_t>(g2, 1), 256, 0, s>>>(v, nslots, pn);
         count_launch();
     }
+    OT_CUDA(cudaGetLastError());
+    const ot_status st = close_need_flags(t, need, s);
+    if (st != OT_OK) {
+        cudaFree(need);
+        return st;
+    }
+    t->d_need_flags = need;
     OT_CUDA(cudaGetLastError());
     return OT_OK;
 }
@@ -224,6 +240,8 @@ namespace {
 
 // Drops the octree's table (freed when the library owns it).
 void drop_mates(ot_octree* t) {
+    if (t->d_need_flags) cudaFree(t->d_need_flags);  // without the table every mean is computed again
+    t->d_need_flags = nullptr;
     if (t->d_mates && t->mates_owned) cudaFree(t->d_mates);
     t->d_mates = nullptr;
     t->mates_owned = false;

@@ -54,50 +54,114 @@ __device__ __forceinline__ void children_mean(const uint8_t* __restrict__ level,
 // Level Lc of the pyramid: cell c holds leaves [pmap[c], pmap[c+1]); one leaf covers it when
 // that range has at most one leaf.
 template <typename T>
-__global__ void __launch_bounds__(256) k_pyr_base(const uint32_t* __restrict__ pmap, const uint8_t* __restrict__ level,
-                                                  int n, int Lc, const T* __restrict__ field,
-                                                  const T* __restrict__ child, T* __restrict__ out) {
+__device__ __forceinline__ void base_mean(const uint32_t* __restrict__ pmap, const uint8_t* __restrict__ level, int n,
+                                          int Lc, const T* __restrict__ field, const T* __restrict__ child, int64_t c,
+                                          T* __restrict__ out) {
     using V = Vec4<T>;
     const int64_t ncell = (int64_t)1 << (3 * Lc);
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
-        const int a = (int)pmap[c];
-        const int e = c + 1 < ncell ? (int)pmap[c + 1] : n;
-        T* p = out + 4 * c;
-        if (e - a <= 1) {
-            const auto f = V::load(field, a);
-            p[0] = f.x, p[1] = f.y, p[2] = f.z, p[3] = T(0);
-        } else {
-            children_mean<T>(level, Lc, field, child, a, p);
-        }
+    const int a = (int)pmap[c];
+    const int e = c + 1 < ncell ? (int)pmap[c + 1] : n;
+    T* p = out + 4 * c;
+    if (e - a <= 1) {
+        const auto f = V::load(field, a);
+        p[0] = f.x, p[1] = f.y, p[2] = f.z, p[3] = T(0);
+    } else {
+        children_mean<T>(level, Lc, field, child, a, p);
     }
 }
 
-// Refined cells of level l listed in nodes[0, cnt): their means, at index first leaf.
+// need (nullable): only the cells flagged there
+template <typename T>
+__global__ void __launch_bounds__(256) k_pyr_base(const uint32_t* __restrict__ pmap, const uint8_t* __restrict__ level,
+                                                  int n, int Lc, const T* __restrict__ field,
+                                                  const T* __restrict__ child, T* __restrict__ out,
+                                                  const uint8_t* __restrict__ need) {
+    const int64_t ncell = (int64_t)1 << (3 * Lc);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x)
+        if (!need || need[c]) base_mean<T>(pmap, level, n, Lc, field, child, c, out);
+}
+
+// Refined cells of level l listed in nodes[0, cnt): their means, at index first leaf (need,
+// nullable: only the cells flagged there, by first leaf).
 template <typename T>
 __global__ void __launch_bounds__(256) k_node_means(const int* __restrict__ nodes, int64_t cnt,
                                                     const uint8_t* __restrict__ level, int l,
                                                     const T* __restrict__ field, const T* __restrict__ child,
-                                                    T* __restrict__ out) {
+                                                    T* __restrict__ out, const uint8_t* __restrict__ need) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
         const int a = nodes[i];
-        children_mean<T>(level, l, field, child, a, out + 4 * (int64_t)a);
+        if (!need || need[a]) children_mean<T>(level, l, field, child, a, out + 4 * (int64_t)a);
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_pyr_up(const T* __restrict__ fine, T* __restrict__ coarse, int64_t ncell) {
+__device__ __forceinline__ void up_mean(const T* __restrict__ fine, T* __restrict__ coarse, int64_t c) {
     using V = Vec4<T>;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
-        T s0 = T(0), s1 = T(0), s2 = T(0);
+    T s0 = T(0), s1 = T(0), s2 = T(0);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const auto f = V::load(fine, 8 * c + k);
-            s0 += f.x;
-            s1 += f.y;
-            s2 += f.z;
-        }
-        T* p = coarse + 4 * c;
-        p[0] = s0 * T(0.125), p[1] = s1 * T(0.125), p[2] = s2 * T(0.125), p[3] = T(0);
+    for (int k = 0; k < 8; ++k) {
+        const auto f = V::load(fine, 8 * c + k);
+        s0 += f.x;
+        s1 += f.y;
+        s2 += f.z;
+    }
+    T* p = coarse + 4 * c;
+    p[0] = s0 * T(0.125), p[1] = s1 * T(0.125), p[2] = s2 * T(0.125), p[3] = T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pyr_up(const T* __restrict__ fine, T* __restrict__ coarse, int64_t ncell,
+                                                const uint8_t* __restrict__ need) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x)
+        if (!need || need[c]) up_mean<T>(fine, coarse, c);
+}
+
+// ---- the cell means the level-mate table reads, closed under "a mean needs its children's" ----
+
+// needed dense cell c of level l -> its 8 children of level l + 1
+__global__ void k_close_dense(const uint8_t* __restrict__ need, int64_t ncell, uint8_t* __restrict__ child_need) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x)
+        if (need[c])
+#pragma unroll
+            for (int k = 0; k < 8; ++k) child_need[8 * c + k] = 1;
+}
+
+// The refined children of a refined cell of level l whose first leaf is a (anchor key[a]): each
+// child's first leaf is the leaf holding its anchor, searched within the cell's leaves from a.
+__device__ __forceinline__ void mark_refined_children(const uint64_t* __restrict__ key,
+                                                      const uint8_t* __restrict__ level, int n, int l, int a,
+                                                      int e, uint8_t* __restrict__ child_need) {
+    const uint64_t anchor = key[a] & ~(key_span(l) - 1);
+    for (int k = 0; k < 8; ++k) {
+        const uint64_t ca = anchor + (uint64_t)k * key_span(l + 1);
+        const int f = search_range(key, a, e - a, ca);
+        if ((int)level[f] > l + 1) child_need[f] = 1;
+    }
+}
+
+// needed base cells (level Lc) that are refined -> their refined children (node level 0)
+__global__ void k_close_base(const uint8_t* __restrict__ need, const uint32_t* __restrict__ pmap,
+                             const uint64_t* __restrict__ key, const uint8_t* __restrict__ level, int n, int Lc,
+                             uint8_t* __restrict__ child_need) {
+    const int64_t ncell = (int64_t)1 << (3 * Lc);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+        if (!need[c]) continue;
+        const int a = (int)pmap[c];
+        const int e = c + 1 < ncell ? (int)pmap[c + 1] : n;
+        if (e - a > 1) mark_refined_children(key, level, n, Lc, a, e, child_need);
+    }
+}
+
+// needed refined cells of level l (by first leaf) -> their refined children (level l + 1)
+__global__ void k_close_node(const uint8_t* __restrict__ need, const uint64_t* __restrict__ key,
+                             const uint8_t* __restrict__ level, int n, int l, uint8_t* __restrict__ child_need) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n; a += (int64_t)gridDim.x * blockDim.x) {
+        if (!need[a]) continue;
+        // the cell's leaves end where the next cell of level l begins (at most 8^(lmax - l) leaves;
+        // the search range is capped at the leaf count)
+        const uint64_t next = (key[a] & ~(key_span(l) - 1)) + key_span(l);
+        const int e = next == 0 ? n : search_range(key, (int)a, n - (int)a, next - 1) + 1;
+        mark_refined_children(key, level, n, l, (int)a, e, child_need);
     }
 }
 
@@ -172,28 +236,66 @@ ot_status build_node_lists(ot_octree* t, cudaStream_t s) {
     return OT_OK;
 }
 
+size_t need_flag_bytes(const ot_octree* t) {
+    return (size_t)pyramid_offset(t->pyr_level + 1) + (size_t)node_levels(t) * (size_t)t->n;
+}
+
+// Closes the flags of the means the level-mate table reads (need: one byte per entry of the
+// means array, dense pyramid then node levels, set by the table builder) under "a mean needs
+// its children's"; the octree keeps them, and every later pyramid computes the flagged means
+// only.
+ot_status close_need_flags(ot_octree* t, uint8_t* need, cudaStream_t s) {
+    const int Lc = t->pyr_level;
+    const int nl = node_levels(t);
+    const int n = (int)t->n;
+    for (int l = 0; l < Lc; ++l) {
+        const int64_t nc = (int64_t)1 << (3 * l);
+        k_close_dense<<<grid_n(nc, 256), 256, 0, s>>>(need + pyramid_offset(l), nc, need + pyramid_offset(l + 1));
+        count_launch();
+    }
+    uint8_t* node_need = need + pyramid_offset(Lc + 1);
+    if (nl > 0) {
+        const int64_t nc = (int64_t)1 << (3 * Lc);
+        k_close_base<<<grid_n(nc, 256), 256, 0, s>>>(need + pyramid_offset(Lc), t->d_pmap, t->d_key, t->d_level, n, Lc,
+                                                     node_need);
+        count_launch();
+    }
+    for (int k = 0; k + 1 < nl; ++k) {
+        k_close_node<<<grid_n(n, 256), 256, 0, s>>>(node_need + (int64_t)k * n, t->d_key, t->d_level, n, Lc + 1 + k,
+                                                     node_need + (int64_t)(k + 1) * n);
+        count_launch();
+    }
+    OT_CUDA(cudaGetLastError());
+    return OT_OK;
+}
+
 template <typename T>
 ot_status launch_pyramid(const ot_octree* t, const T* field, T* pyr, cudaStream_t s) {
     const int Lc = t->pyr_level;
     const int nl = node_levels(t);
     T* nodes = pyr + 4 * pyramid_offset(Lc + 1);
+    // with the level-mate table, only the means it reads and the ones they are made of
+    const uint8_t* need = t->d_need_flags;
     // node means, deepest level first (each reads the next level's)
     for (int k = nl - 1; k >= 0; --k) {
         T* out = nodes + 4 * (int64_t)k * t->n;
         const T* child = k + 1 < nl ? out + 4 * (int64_t)t->n : nullptr;
         if (t->node_cnt[k] > 0) {
+            const uint8_t* nk = need ? need + pyramid_offset(Lc + 1) + (int64_t)k * t->n : nullptr;
             k_node_means<T><<<grid_n(t->node_cnt[k], 256), 256, 0, s>>>(t->d_nodes + t->node_off[k], t->node_cnt[k],
-                                                                       t->d_level, Lc + 1 + k, field, child, out);
+                                                                       t->d_level, Lc + 1 + k, field, child, out, nk);
             count_launch();
         }
     }
     const int64_t ncell = (int64_t)1 << (3 * Lc);
     k_pyr_base<T><<<grid_n(ncell, 256), 256, 0, s>>>(t->d_pmap, t->d_level, (int)t->n, Lc, field,
-                                                    nl > 0 ? nodes : nullptr, pyr + 4 * pyramid_offset(Lc));
+                                                    nl > 0 ? nodes : nullptr, pyr + 4 * pyramid_offset(Lc),
+                                                    need ? need + pyramid_offset(Lc) : nullptr);
     count_launch();
     for (int l = Lc - 1; l >= 0; --l) {
         const int64_t nc = (int64_t)1 << (3 * l);
-        k_pyr_up<T><<<grid_n(nc, 256), 256, 0, s>>>(pyr + 4 * pyramid_offset(l + 1), pyr + 4 * pyramid_offset(l), nc);
+        k_pyr_up<T><<<grid_n(nc, 256), 256, 0, s>>>(pyr + 4 * pyramid_offset(l + 1), pyr + 4 * pyramid_offset(l), nc,
+                                                    need ? need + pyramid_offset(l) : nullptr);
         count_launch();
     }
     OT_CUDA(cudaGetLastError());
