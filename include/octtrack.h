@@ -139,14 +139,21 @@ ot_status ot_octree_set_periodic(ot_octree* t, int periodic);
  * covers it) or its cell-mean entry when it is refined.  With the table built, trilinear
  * interpolation (ot_interpolate and batches created afterwards) finds its host leaf and reads
  * one 32-byte row instead of searching for the 7 level-mates; the results are bit-identical.
- * enable = 1 builds (or rebuilds) it: 256 bytes of device memory per leaf, OT_ERR_LIMIT when
- * the leaf count or the cell-mean count reaches 2^31, OT_ERR_OOM when the memory is not there
- * (the octree is then left without a table).  enable = 0 frees it.  Batches made while a table
- * existed hold its pointer: recreate them after rebuilding or freeing it.  The octree's
+ * Built with it: the parent-block table of the delta kernels (Sec. 2.2 stencils on the finest
+ * level; for every block of 8 finest leaves, the first leaves of the 27 blocks around it), with
+ * which a marker's stencil takes one lookup instead of one per block, and the flags of the
+ * cell means the level-mate table reads, so that the cell means recomputed for trilinear
+ * interpolation are those only.  Both leave every result unchanged bit for bit.
+ * enable = 1 builds (or rebuilds) them: 272 bytes of device memory per leaf plus one byte per
+ * cell-mean entry; OT_ERR_LIMIT when the leaf count or the cell-mean count reaches 2^31,
+ * OT_ERR_OOM when the memory is not there (the octree is then left without a table).
+ * enable = 0 frees them.  Batches made while a table existed hold its pointer: recreate them
+ * after rebuilding or freeing it.  The octree's
  * periodic setting is part of the table: ot_octree_set_periodic rebuilds it (on the legacy
  * default stream).  Synchronises the stream. */
 ot_status ot_octree_build_mates(ot_octree* t, int enable, void* stream);
-/* *bytes = the table's size, 256 bytes per leaf. */
+/* *bytes = the tables' size: 256 bytes per leaf (level-mate rows) + 128 bytes per 8 leaves
+ * (parent-block rows). */
 ot_status ot_octree_mates_bytes(const ot_octree* t, size_t* bytes);
 /* Builds the table in caller memory (d_buffer: 16-byte aligned, at least ot_octree_mates_bytes
  * bytes; the caller keeps ownership and must keep it allocated and untouched while the octree

@@ -1,11 +1,13 @@
-// ot_batch.cu -- one persistent launch over every group of points (IBM markers with a delta
+// ot_batch.cu -- persistent launches over every group of points (IBM markers with a delta
 // kernel, point particles with trilinear interpolation), replayed from a CUDA graph.
 //
 // A graph replay first recomputes the pyramid of cell means of the field (refined trilinear
-// level-mates read it; a few small launches), then runs the batch kernel.  Work is cut into tiles of 32 * tile points; warps take tiles from a global counter, the
-// expensive marker groups first (their tiles come first in the tile space), so uneven groups
-// balance across the SMs without a host round trip.  The counter is reset by a memset node
-// captured in the same graph.
+// level-mates read it; a few small launches), then runs the batch kernel: one launch over all
+// groups, or, with the octree's level-mate table, a launch for the delta-kernel groups and
+// one for the trilinear groups, each at its own occupancy.  Work is cut into tiles of
+// 32 * tile points; warps take tiles from a global counter, the expensive marker groups first
+// (their tiles come first in the tile space), so uneven groups balance across the SMs without
+// a host round trip.  The counters are reset by a memset node captured in the same graph.
 #include <algorithm>
 #include <type_traits>
 #include <vector>
