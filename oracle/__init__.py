@@ -54,7 +54,6 @@ def _L():
                 "or_free": (None, [P]),
                 "or_count_unbalanced": (i64, [P, P, i64, i32]),
                 "or_leaf_centres": (None, [P, P, i64, P]),
-                "or_locate_alg1": (None, [P, P, i64, i32, i32, P, P, P, i64, P]),
                 "or_locate_ub": (None, [P, P, i64, P, P, P, i64, P]),
                 "or_locate_brute": (None, [P, P, i64, P, P, P, i64, P]),
                 "or_phi_peskin4": (dbl, [dbl]),
@@ -137,14 +136,6 @@ def leaf_centres(keys, levels) -> np.ndarray:
 
 def _pts(x, y, z):
     return _c(x, np.float64), _c(y, np.float64), _c(z, np.float64)
-
-
-def locate_alg1(keys, levels, lmin, lmax, x, y, z) -> np.ndarray:
-    k, l = _c(keys, np.uint64), _c(levels, np.uint8)
-    x, y, z = _pts(x, y, z)
-    out = np.empty(x.size, np.int32)
-    _L().or_locate_alg1(_p(k), _p(l), k.size, lmin, lmax, _p(x), _p(y), _p(z), x.size, _p(out))
-    return out
 
 
 def locate_ub(keys, levels, x, y, z) -> np.ndarray:

@@ -21,7 +21,8 @@
  * Parity status:
  *   or_morton, or_unmorton ............ pinned (closed-form keys, round trip)
  *   or_octree_build ................... pinned (independent dense builder, partition, balance)
- *   or_locate_alg1 / ub / brute ....... pinned (mutual agreement, brute force on tiny trees)
+ *   or_locate_ub / brute .............. pinned (agreement with each other and with a dense-grid
+ *                                       painting of the leaves; faces, corners, NaN)
  *   or_phi_peskin4, or_phi_roma3 ...... pinned (closed-form values, moment conditions)
  *   or_interp_delta, or_spread_delta .. pinned (linear exactness, adjoint identity, conservation)
  *   or_interp_trilinear ............... pinned for same-level and refined level-mates (linear
@@ -29,7 +30,9 @@
  *                                       parity unpinned for hanging (coarser) and out-of-domain
  *                                       level-mates beyond constant-field reproduction
  *   or_mlp_loss_grad .................. pinned (central finite differences)
- *   or_advect_ab2 ..................... pinned (closed-form relaxation of a constant field)
+ *   or_advect_ab2 ..................... pinned (closed-form relaxation of a constant field;
+ *                                       periodic wrap: exact crossings of each face, the
+ *                                       x >= 1 fix-up, state other than x unchanged)
  *   periodic variants (_p) ............ pinned (uniform periodic trees against independent
  *                                       numpy sums over wrapped indices and scipy trilinear on
  *                                       a wrap-padded grid; spread conservation at the walls)
@@ -339,38 +342,10 @@ static int point_coords(double x, double y, double z, uint32_t q[3]) {
     return 1;
 }
 
-/* Algorithm 1 written out: for each level from lmin to lmax build the test cell whose
- * anchor is floor(x 2^level) 2^(MAXLEVEL-level) per axis, binary-search the Z-ordered leaf
- * array for a leaf equal to it (same anchor and same level), and stop at the first hit.
- * The tree loop of Algorithm 1 collapses: there is one tree (the unit cube).
- * Points outside [0,1)^3 (or NaN) get -1. */
-void or_locate_alg1(const uint64_t *key, const uint8_t *level, int64_t n, int lmin, int lmax, const double *x,
-                    const double *y, const double *z, int64_t np, int32_t *host) {
-#pragma omp parallel for schedule(static)
-    for (int64_t p = 0; p < np; ++p) {
-        int32_t found = -1;
-        double pt[3] = {x[p], y[p], z[p]};
-        int inside = 1;
-        for (int d = 0; d < 3; ++d)
-            if (!(pt[d] >= 0.0 && pt[d] < 1.0)) inside = 0;
-        if (inside) {
-            for (int l = lmin; l <= lmax; ++l) {
-                uint32_t a[3];
-                for (int d = 0; d < 3; ++d)
-                    a[d] = (uint32_t)floor(pt[d] * ldexp(1.0, l)) * cell_len(l);
-                uint64_t tk = or_morton(a[0], a[1], a[2]);
-                int64_t idx = lower_bound(key, n, tk);
-                if (idx < n && key[idx] == tk && level[idx] == l) {
-                    found = (int32_t)idx;
-                    break;
-                }
-            }
-        }
-        host[p] = found;
-    }
-}
-
-/* The same answer as one search: the last leaf whose anchor key is <= the point's key. */
+/* Host of a point: the leaf whose half-open box holds it (Sec. 3.2, the host cell that
+ * Algorithm 1 identifies).  Leaves tile the cube and the MAXLEVEL descendants of a level-l leaf
+ * are the contiguous keys [anchor, anchor + 8^(21-l)), so that leaf is the last one whose
+ * anchor key is <= the key of the point's MAXLEVEL cell. */
 void or_locate_ub(const uint64_t *key, const uint8_t *level, int64_t n, const double *x, const double *y,
                   const double *z, int64_t np, int32_t *host) {
     (void)level;

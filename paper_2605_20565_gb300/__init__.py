@@ -488,7 +488,7 @@ def ot_octree_build_mates_in(tree: Octree, buffer, stream=None):
     torch = _torch()
     if not (isinstance(buffer, torch.Tensor) and buffer.is_cuda and buffer.dtype == torch.uint8
             and buffer.is_contiguous()):
-        raise OtError("buffer must be a contiguous CUDA uint8 tensor")
+        raise OtError(-1, "buffer must be a contiguous CUDA uint8 tensor")
     _check(_L().ot_octree_build_mates_in(tree.handle, C.c_void_p(buffer.data_ptr()), buffer.numel(),
                                          _stream(stream)))
     tree.keep_mates = buffer

@@ -1,8 +1,11 @@
 """Seeded synthetic inputs shaped like the paper's workloads.
 
 This module is the only code that both the CUDA path and the CPU oracle are fed from.  It
-holds no arithmetic of the method itself (no Morton keys, no search, no delta kernels): it
-draws sphere lists, marker and particle positions, forces and velocity fields, nothing else.
+holds no arithmetic of the method itself (no search, no interpolation, no delta kernels, no
+spreading): it draws sphere lists, marker and particle positions, forces and velocity fields.
+One helper, marker_morton_order, computes level-10 Morton keys of the markers, but only to
+choose the order in which the markers are stored; that permutation is applied to the input
+arrays before either side sees them, so both sides receive the same reordered inputs.
 
 Random numbers come from SplitMix64 (Steele, Lea & Flood, OOPSLA 2014), used as a
 counter-based generator: value i of stream s under seed S is splitmix64_mix(base(S, s) +

@@ -192,8 +192,7 @@ def test_locate_special_points(ot, tiny, torch_mod):
     w, ko, lo, tree = tiny
     P = special_points(ko, lo, np.random.default_rng(5), 3000)
     ref = oracle.locate_ub(ko, lo, *P.T)
-    ref_alg1 = oracle.locate_alg1(ko, lo, w.lmin, w.lmax, *P.T)
-    assert np.array_equal(ref, ref_alg1)
+    assert np.array_equal(ref, oracle.locate_brute(ko, lo, *P.T))
     miss = torch.zeros(1, dtype=torch.int64, device="cuda")
     h = ot.ot_locate(tree, *pts(P.T), n_miss=miss)
     assert np.array_equal(h.cpu().numpy(), ref)

@@ -203,13 +203,42 @@ def test_count_unbalanced_detects_violation():
 # Host-cell search (Algorithm 1)
 # ---------------------------------------------------------------------------------------
 
+def _unmorton_np(keys):
+    """Integer anchor coordinates of Morton keys (bit loop in numpy, independent of the oracle)."""
+    k = np.asarray(keys, np.uint64)
+    out = np.zeros((k.size, 3), np.int64)
+    for b in range(21):
+        for d in range(3):
+            out[:, d] |= ((k >> np.uint64(3 * b + d)) & np.uint64(1)).astype(np.int64) << b
+    return out
+
+
+def paint_host_grid(keys, levels, lmax):
+    """Dense (2^lmax)^3 grid holding, in every finest cell, the index of the leaf whose box
+    covers it: each leaf paints its own block.  Every cell must be painted exactly once."""
+    n = 1 << lmax
+    grid = np.full((n, n, n), -1, np.int64)
+    cnt = np.zeros((n, n, n), np.int64)
+    anc = _unmorton_np(keys) >> (21 - lmax)
+    for i, (a, lv) in enumerate(zip(anc, levels)):
+        b = 1 << (lmax - int(lv))
+        grid[a[0]:a[0] + b, a[1]:a[1] + b, a[2]:a[2] + b] = i
+        cnt[a[0]:a[0] + b, a[1]:a[1] + b, a[2]:a[2] + b] += 1
+    assert (cnt == 1).all()
+    return grid
+
+
 def test_locate_three_ways(tiny_tree, tiny_workload):
+    """The key-order search, the leaf-by-leaf box scan and a lookup in a dense painting of the
+    leaves agree on every point (the host is the unique leaf whose half-open box holds it)."""
     k, l = tiny_tree
     w = tiny_workload
     x, y, z = w.particles
-    a = oracle.locate_alg1(k, l, w.lmin, w.lmax, x, y, z)
     b = oracle.locate_ub(k, l, x, y, z)
     c = oracle.locate_brute(k, l, x, y, z)
+    grid = paint_host_grid(k, l, w.lmax)
+    cell = np.floor(np.stack([x, y, z]) * (1 << w.lmax)).astype(np.int64)
+    a = grid[cell[0], cell[1], cell[2]]
     assert np.array_equal(a, c) and np.array_equal(b, c)
     assert (c >= 0).all()
     # each point inside exactly one leaf: the containing box test counts 1
@@ -229,14 +258,12 @@ def test_locate_faces_and_outside(tiny_tree, tiny_workload):
     h = 2.0 ** -l.astype(np.float64)
     lo = cen - 0.5 * h[:, None]  # anchors: points on three faces at once
     x, y, z = lo.T
-    for fn in (lambda: oracle.locate_alg1(k, l, w.lmin, w.lmax, x, y, z),
-               lambda: oracle.locate_ub(k, l, x, y, z),
+    for fn in (lambda: oracle.locate_ub(k, l, x, y, z),
                lambda: oracle.locate_brute(k, l, x, y, z)):
         assert np.array_equal(fn(), np.arange(k.size, dtype=np.int32))
     bad = np.array([1.0, -1e-300, np.nan, 2.0, 0.5, 0.5])
     ok = np.array([0.5, 0.5, 0.5, 0.5, np.nextafter(1.0, 0.0), -0.0])
-    for fn in (lambda a, b: oracle.locate_alg1(k, l, w.lmin, w.lmax, a, b, b),
-               lambda a, b: oracle.locate_ub(k, l, a, b, b),
+    for fn in (lambda a, b: oracle.locate_ub(k, l, a, b, b),
                lambda a, b: oracle.locate_brute(k, l, a, b, b)):
         r = fn(bad, ok)
         assert list(r[:4]) == [-1, -1, -1, -1]
@@ -693,3 +720,66 @@ def test_ab2_schiller_naumann_factor():
     oracle.advect_ab2(st, u, 1.0, 3.0, 0.1, True)
     fp = 1 + 0.15 * (3.0 * 2.0) ** 0.687
     assert abs(st["v"][0, 0] - 0.1 * fp * 2.0) < 1e-14
+
+
+def _state(x, v):
+    x = np.array(x, np.float64).reshape(3, -1).copy()
+    v = np.array(v, np.float64).reshape(3, -1).copy()
+    return {"x": x, "v": v, "a_prev": np.zeros_like(x), "v_prev": np.zeros_like(x)}
+
+
+def test_ab2_periodic_crossings_exact():
+    """Periodic box (Sec. 5.2): a particle leaving through one face re-enters through the
+    opposite one.  Values chosen so that every sum is exact in binary: an Euler step with the
+    fluid moving with the particle (no drag) moves x by dt v exactly."""
+    # per column: start, velocity, wrapped result (dt = 1)
+    cases = [(0.75, 0.5, 0.25),          # crosses x = 1 upwards
+             (0.25, -0.5, 0.75),         # crosses x = 0 downwards
+             (0.5, 0.5, 0.0),            # lands exactly on x = 1: the image is 0
+             (0.0, -0.25, 0.75),         # leaves from the face x = 0
+             (1.0 - 2.0 ** -10, 2.0 ** -9, 2.0 ** -10),
+             (0.375, 0.125, 0.5)]        # stays inside: untouched
+    x0 = np.array([c[0] for c in cases])
+    v0 = np.array([c[1] for c in cases])
+    ref = np.array([c[2] for c in cases])
+    for axis in range(3):
+        x = np.full((3, len(cases)), 0.5)
+        v = np.zeros((3, len(cases)))
+        x[axis], v[axis] = x0, v0
+        st = _state(x, v)
+        oracle.advect_ab2(st, st["v"].copy(), 1.0, 0.0, 1.0, True, periodic=True)
+        assert np.array_equal(st["x"][axis], ref)
+        others = [d for d in range(3) if d != axis]
+        assert np.array_equal(st["x"][others], np.full((2, len(cases)), 0.5))
+        assert np.array_equal(st["v"], v)  # the wrap moves positions only
+
+
+def test_ab2_periodic_rounds_to_zero_not_one():
+    """x just below 0 by less than half an ulp of 1 has the image 1 - 2^-60, which rounds to
+    1.0 in FP64; the wrapped position must still lie in [0, 1): it becomes 0."""
+    st = _state([[0.0], [0.5], [0.5]], [[-2.0 ** -60], [0.0], [0.0]])
+    oracle.advect_ab2(st, st["v"].copy(), 1.0, 0.0, 1.0, True, periodic=True)
+    assert st["x"][0, 0] == 0.0
+
+
+def test_ab2_periodic_differs_from_free_by_whole_turns():
+    """On random states with drag, the periodic step gives the free step's positions shifted by
+    whole turns into [0, 1), and identical velocities and histories."""
+    rng = np.random.default_rng(7)
+    n = 4000
+    x = rng.uniform(0.0, 1.0, (3, n))
+    v = rng.normal(0.0, 0.3, (3, n))
+    u = rng.normal(0.0, 0.3, (3, n))
+    free, per = _state(x, v), _state(x, v)
+    for s in range(3):
+        oracle.advect_ab2(free, u, 0.7, 2.0, 0.05, s == 0)
+        oracle.advect_ab2(per, u, 0.7, 2.0, 0.05, s == 0, periodic=True)
+        # the periodic run restarts from its own (wrapped) positions: compare one step at a time
+        for key in ("v", "a_prev", "v_prev"):
+            assert np.array_equal(free[key], per[key])
+        assert ((per["x"] >= 0.0) & (per["x"] < 1.0)).all()
+        turns = free["x"] - per["x"]
+        assert np.allclose(turns, np.round(turns), rtol=0, atol=4e-16)
+        crossed = np.round(turns) != 0
+        assert crossed.any()
+        free["x"] = per["x"].copy()
