@@ -238,7 +238,7 @@ ot_status ot_locate(const ot_octree* t, const double* d_x, const double* d_y, co
  *     c + {0, s_d} per axis where s_d = sign of the offset from the host centre; a
  *     level-mate inside a coarser leaf takes that leaf's value, a refined one the
  *     volume-weighted mean of its leaves, one outside the cube the host's index on that axis.
- *     The refined means are rebuilt by each call from the field, in stream-ordered scratch:
+ *     The refined means are rebuilt by each call from the field, in the caller's workspace:
  *     a dense pyramid of cell means over levels 0 .. L = min(lmax, 7) (16 * (8^(L+1) - 1) / 7
  *     bytes in FP32, 38 MB at L = 7) and, for levels L+1 .. lmax-1, one array of N means per
  *     level indexed by the refined cell's first leaf (16 N bytes per level in FP32).
@@ -248,17 +248,27 @@ ot_status ot_locate(const ot_octree* t, const double* d_x, const double* d_y, co
  *     dropped and flagged (OT_DEV_STENCIL).
  * d_u: 3 planes of n floats.  d_host_in: host leaves from ot_locate, or NULL to locate
  * here (search selects how); d_host_out (nullable) receives them.  For the delta kernels the
- * host is the finest cell holding X when that cell is a leaf, else a plain search result. */
+ * host is the finest cell holding X when that cell is a leaf, else a plain search result.
+ * d_workspace: ot_interpolate_workspace_size bytes, 16-byte aligned (OT_ERR_ARG when short);
+ * the delta kernels need none (NULL, 0).  Nothing is allocated: every temporary lives there. */
 ot_status ot_interpolate(const ot_octree* t, int kernel, const double* d_x, const double* d_y, const double* d_z,
                          int64_t n, const int32_t* d_host_in, int search, const float* d_field, float* d_u,
-                         int32_t* d_host_out, void* stream);
+                         int32_t* d_host_out, void* d_workspace, size_t ws_bytes, void* stream);
 
 /* FP64 variant: d_field is N x 4 doubles, d_u 3 planes of n doubles; weights in FP64. */
 ot_status ot_interpolate_f64(const ot_octree* t, int kernel, const double* d_x, const double* d_y,
                              const double* d_z, int64_t n, const int32_t* d_host_in, int search,
-                             const double* d_field, double* d_u, int32_t* d_host_out, void* stream);
+                             const double* d_field, double* d_u, int32_t* d_host_out, void* d_workspace,
+                             size_t ws_bytes, void* stream);
 
-/* Workspace for OT_SORTED spreading of n markers with the given kernel. */
+/* *bytes = the workspace of ot_interpolate (fp64 = 0) or ot_interpolate_f64 (fp64 = 1) with
+ * the given kernel on this octree: the cell means for OT_TRILINEAR, 0 for the delta kernels.
+ * It does not depend on the point count. */
+ot_status ot_interpolate_workspace_size(const ot_octree* t, int kernel, int fp64, size_t* bytes);
+
+/* Workspace for OT_SORTED spreading of n markers with the given kernel: every temporary of
+ * the sorted spreading (pairs, sort buffers, histograms, scan totals, marker records), so that
+ * ot_spread allocates nothing. */
 ot_status ot_spread_workspace_size(const ot_octree* t, int kernel, int64_t n, size_t* bytes);
 
 /* Force spreading, the exact adjoint of the delta-kernel interpolation (Sec. 2.2, Eq. for
@@ -268,7 +278,8 @@ ot_status ot_spread_workspace_size(const ot_octree* t, int kernel, int64_t n, si
  *   OT_SORTED: one pair per (marker, overlapping 2x2x2 block of finest cells) is radix-sorted
  *     by block (stable); each block sums its 8 cells' contributions in marker order:
  *     bit-identical run to run and for any launch shape.
- *     Needs d_workspace of ot_spread_workspace_size bytes (16-byte aligned).
+ *     Needs d_workspace of ot_spread_workspace_size bytes (16-byte aligned); nothing is
+ *     allocated.
  *   OT_ATOMIC: float atomics; order varies run to run.  d_workspace may be NULL. */
 ot_status ot_spread(const ot_octree* t, int kernel, int mode, const double* d_x, const double* d_y,
                     const double* d_z, const float* d_F, const float* d_dV, int64_t n, float* d_f,
@@ -291,7 +302,9 @@ ot_status ot_spread_f64(const ot_octree* t, int kernel, int mode, const double* 
  * holds about 459 bytes per marker for OT_PESKIN4 (at most 146,202 markers) and 136 bytes per
  * marker for OT_ROMA3 (at most 493,432); larger n returns OT_ERR_LIMIT and launches nothing.
  * The first call on a device (with that device current) looks up the scratch address; make
- * that first call before any stream capture.  All calls share the one array: calls whose
+ * that first call before any stream capture.  The address is looked up again when the device's
+ * context changed (after cudaDeviceReset, say): make the first call after such a change
+ * outside a stream capture too.  All calls share the one array: calls whose
  * work overlaps on the GPU (different streams, or different threads without ordering) race
  * and give wrong results; order them on one stream.  The array keeps the last call's
  * contents; nothing in it needs clearing between calls. */
@@ -416,8 +429,11 @@ ot_status ot_field_fourier(const ot_octree* t, int n_modes, const int32_t* h_wav
 /* Mean-force removal in a periodic box (Sec. 5.2): subtracts from every leaf of d_field
  * (float4 per leaf) its volume-weighted mean over the unit cube, sum_c f_c 8^-level_c,
  * summed in FP64 in a fixed order (deterministic).  d_mean (nullable, device): the 3
- * subtracted components.  Stream-ordered scratch; asynchronous on `stream`. */
-ot_status ot_field_subtract_mean(const ot_octree* t, float* d_field, double* d_mean, void* stream);
+ * subtracted components.  d_workspace: ot_field_mean_workspace_size bytes (24,600 bytes),
+ * 8-byte aligned, for the block partials; nothing is allocated.  Asynchronous on `stream`. */
+ot_status ot_field_mean_workspace_size(const ot_octree* t, size_t* bytes);
+ot_status ot_field_subtract_mean(const ot_octree* t, float* d_field, double* d_mean, void* d_workspace,
+                                 size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Morton order of a point set (not in the paper's API; its ranks keep their Lagrangian points

@@ -20,7 +20,8 @@ __all__ = [
     "OT_ROOT_LINEAR", "OT_ROOT_MLP", "OT_DEV_OUTSIDE", "OT_DEV_STENCIL", "OT_DEV_REFINED_CAP", "OT_DEV_WINDOW",
     "OtError", "Octree", "Batch", "library_path", "ot_octree_build", "ot_octree_from_leaves", "ot_octree_info",
     "ot_octree_copy_leaves", "ot_octree_set_map_level", "ot_octree_get_map_level", "ot_octree_centres", "ot_octree_destroy", "ot_index_train", "ot_index_get_stats", "ot_index_get_root_params",
-    "ot_index_mlp_grad", "ot_locate", "ot_interpolate", "ot_interpolate_f64", "ot_spread_workspace_size",
+    "ot_index_mlp_grad", "ot_locate", "ot_interpolate", "ot_interpolate_f64", "ot_interpolate_workspace_size",
+    "ot_field_mean_workspace_size", "ot_spread_workspace_size",
     "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_ibm_mdf", "ot_points_morton_order", "ot_field_fourier", "ot_body_sums", "ot_octree_set_periodic",
     "ot_octree_build_mates", "ot_octree_has_mates", "ot_octree_mates_bytes", "ot_octree_build_mates_in", "ot_field_subtract_mean", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
     "ot_last_error", "ot_launch_count",
@@ -116,8 +117,10 @@ def _L():
                 "ot_index_get_root_params": (st, [P, P]),
                 "ot_index_mlp_grad": (st, [P, P, P, i64, P, P, P]),
                 "ot_locate": (st, [P, P, P, P, i64, i32, P, P, P]),
-                "ot_interpolate": (st, [P, i32, P, P, P, i64, P, i32, P, P, P, P]),
-                "ot_interpolate_f64": (st, [P, i32, P, P, P, i64, P, i32, P, P, P, P]),
+                "ot_interpolate": (st, [P, i32, P, P, P, i64, P, i32, P, P, P, P, C.c_size_t, P]),
+                "ot_interpolate_f64": (st, [P, i32, P, P, P, i64, P, i32, P, P, P, P, C.c_size_t, P]),
+                "ot_interpolate_workspace_size": (st, [P, i32, i32, P]),
+                "ot_field_mean_workspace_size": (st, [P, P]),
                 "ot_spread_workspace_size": (st, [P, i32, i64, P]),
                 "ot_spread": (st, [P, i32, i32, P, P, P, P, P, i64, P, P, C.c_size_t, P]),
                 "ot_spread_f64": (st, [P, i32, i32, P, P, P, P, P, i64, P, P, C.c_size_t, P]),
@@ -132,7 +135,7 @@ def _L():
                 "ot_octree_has_mates": (st, [P, P]),
                 "ot_octree_mates_bytes": (st, [P, P]),
                 "ot_octree_build_mates_in": (st, [P, P, C.c_size_t, P]),
-                "ot_field_subtract_mean": (st, [P, P, P, P]),
+                "ot_field_subtract_mean": (st, [P, P, P, P, C.c_size_t, P]),
                 "ot_points_morton_order": (st, [P, P, P, i64, i32, P, P, C.c_size_t, P]),
                 "ot_ibm_mdf": (st, [P, i32, P, P, P, P, P, i64, C.c_float, C.c_float, i32, P, P, P, P, C.c_size_t, P]),
                 "ot_batch_run": (st, [P, P]),
@@ -331,31 +334,43 @@ def ot_locate(tree: Octree, x, y, z, search: int = OT_BINARY, host=None, n_miss=
     return host
 
 
-def _interp(fn, dtype, tree, kernel, x, y, z, field, search, host_in, u, host_out, stream):
+def ot_interpolate_workspace_size(tree: Octree, kernel: int, fp64: bool = False) -> int:
+    """Bytes of workspace ot_interpolate (fp64=False) or ot_interpolate_f64 needs."""
+    b = C.c_size_t()
+    _check(_L().ot_interpolate_workspace_size(tree.handle, kernel, int(fp64), C.byref(b)))
+    return b.value
+
+
+def _interp(fn, dtype, tree, kernel, x, y, z, field, search, host_in, u, host_out, workspace, stream):
     torch = _torch()
     n, px, py, pz = _xyz(x, y, z)
     if u is None:
         u = torch.empty((3, n), dtype=dtype, device="cuda")
+    if workspace is None:
+        need = ot_interpolate_workspace_size(tree, kernel, dtype == torch.float64)
+        workspace = torch.empty(need, dtype=torch.uint8, device="cuda") if need else None
+    have = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(fn(tree.handle, kernel, px, py, pz, n, _dptr(host_in, torch.int32, "host_in"), search,
               _dptr(field, dtype, "field"), _dptr(u, dtype, "u"), _dptr(host_out, torch.int32, "host_out"),
-              _stream(stream)))
+              _dptr(workspace, None, "workspace"), have, _stream(stream)))
     return u
 
 
 def ot_interpolate(tree: Octree, kernel: int, x, y, z, field, search: int = OT_BINARY, host_in=None, u=None,
-                   host_out=None, stream=None):
-    """field: (N, 4) float32; returns u (3, n) float32."""
+                   host_out=None, workspace=None, stream=None):
+    """field: (N, 4) float32; returns u (3, n) float32.  workspace: a CUDA uint8 tensor of
+    ot_interpolate_workspace_size bytes (allocated here when None)."""
     torch = _torch()
     return _interp(_L().ot_interpolate, torch.float32, tree, kernel, x, y, z, field, search, host_in, u, host_out,
-                   stream)
+                   workspace, stream)
 
 
 def ot_interpolate_f64(tree: Octree, kernel: int, x, y, z, field, search: int = OT_BINARY, host_in=None, u=None,
-                       host_out=None, stream=None):
+                       host_out=None, workspace=None, stream=None):
     """field: (N, 4) float64; returns u (3, n) float64."""
     torch = _torch()
     return _interp(_L().ot_interpolate_f64, torch.float64, tree, kernel, x, y, z, field, search, host_in, u,
-                   host_out, stream)
+                   host_out, workspace, stream)
 
 
 def ot_spread_workspace_size(tree: Octree, kernel: int, n: int) -> int:
@@ -500,12 +515,23 @@ def ot_octree_has_mates(tree: Octree) -> bool:
     return bool(v.value)
 
 
-def ot_field_subtract_mean(tree: Octree, field, stream=None):
-    """Subtracts the volume-weighted mean of field ((N, 4) float32, in place); returns the mean."""
+def ot_field_mean_workspace_size(tree: Octree) -> int:
+    b = C.c_size_t()
+    _check(_L().ot_field_mean_workspace_size(tree.handle, C.byref(b)))
+    return b.value
+
+
+def ot_field_subtract_mean(tree: Octree, field, mean=None, workspace=None, stream=None):
+    """Subtracts the volume-weighted mean of field ((N, 4) float32, in place); returns the mean
+    (3 float64).  workspace: a CUDA uint8 tensor of ot_field_mean_workspace_size bytes."""
     torch = _torch()
-    mean = torch.empty(3, dtype=torch.float64, device=field.device)
+    if mean is None:
+        mean = torch.empty(3, dtype=torch.float64, device=field.device)
+    if workspace is None:
+        workspace = torch.empty(ot_field_mean_workspace_size(tree), dtype=torch.uint8, device=field.device)
     _check(_L().ot_field_subtract_mean(tree.handle, _dptr(field, torch.float32, "field"), _dptr(mean),
-                                       _stream(stream)))
+                                       _dptr(workspace, None, "workspace"),
+                                       workspace.numel() * workspace.element_size(), _stream(stream)))
     return mean
 
 

@@ -129,13 +129,14 @@ __global__ void __launch_bounds__(256) k_advect4(double* __restrict__ x, float* 
 template <typename T>
 ot_status interp_any(const ot_octree* t, int kernel, const double* x, const double* y, const double* z,
                             int64_t n, const int32_t* host_in, int search, const T* field, T* u, int32_t* host_out,
-                            void* stream) {
+                            void* ws, size_t ws_bytes, void* stream) {
     ot_status st = check_points(t, x, y, z, n);
     if (st != OT_OK) return st;
     if (!kernel_ok(kernel) || !search_ok(search) || (n > 0 && (!field || !u))) return OT_ERR_ARG;
     if (kernel != OT_TRILINEAR && t->lmax < 1) return OT_ERR_ARG;
     if (search == OT_LEARNED && !t->has_index && !(kernel == OT_TRILINEAR && host_in)) return OT_ERR_NO_INDEX;
-    return launch_interp<T>(t, kernel, x, y, z, n, host_in, search, field, u, host_out, (cudaStream_t)stream);
+    return launch_interp<T>(t, kernel, x, y, z, n, host_in, search, field, u, host_out, ws, ws_bytes,
+                            (cudaStream_t)stream);
 }
 
 template <typename T>
@@ -368,16 +369,22 @@ ot_status ot_locate(const ot_octree* t, const double* x, const double* y, const 
     return launch_locate(t, x, y, z, n, search, host, n_miss, (cudaStream_t)stream);
 }
 
+ot_status ot_interpolate_workspace_size(const ot_octree* t, int kernel, int fp64, size_t* bytes) {
+    if (!t || !bytes || !kernel_ok(kernel)) return OT_ERR_ARG;
+    *bytes = interp_ws_bytes(t, kernel, fp64 ? sizeof(double) : sizeof(float));
+    return OT_OK;
+}
+
 ot_status ot_interpolate(const ot_octree* t, int kernel, const double* x, const double* y, const double* z, int64_t n,
                          const int32_t* host_in, int search, const float* field, float* u, int32_t* host_out,
-                         void* stream) {
-    return interp_any<float>(t, kernel, x, y, z, n, host_in, search, field, u, host_out, stream);
+                         void* ws, size_t ws_bytes, void* stream) {
+    return interp_any<float>(t, kernel, x, y, z, n, host_in, search, field, u, host_out, ws, ws_bytes, stream);
 }
 
 ot_status ot_interpolate_f64(const ot_octree* t, int kernel, const double* x, const double* y, const double* z,
                              int64_t n, const int32_t* host_in, int search, const double* field, double* u,
-                             int32_t* host_out, void* stream) {
-    return interp_any<double>(t, kernel, x, y, z, n, host_in, search, field, u, host_out, stream);
+                             int32_t* host_out, void* ws, size_t ws_bytes, void* stream) {
+    return interp_any<double>(t, kernel, x, y, z, n, host_in, search, field, u, host_out, ws, ws_bytes, stream);
 }
 
 ot_status ot_spread_workspace_size(const ot_octree* t, int kernel, int64_t n, size_t* bytes) {

@@ -246,6 +246,13 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
         launches.push_back(Launch{fn, args, (unsigned)(num_sms() * per_sm)});
         return cudaSuccess;
     };
+    // every warp takes one tile number past the last tile before it stops: the 32-bit tile
+    // counter must hold ntiles plus one per warp of the launch without wrapping
+    auto counter_fits = [&]() {
+        for (const Launch& l : launches)
+            if ((uint64_t)l.args.ntiles + (uint64_t)l.grid * (uint64_t)(block / 32) >= (1ULL << 32)) return false;
+        return true;
+    };
     if (!t->d_mates) {
         void* fn = learned ? (two ? (void*)k_batch<true, 2, false> : (void*)k_batch<true, 3, false>)
                            : (two ? (void*)k_batch<false, 2, false> : (void*)k_batch<false, 3, false>);
@@ -273,6 +280,10 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
             void* fn = learned ? (void*)k_batch<true, TRI_MINB, true, K_TRI> : (void*)k_batch<false, TRI_MINB, true, K_TRI>;
             if ((e = add_launch(fn, part[1], tri_per_sm)) != cudaSuccess) return fail(e);
         }
+    }
+    if (!counter_fits()) {
+        ot_batch_destroy(b);
+        return OT_ERR_LIMIT;
     }
     if (launches.size() > 1) {
         cudaFree(b->d_counter);

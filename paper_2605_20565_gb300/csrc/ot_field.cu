@@ -91,19 +91,30 @@ __global__ void __launch_bounds__(MT) k_field_sub(float4* __restrict__ f, int64_
 
 using namespace ot;
 
-extern "C" ot_status ot_field_subtract_mean(const ot_octree* t, float* d_field, double* d_mean, void* stream) {
-    if (!t || !d_field) return OT_ERR_ARG;
+// Block partials of the mean: at most MEAN_BLOCKS blocks, so the workspace has a fixed size.
+constexpr int MEAN_BLOCKS = 1024;
+
+extern "C" ot_status ot_field_mean_workspace_size(const ot_octree* t, size_t* bytes) {
+    if (!t || !bytes) return OT_ERR_ARG;
+    *bytes = sizeof(double) * (3 * (size_t)MEAN_BLOCKS + 3);
+    return OT_OK;
+}
+
+extern "C" ot_status ot_field_subtract_mean(const ot_octree* t, float* d_field, double* d_mean, void* d_workspace,
+                                            size_t ws_bytes, void* stream) {
+    if (!t || !d_field || !d_workspace || ((uintptr_t)d_workspace & 7) ||
+        ws_bytes < sizeof(double) * (3 * (size_t)MEAN_BLOCKS + 3))
+        return OT_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((t->n + MT - 1) / MT, (int64_t)num_sms() * 4));
-    double* part = nullptr;
-    OT_CUDA(cudaMallocAsync(&part, sizeof(double) * (3 * (size_t)nb + 3), s));
+    const int nb = (int)std::max<int64_t>(
+        1, std::min<int64_t>({(t->n + MT - 1) / MT, (int64_t)num_sms() * 4, (int64_t)MEAN_BLOCKS}));
+    double* part = static_cast<double*>(d_workspace);
     double* mean = part + 3 * nb;
     k_field_sum<<<nb, MT, 0, s>>>(t->d_level, t->n, reinterpret_cast<const float4*>(d_field), part);
     k_field_mean_finish<<<1, 32, 0, s>>>(part, nb, mean);
     k_field_sub<<<nb, MT, 0, s>>>(reinterpret_cast<float4*>(d_field), t->n, mean);
     count_launch(3);
     if (d_mean) OT_CUDA(cudaMemcpyAsync(d_mean, mean, sizeof(double) * 3, cudaMemcpyDeviceToDevice, s));
-    OT_CUDA(cudaFreeAsync(part, s));
     OT_CUDA(cudaGetLastError());
     return OT_OK;
 }

@@ -73,10 +73,14 @@ TreeView tree_view(const ot_octree* t);
 // Exclusive scan of n uint32 (in place allowed); returns the total in *d_total if non-null.
 // Temporary storage is allocated stream-ordered and released before return.
 ot_status scan_u32(const uint32_t* d_in, uint32_t* d_out, int64_t n, uint32_t* d_total, cudaStream_t s);
+// The same scan with its temporaries in ws (scan_ws_bytes(n) bytes, 4-byte aligned): no allocation.
+size_t scan_ws_bytes(int64_t n);
+ot_status scan_u32_ws(const uint32_t* d_in, uint32_t* d_out, int64_t n, uint32_t* d_total, void* ws, cudaStream_t s);
 // Stable LSD radix sort of n uint64 by bits [bit0, bit1) (8-bit digits).  d_tmp: n uint64
 // scratch.  Result in d_keys.  Temporaries (histograms) are stream-ordered allocations.
 ot_status radix_sort_u64(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bit0, int bit1, cudaStream_t s);
-// Histogram + offset workspace bytes for radix_sort_u64_ws.
+// Workspace bytes of radix_sort_u64_ws / radix_sort_u64_dn (histograms, offsets and the
+// scan's temporaries): with it those sorts allocate nothing.
 size_t radix_ws_bytes(int64_t n);
 // Sort of the first *d_n (device value, <= n_max) keys with workspace of radix_ws_bytes(n_max)
 // bytes; *result is the buffer (d_keys or d_tmp) holding the sorted keys.
@@ -114,9 +118,13 @@ ot_status mlp_grad(const float* d_params, const float* d_x, const float* d_t, in
 // point kernels (ot_interp.cu) -------------------------------------------------------------------
 ot_status launch_locate(const ot_octree* t, const double* x, const double* y, const double* z, int64_t n, int search,
                         int32_t* host, unsigned long long* n_miss, cudaStream_t s);
+// Trilinear interpolation needs interp_ws_bytes(t, OT_TRILINEAR, sizeof(T)) bytes of workspace
+// (the cell means of the field, 16-byte aligned); the delta kernels need none.
 template <typename T>
 ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const double* y, const double* z, int64_t n,
-                        const int32_t* host_in, int search, const T* field, T* u, int32_t* host_out, cudaStream_t s);
+                        const int32_t* host_in, int search, const T* field, T* u, int32_t* host_out, void* ws,
+                        size_t ws_bytes, cudaStream_t s);
+size_t interp_ws_bytes(const ot_octree* t, int kernel, size_t elem);
 
 // pyramid of cell means over levels 0 .. lmap_level (ot_pyramid.cu) ---------------------------
 // Level l occupies cells [pyramid_offset(l), pyramid_offset(l) + 8^l), 4 values per cell.

@@ -135,8 +135,11 @@ ot_status launch_locate(const ot_octree* t, const double* x, const double* y, co
 
 template <typename T>
 ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const double* y, const double* z, int64_t n,
-                        const int32_t* host_in, int search, const T* field, T* u, int32_t* host_out, cudaStream_t s) {
+                        const int32_t* host_in, int search, const T* field, T* u, int32_t* host_out, void* ws,
+                        size_t ws_bytes, cudaStream_t s) {
     if (n == 0) return OT_OK;
+    if (kernel == OT_TRILINEAR && (ws_bytes < interp_ws_bytes(t, kernel, sizeof(T)) || !ws || ((uintptr_t)ws & 15)))
+        return OT_ERR_ARG;
     const bool learned = search == OT_LEARNED;
     TreeView v = tree_view(t);
     const size_t smem = 0;
@@ -149,14 +152,9 @@ ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const d
         k_<<<persistent_grid(k_, block, smem, n), block, smem, s>>>(__VA_ARGS__);          \
     } while (0)
     if (kernel == OT_TRILINEAR) {
-        // pyramid of cell means (refined level-mates), stream-ordered scratch
-        void* pws = nullptr;
-        OT_CUDA(cudaMallocAsync(&pws, pyramid_bytes(t, sizeof(T)), s));
-        T* pyr = static_cast<T*>(pws);
-        if ((st = launch_pyramid<T>(t, field, pyr, s)) != OT_OK) {
-            cudaFreeAsync(pws, s);
-            return st;
-        }
+        // cell means of the field (refined level-mates), in the caller's workspace
+        T* pyr = static_cast<T*>(ws);
+        if ((st = launch_pyramid<T>(t, field, pyr, s)) != OT_OK) return st;
         if (t->d_mates && learned)
             OT_LAUNCH((k_trilinear<T, true, true>), v, x, y, z, n, host_in, field, pyr, u, host_out);
         else if (t->d_mates)
@@ -165,7 +163,6 @@ ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const d
             OT_LAUNCH((k_trilinear<T, true, false>), v, x, y, z, n, host_in, field, pyr, u, host_out);
         else
             OT_LAUNCH((k_trilinear<T, false, false>), v, x, y, z, n, host_in, field, pyr, u, host_out);
-        cudaFreeAsync(pws, s);
     } else if (kernel == OT_PESKIN4) {
         if (learned)
             OT_LAUNCH((k_delta<T, OT_PESKIN4, true>), v, x, y, z, n, field, u, host_out);
@@ -184,8 +181,14 @@ ot_status launch_interp(const ot_octree* t, int kernel, const double* x, const d
 }
 
 template ot_status launch_interp<float>(const ot_octree*, int, const double*, const double*, const double*, int64_t,
-                                        const int32_t*, int, const float*, float*, int32_t*, cudaStream_t);
+                                        const int32_t*, int, const float*, float*, int32_t*, void*, size_t,
+                                        cudaStream_t);
 template ot_status launch_interp<double>(const ot_octree*, int, const double*, const double*, const double*, int64_t,
-                                         const int32_t*, int, const double*, double*, int32_t*, cudaStream_t);
+                                         const int32_t*, int, const double*, double*, int32_t*, void*, size_t,
+                                         cudaStream_t);
+
+size_t interp_ws_bytes(const ot_octree* t, int kernel, size_t elem) {
+    return kernel == OT_TRILINEAR ? pyramid_bytes(t, elem) : 0;
+}
 
 } // namespace ot

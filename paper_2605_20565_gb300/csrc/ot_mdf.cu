@@ -84,7 +84,7 @@ ot_status launch_mdf(const ot_octree* t, int kernel, const double* x, const doub
     if (slip) OT_CUDA(cudaMemsetAsync(s2, 0, sizeof(double) * (size_t)(n_iter + 1), s));
     ot_status st;
     for (int it = 0; it <= n_iter; ++it) {
-        if ((st = launch_interp<float>(t, kernel, x, y, z, n, nullptr, OT_BINARY, u, uk, nullptr, s)) != OT_OK)
+        if ((st = launch_interp<float>(t, kernel, x, y, z, n, nullptr, OT_BINARY, u, uk, nullptr, nullptr, 0, s)) != OT_OK)
             return st;
         k_mdf_force<<<grid_of(3 * n), 256, 0, s>>>(U, uk, n, 1.0f / dt, Fk, slip ? s2 + it : nullptr);
         count_launch();

@@ -9,6 +9,8 @@
 // buffer and the radix-sort histograms) lives in one file-scope device array of a fixed size,
 // OT_NOALLOC_SCRATCH_BYTES.  Every GPU that loads this library holds that array until the
 // process exits.
+#include <cuda.h>  // driver types only: the two driver calls below are reached through the runtime
+
 #include <mutex>
 
 #include "ot_internal.h"
@@ -16,26 +18,59 @@
 namespace {
 
 // The scratch.  In host code this name is only a stand-in for the symbol, never a device
-// address: the address comes from cudaGetSymbolAddress, once per device.
+// address: the address comes from cudaGetSymbolAddress, once per device and context.
 static __device__ __align__(256) unsigned char g_spread_scratch[OT_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of the scratch on the current device, looked up on the first call made with
-// that device current.
+// Identity of the current CUDA context (0 when the driver does not say).  A context that was
+// destroyed and created again -- cudaDeviceReset, for instance -- has a new identity, and the
+// library's device array may then sit at a new address, so the address is looked up again.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
+
+// Device address of the scratch on the current device: looked up with cudaGetSymbolAddress on
+// the first call made with that device current (the set-up; it must not run inside a stream
+// capture), and again whenever the device's context is not the one the address came from.
 cudaError_t scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    // a call without a context yet: the lookup below creates the primary context, after which
+    // the identity is read again
+    unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (!g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_spread_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = current_context_id();
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;

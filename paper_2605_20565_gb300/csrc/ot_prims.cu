@@ -86,38 +86,56 @@ __global__ void k_total(const uint32_t* in_last, const uint32_t* scan_last, uint
     *total = *in_last + *scan_last;
 }
 
-ot_status scan_u32(const uint32_t* d_in, uint32_t* d_out, int64_t n, uint32_t* d_total, cudaStream_t s) {
+// Tile totals of every level of the recursive scan of n values.
+static int64_t scan_tile_elems(int64_t n) {
+    int64_t total = 0;
+    for (int64_t m = n; m > SCAN_TILE; m = (m + SCAN_TILE - 1) / SCAN_TILE) total += (m + SCAN_TILE - 1) / SCAN_TILE;
+    return total;
+}
+
+size_t scan_ws_bytes(int64_t n) { return (size_t)(scan_tile_elems(n) + 1) * sizeof(uint32_t) + 256; }
+
+// The recursive scan with its tile totals in tmp (scan_tile_elems(n) uint32).
+static ot_status scan_levels(const uint32_t* d_in, uint32_t* d_out, int64_t n, uint32_t* tmp, cudaStream_t s) {
+    const int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nt == 1) {
+        k_scan_tiles<<<1, SCAN_T, 0, s>>>(d_in, d_out, n, nullptr);
+        count_launch();
+        return OT_OK;
+    }
+    k_scan_tiles<<<(unsigned)nt, SCAN_T, 0, s>>>(d_in, d_out, n, tmp);
+    count_launch();
+    ot_status st = scan_levels(tmp, tmp, nt, tmp + nt, s);
+    if (st != OT_OK) return st;
+    k_scan_add<<<(unsigned)nt, 256, 0, s>>>(d_out, n, tmp);
+    count_launch();
+    return OT_OK;
+}
+
+ot_status scan_u32_ws(const uint32_t* d_in, uint32_t* d_out, int64_t n, uint32_t* d_total, void* ws, cudaStream_t s) {
     if (n <= 0) {
         if (d_total) OT_CUDA(cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s));
         return OT_OK;
     }
-    const int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
     // the total needs the last input, which an in-place scan overwrites: keep it first
-    uint32_t* last = nullptr;
-    if (d_total) {
-        OT_CUDA(cudaMallocAsync(&last, sizeof(uint32_t), s));
-        OT_CUDA(cudaMemcpyAsync(last, d_in + n - 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-    }
-    if (nt == 1) {
-        k_scan_tiles<<<1, SCAN_T, 0, s>>>(d_in, d_out, n, nullptr);
-        count_launch();
-    } else {
-        uint32_t* tiles = nullptr;
-        OT_CUDA(cudaMallocAsync(&tiles, sizeof(uint32_t) * nt, s));
-        k_scan_tiles<<<(unsigned)nt, SCAN_T, 0, s>>>(d_in, d_out, n, tiles);
-        ot_status st = scan_u32(tiles, tiles, nt, nullptr, s);
-        if (st != OT_OK) return st;
-        k_scan_add<<<(unsigned)nt, 256, 0, s>>>(d_out, n, tiles);
-        count_launch(2);
-        OT_CUDA(cudaFreeAsync(tiles, s));
-    }
+    uint32_t* last = static_cast<uint32_t*>(ws);
+    if (d_total) OT_CUDA(cudaMemcpyAsync(last, d_in + n - 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    ot_status st = scan_levels(d_in, d_out, n, last + 1, s);
+    if (st != OT_OK) return st;
     if (d_total) {
         k_total<<<1, 1, 0, s>>>(last, d_out + n - 1, d_total);
         count_launch();
-        OT_CUDA(cudaFreeAsync(last, s));
     }
     OT_CUDA(cudaGetLastError());
     return OT_OK;
+}
+
+ot_status scan_u32(const uint32_t* d_in, uint32_t* d_out, int64_t n, uint32_t* d_total, cudaStream_t s) {
+    void* ws = nullptr;
+    OT_CUDA(cudaMallocAsync(&ws, scan_ws_bytes(n), s));
+    ot_status st = scan_u32_ws(d_in, d_out, n, d_total, ws, s);
+    cudaFreeAsync(ws, s);
+    return st;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -183,15 +201,17 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ in, uint64_t* __res
     }
 }
 
+// Histograms and offsets (256 per tile each), then the scan's temporaries.
 size_t radix_ws_bytes(int64_t n) {
     int64_t nt = (n + RTILE - 1) / RTILE;
     if (nt < 1) nt = 1;
-    return (size_t)(2 * 256 * nt) * sizeof(uint32_t) + 256;
+    return (size_t)(2 * 256 * nt) * sizeof(uint32_t) + scan_ws_bytes(256 * nt) + 256;
 }
 
 static ot_status radix_passes(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bit0, int bit1, uint32_t* hist,
                               uint32_t* offs, cudaStream_t s, const uint32_t* d_n = nullptr,
                               uint64_t** result = nullptr) {
+    uint32_t* stmp = offs + 256 * ((n + RTILE - 1) / RTILE);
     const int nt = (int)((n + RTILE - 1) / RTILE);
     uint64_t* src = d_keys;
     uint64_t* dst = d_tmp;
@@ -200,7 +220,7 @@ static ot_status radix_passes(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int 
         const uint32_t mask = (1u << nb) - 1u;
         k_radix_hist<<<nt, RT, 0, s>>>(src, n, sh, mask, hist, nt, d_n);
         count_launch();
-        ot_status st = scan_u32(hist, offs, (int64_t)256 * nt, nullptr, s);
+        ot_status st = scan_u32_ws(hist, offs, (int64_t)256 * nt, nullptr, stmp, s);
         if (st != OT_OK) return st;
         k_radix_scatter<<<nt, RT, 0, s>>>(src, dst, n, sh, mask, offs, nt, d_n);
         count_launch();

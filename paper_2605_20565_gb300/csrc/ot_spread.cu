@@ -354,10 +354,12 @@ ot_status spread_sorted(const ot_octree* t, const double* x, const double* y, co
     uint32_t* off = reinterpret_cast<uint32_t*>(p);
     p += align_up((size_t)n * sizeof(uint32_t));
     uint32_t* d_np = reinterpret_cast<uint32_t*>(p);
+    p += 256;
+    void* scan_ws = p;
     auto kc = k_spread_count<K>;
     kc<<<grid_for(kc, 256, 0, n), 256, 0, s>>>(x, y, z, n, t->lmax, cnt);
     count_launch();
-    if ((st = scan_u32(cnt, off, n, d_np, s)) != OT_OK) return st;
+    if ((st = scan_u32_ws(cnt, off, n, d_np, scan_ws, s)) != OT_OK) return st;
     auto ke = k_spread_emit_rec<T, K>;
     if ((st = prep(ke, smem)) != OT_OK) return st;
     ke<<<grid_for(ke, 256, smem, n), 256, smem, s>>>(v, x, y, z, F, dV, n, off, pairs, recs);
@@ -381,7 +383,7 @@ size_t spread_ws_bytes(const ot_octree* t, int kernel, int64_t n) {
     (void)t;
     const int64_t np = n * stencil_cells(kernel);
     return (size_t)np * 16 + align_up(radix_ws_bytes(np)) + align_up((size_t)n * sizeof(MarkerRec<double>)) +
-           2 * align_up((size_t)n * sizeof(uint32_t)) + 512;
+           2 * align_up((size_t)n * sizeof(uint32_t)) + 256 + align_up(scan_ws_bytes(n)) + 512;
 }
 
 template <typename T>

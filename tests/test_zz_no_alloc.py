@@ -1,7 +1,9 @@
 """ot_spread_noalloc through the C ABI: the sorted spreading variant for callers that cannot
-allocate device memory (its scratch is the library's fixed device array).  Its output must
-match the allocating ot_spread(OT_SORTED) on two calls in a row, and sizes beyond the fixed
-scratch must be refused before anything is launched.  This file is collected last."""
+allocate device memory (its scratch is the library's fixed device array).  Its output must equal
+the allocating ot_spread(OT_SORTED) bit for bit on two calls in a row (the same per-leaf sums in
+the same marker order), match the FP64 oracle within the FP32 tolerance, accept exactly the
+documented maximum marker counts and refuse one more before anything is launched.  This file
+is collected last."""
 import ctypes as C
 
 import numpy as np
@@ -10,6 +12,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-5
+MAX_MARKERS = {2: 146_202, 3: 493_432}  # the limits stated in include/octtrack.h
 
 
 @pytest.fixture(scope="module")
@@ -40,6 +43,7 @@ def _call(torch, fn, tree, kernel, X, F, dV, f):
 @pytest.mark.parametrize("kernel", [2, 3])
 @pytest.mark.parametrize("with_dv", [False, True])
 def test_noalloc_matches_sorted_spread_twice(env, kernel, with_dv):
+    import oracle
     torch, ot, fn, w, tree = env
     n_leaves = ot.ot_octree_info(tree)[0]
     rng = np.random.default_rng(41)
@@ -51,13 +55,42 @@ def test_noalloc_matches_sorted_spread_twice(env, kernel, with_dv):
         dV = torch.as_tensor((rng.uniform(0.5, 2.0, n) * 2.0 ** (-3 * w.lmax)).astype(np.float32), device="cuda")
     ref = torch.zeros((n_leaves, 4), dtype=torch.float32, device="cuda")
     ot.ot_spread(tree, kernel, ot.OT_SORTED, X[0], X[1], X[2], F, ref, dV=dV)
-    scale = float(ref[:, :3].abs().max())
     for _ in range(2):
         f = torch.zeros((n_leaves, 4), dtype=torch.float32, device="cuda")
         assert _call(torch, fn, tree, kernel, X, F, dV, f) == 0
         torch.cuda.synchronize()
-        assert float((f - ref).abs().max()) <= TOL32 * scale
-        assert torch.all(f[:, 3] == 0)
+        assert torch.equal(f, ref)
+    # and against the FP64 oracle on the same inputs
+    ko, lo = oracle.octree_build(w.spheres, w.lmin, w.lmax)
+    f_ref, _ = oracle.spread_delta(ko, lo, w.lmax, kernel, *w.markers, F.double().cpu().numpy(),
+                                   dV=None if dV is None else dV.double().cpu().numpy())
+    scale = float(np.abs(f_ref[:, :3]).max())
+    assert float(np.abs(f.cpu().numpy()[:, :3] - f_ref[:, :3]).max()) <= TOL32 * scale
+    assert torch.all(f[:, 3] == 0)
+
+
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_noalloc_limit_is_exact(env, kernel):
+    """The documented maximum runs (and equals the allocating spreading); one more marker is
+    refused with OT_ERR_LIMIT and leaves the output untouched."""
+    torch, ot, fn, w, tree = env
+    n_leaves = ot.ot_octree_info(tree)[0]
+    m = MAX_MARKERS[kernel]
+    reps = -(-m // w.markers.shape[1])
+    Xh = np.tile(w.markers, reps)[:, :m + 1]
+    X = [torch.as_tensor(np.ascontiguousarray(Xh[d]), device="cuda") for d in range(3)]
+    F = torch.as_tensor(np.random.default_rng(5).normal(size=(3, m + 1)).astype(np.float32), device="cuda")
+    f = torch.zeros((n_leaves, 4), dtype=torch.float32, device="cuda")
+    over = _call(torch, fn, tree, kernel, X, F, None, f)
+    torch.cuda.synchronize()
+    assert over == -8 and torch.count_nonzero(f) == 0
+    Xm = [x[:m].contiguous() for x in X]
+    Fm = F[:, :m].contiguous()
+    assert _call(torch, fn, tree, kernel, Xm, Fm, None, f) == 0
+    ref = torch.zeros_like(f)
+    ot.ot_spread(tree, kernel, ot.OT_SORTED, Xm[0], Xm[1], Xm[2], Fm, ref)
+    torch.cuda.synchronize()
+    assert torch.equal(f, ref)
 
 
 def test_noalloc_refuses_sizes_beyond_its_scratch(env):
