@@ -381,6 +381,15 @@ typedef struct {
                           per SM, capped by occupancy (0: 2, which measured fastest: its loads
                           are latency-bound and fewer warps keep more of each SM's cache
                           per warp)                                                          */
+    int tri_records;   /* with the level-mate table: 0 (default): value records for the hot
+                          leaves -- the leaves of level <= min(level-map level, hot level),
+                          the hot level being the deepest at which the trilinear points, spread
+                          evenly, would give every leaf at least 4 -- holding for each octant
+                          of the leaf's cell its 8 level-mate values (96 bytes), rewritten from
+                          the field at every replay; a point in a level-map cell inside a hot
+                          leaf reads the cell's 8-byte entry and one record instead of the
+                          level-mate row and 8 scattered values; identical results.  Costs
+                          8 bytes per level-map cell and 768 bytes per hot leaf.  -1: off    */
 } ot_launch;
 
 /* Create a batch over groups (copied) reading d_field (float4 per leaf).  search selects

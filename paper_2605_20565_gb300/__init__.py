@@ -75,9 +75,9 @@ class _Group(C.Structure):
 
 class _Launch(C.Structure):
     _fields_ = [("block", C.c_int), ("tile", C.c_int), ("blocks_per_sm", C.c_int), ("order_level", C.c_int),
-                ("tri_tile", C.c_int), ("tri_blocks_per_sm", C.c_int)]
+                ("tri_tile", C.c_int), ("tri_blocks_per_sm", C.c_int), ("tri_records", C.c_int)]
 
-    _names = ("block", "tile", "blocks_per_sm", "order_level", "tri_tile", "tri_blocks_per_sm")
+    _names = ("block", "tile", "blocks_per_sm", "order_level", "tri_tile", "tri_blocks_per_sm", "tri_records")
 
     @classmethod
     def of(cls, d: dict):

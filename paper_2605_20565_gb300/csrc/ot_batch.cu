@@ -25,6 +25,13 @@ struct ot_batch {
     unsigned* d_counter = nullptr;
     float* d_pyr = nullptr;    // pyramid of cell means, recomputed at every replay
     int kernels = 1;           // kernels in one replay of the graph
+    // value records of the hot leaves (trilinear launch with the level-mate table): per
+    // level-map cell its entry, per hot leaf its index, per (hot leaf, octant) the 8 level-mate
+    // values, rewritten from the field at every replay
+    uint2* d_ent = nullptr;
+    int* d_hot_leaf = nullptr;
+    float* d_rec = nullptr;
+    int64_t n_rec = 0;
 };
 
 namespace ot {
@@ -106,6 +113,171 @@ __global__ void __launch_bounds__(256, MINB) k_batch(TreeView t, BatchArgs a, co
 }
 
 
+// ------------------------------------------------------------------------------------------
+// Value records of the hot leaves.  A level-map cell that lies inside one leaf of level at most
+// the hot level (a level whose leaves receive several points per launch) gets the entry
+// (leaf, level << 27 | hot ordinal); every other cell (leaf, ~0).  For every hot leaf and octant
+// of its cell, the record holds the 8 level-mate values of its level-mate row (24 floats, corner
+// order), copied from the field and the cell means at every replay.  A point in such a cell then
+// reads one cell entry and one 96-byte record (three 32-byte loads) instead of the row and 8
+// scattered values; the values and the sum are the same, so the results are bit-identical.
+// ------------------------------------------------------------------------------------------
+constexpr uint32_t REC_NONE = 0xFFFFFFFFu;
+constexpr int REC_FLOATS = 24;
+
+__global__ void k_hot_flags(const uint8_t* __restrict__ level, int64_t n, int hot_l, uint32_t* __restrict__ flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = level[i] <= hot_l ? 1u : 0u;
+}
+
+__global__ void k_hot_list(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ ord, int64_t n,
+                           int* __restrict__ hot_leaf) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) hot_leaf[ord[i]] = (int)i;
+}
+
+__global__ void k_cell_entries(TreeView t, const uint32_t* __restrict__ ord, int hot_l, uint2* __restrict__ ent) {
+    const int64_t ncell = (int64_t)1 << (3 * t.lmap_level);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)t.lmap[c];
+        const int e = c + 1 < ncell ? (int)t.lmap[c + 1] : t.n;
+        const int lv = t.level[a];
+        const bool hot = e - a <= 1 && lv <= hot_l;
+        ent[c] = make_uint2((uint32_t)a, hot ? ((uint32_t)lv << 27) | ord[a] : REC_NONE);
+    }
+}
+
+// One record per (hot leaf, octant), rewritten from the field and the cell means.
+__global__ void __launch_bounds__(256) k_hot_records(TreeView t, const int* __restrict__ hot_leaf, int64_t n_rec,
+                                                     const float* __restrict__ field, const float* __restrict__ pyr,
+                                                     float* __restrict__ rec) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rec; r += (int64_t)gridDim.x * blockDim.x) {
+        const int h = hot_leaf[r >> 3];
+        const uint4* row = t.mates + 2 * (8 * (long long)h + (r & 7));
+        const uint4 r0 = __ldg(row), r1 = __ldg(row + 1);
+        const uint32_t sl[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        float v[REC_FLOATS];
+#pragma unroll
+        for (int corner = 0; corner < 8; ++corner) {
+            const uint32_t sv = sl[corner];
+            const float4 f = Vec4<float>::load((sv >> 31) ? pyr : field, (long long)(sv & 0x7FFFFFFFu));
+            v[3 * corner] = f.x, v[3 * corner + 1] = f.y, v[3 * corner + 2] = f.z;
+        }
+        float4* dst = reinterpret_cast<float4*>(rec + REC_FLOATS * r);
+#pragma unroll
+        for (int k = 0; k < REC_FLOATS / 4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+}
+
+// 32 bytes from global memory in one load (sm_100 and later), read-only path.
+__device__ __forceinline__ void ld_nc_v8(const float* p, float* r) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+        : "l"(p));
+}
+
+// The trilinear launch with value records.  Per 32-point row: quantise, read the level-map
+// cell's entry; a point in a hot cell takes its octant's record and is done; the others (cold:
+// deeper leaves, uncovered cells) are queued per warp and, whenever 32 are queued (and at the
+// end), interpolated together by the level-mate-table routine with every lane busy.
+template <bool LEARNED>
+__global__ void __launch_bounds__(256, TRI_MINB) k_tri_rec(TreeView t, BatchArgs a, const float* __restrict__ field,
+                                                          const float* __restrict__ pyr,
+                                                          unsigned* __restrict__ counter,
+                                                          const uint2* __restrict__ ent,
+                                                          const float* __restrict__ rec) {
+    __shared__ HostQueue s_queue[256 / 32];
+    __shared__ RootModel s_root;
+    __shared__ long long s_cold[256 / 32][64];
+    const int wid = threadIdx.x >> 5;
+    HostQueue& wq = s_queue[wid];
+    long long* cq = s_cold[wid];
+    stage_root<LEARNED>(t, s_root);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int ent_shift = 3 * (MAXLEVEL - t.lmap_level);
+    const int64_t tile_pts = 32 * (int64_t)a.tile;
+    int qn = 0;  // queued cold points (warp-uniform)
+    // the first cnt queued points, one per lane (warp-wide)
+    auto drain = [&](int cnt) {
+        const bool act = lane < cnt;
+        const long long it = act ? cq[lane] : 0;
+        const GroupDev& gq = a.g[(int)(it >> 40)];
+        const int64_t i = it & ((1LL << 40) - 1);
+        const double x = act ? gq.x[i] : 0.0, y = act ? gq.y[i] : 0.0, z = act ? gq.z[i] : 0.0;
+        float o[3];
+        const int h = trilinear_mates<float, LEARNED>(t, s_root, field, pyr, wq, act, x, y, z, -1, o);
+        if (act) {
+            gq.u[i] = o[0];
+            gq.u[gq.n + i] = o[1];
+            gq.u[2 * gq.n + i] = o[2];
+            if (gq.host) gq.host[i] = h;
+        }
+    };
+    for (;;) {
+        unsigned tl = 0;
+        if (lane == 0) tl = atomicAdd(counter, 1u);
+        tl = __shfl_sync(0xffffffffu, tl, 0);
+        if ((int64_t)tl >= a.ntiles) break;
+        int g = 0;
+        while (g + 1 < a.ng && (int64_t)tl >= a.g[g + 1].tile0) ++g;
+        const GroupDev& gr = a.g[g];
+        const int64_t base = ((int64_t)tl - gr.tile0) * tile_pts;
+        for (int j = 0; j < a.tile; ++j) {
+            const int64_t i = base + (int64_t)j * 32 + lane;
+            const bool active = i < gr.n;
+            if (!__any_sync(0xffffffffu, active)) break;  // warp-uniform
+            const double x = active ? gr.x[i] : 0.0, y = active ? gr.y[i] : 0.0, z = active ? gr.z[i] : 0.0;
+            uint64_t X[3];
+            const bool ok = active && fixpoint3(x, y, z, X);
+            uint2 e = make_uint2(0u, REC_NONE);
+            if (ok) {
+                const uint64_t q = morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32));
+                e = __ldg(ent + (q >> ent_shift));
+            }
+            const bool hot = e.y != REC_NONE;
+            if (hot) {
+                float at[3];
+                const int oc = tri_octant<float>(X, (int)(e.y >> 27), at);
+                const float* rp = rec + (8 * (size_t)(e.y & 0x7FFFFFFu) + oc) * REC_FLOATS;
+                float vv[REC_FLOATS];
+                ld_nc_v8(rp, vv);
+                ld_nc_v8(rp + 8, vv + 8);
+                ld_nc_v8(rp + 16, vv + 16);
+                float v[8][3];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[c][0] = vv[3 * c], v[c][1] = vv[3 * c + 1], v[c][2] = vv[3 * c + 2];
+                float o[3];
+                tri_sum<float>(at, v, o);
+                gr.u[i] = o[0];
+                gr.u[gr.n + i] = o[1];
+                gr.u[2 * gr.n + i] = o[2];
+                if (gr.host) gr.host[i] = (int)e.x;
+            } else if (active && !ok) {  // outside the cube: no host, no value
+                atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
+                const float nan = qnan<float>();
+                gr.u[i] = nan;
+                gr.u[gr.n + i] = nan;
+                gr.u[2 * gr.n + i] = nan;
+                if (gr.host) gr.host[i] = -1;
+            }
+            const bool cold = ok && !hot;
+            const unsigned m = __ballot_sync(0xffffffffu, cold);
+            if (cold) cq[qn + __popc(m & lt)] = ((long long)g << 40) | i;
+            qn += __popc(m);
+            __syncwarp();
+            if (qn >= 32) {
+                drain(32);
+                __syncwarp();
+                qn -= 32;
+                if (lane < qn) cq[lane] = cq[32 + lane];
+                __syncwarp();
+            }
+        }
+    }
+    if (qn > 0) drain(qn);
+}
+
 // Ordered copies of a group's positions: the i-th ordered point is point (pairs[i] & mask).
 __global__ void __launch_bounds__(256) k_gather_points(const uint64_t* __restrict__ pairs, int64_t n, uint64_t mask,
                                                        const double* __restrict__ x, const double* __restrict__ y,
@@ -136,6 +308,53 @@ unsigned grid_b(int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8));
 }
 
+// Cell entries, hot-leaf list and record buffer of a batch (synchronises the legacy stream;
+// batch creation is not stream-ordered work).  Leaves b->n_rec = 0 when no leaf is hot or the
+// ordinals would not fit the entry's 27 bits.
+ot_status build_hot_records(const ot_octree* t, int hot_l, ot_batch* b) {
+    const int64_t n = t->n;
+    uint32_t *flag = nullptr, *ord = nullptr, *tot = nullptr;
+    auto cleanup = [&]() {
+        if (flag) cudaFree(flag);
+        if (ord) cudaFree(ord);
+        if (tot) cudaFree(tot);
+    };
+    cudaStream_t s = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&flag, sizeof(uint32_t) * n)) != cudaSuccess || (e = cudaMalloc(&ord, sizeof(uint32_t) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&tot, sizeof(uint32_t))) != cudaSuccess) {
+        cleanup();
+        return cuda_status(e);
+    }
+    k_hot_flags<<<grid_b(n), 256, 0, s>>>(t->d_level, n, hot_l, flag);
+    count_launch();
+    ot_status st = scan_u32(flag, ord, n, tot, s);
+    uint32_t n_hot = 0;
+    if (st == OT_OK && (e = cudaMemcpy(&n_hot, tot, sizeof(uint32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        st = cuda_status(e);
+    if (st != OT_OK || n_hot == 0 || n_hot >= (1u << 27)) {
+        cleanup();
+        return st;
+    }
+    const int64_t ncell = (int64_t)1 << (3 * t->lmap_level);
+    if ((e = cudaMalloc(&b->d_hot_leaf, sizeof(int) * (size_t)n_hot)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_ent, sizeof(uint2) * (size_t)ncell)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_rec, sizeof(float) * REC_FLOATS * 8 * (size_t)n_hot)) != cudaSuccess) {
+        cleanup();
+        return cuda_status(e);
+    }
+    TreeView v = tree_view(t);
+    k_hot_list<<<grid_b(n), 256, 0, s>>>(flag, ord, n, b->d_hot_leaf);
+    k_cell_entries<<<grid_b(ncell), 256, 0, s>>>(v, ord, hot_l, b->d_ent);
+    count_launch(2);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return cuda_status(e);
+    b->n_rec = 8 * (int64_t)n_hot;
+    return OT_OK;
+}
+
 } // namespace ot
 
 using namespace ot;
@@ -151,6 +370,8 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     const int order_level = launch ? launch->order_level : 0;
     const int tri_tile = (launch && launch->tri_tile) ? launch->tri_tile : tile;
     const int tri_per_sm = (launch && launch->tri_blocks_per_sm) ? launch->tri_blocks_per_sm : 2;
+    const int tri_records = launch ? launch->tri_records : 0;
+    if (tri_records < -1 || tri_records > 1) return OT_ERR_ARG;
     if (block < 64 || block > 256 || block % 32 || tile < 1 || tile > 64) return OT_ERR_ARG;
     if (tri_tile < 1 || tri_tile > 64 || tri_per_sm < 1 || (launch && launch->blocks_per_sm < 0)) return OT_ERR_ARG;
     if (order_level < 0 || order_level > MAXLEVEL) return OT_ERR_ARG;
@@ -235,6 +456,7 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
         void* fn;
         BatchArgs args;
         unsigned grid;
+        bool records;  // k_tri_rec: two more arguments
     };
     std::vector<Launch> launches;
     auto add_launch = [&](void* fn, const BatchArgs& args, int cap) -> cudaError_t {
@@ -243,7 +465,7 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
         if (err != cudaSuccess) return err;
         if (cap > 0) per_sm = std::min(per_sm, cap);
         per_sm = std::max(per_sm, 1);
-        launches.push_back(Launch{fn, args, (unsigned)(num_sms() * per_sm)});
+        launches.push_back(Launch{fn, args, (unsigned)(num_sms() * per_sm), false});
         return cudaSuccess;
     };
     // every warp takes one tile number past the last tile before it stops: the 32-bit tile
@@ -277,8 +499,27 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
             if ((e = add_launch(fn, part[0], launch ? launch->blocks_per_sm : 0)) != cudaSuccess) return fail(e);
         }
         if (part[1].ng > 0) {
-            void* fn = learned ? (void*)k_batch<true, TRI_MINB, true, K_TRI> : (void*)k_batch<false, TRI_MINB, true, K_TRI>;
+            // value records of the hot leaves: leaves of level <= min(map level, hot level), where
+            // the hot level is the deepest whose leaves would receive at least 4 of the trilinear
+            // points if these were spread evenly over the cube (n 8^-l >= 4)
+            int64_t n_tri = 0;
+            for (int k = 0; k < part[1].ng; ++k) n_tri += part[1].g[k].n;
+            int hot_l = 0;
+            while (hot_l < MAXLEVEL && (n_tri >> (3 * (hot_l + 1))) >= 4) ++hot_l;
+            hot_l = std::min(hot_l, t->lmap_level);
+            if (tri_records >= 0 && t->d_lmap) {
+                ot_status st = build_hot_records(t, hot_l, b);
+                if (st != OT_OK) {
+                    ot_batch_destroy(b);
+                    return st;
+                }
+            }
+            const bool rec = b->n_rec > 0;
+            void* fn = rec ? (learned ? (void*)k_tri_rec<true> : (void*)k_tri_rec<false>)
+                           : (learned ? (void*)k_batch<true, TRI_MINB, true, K_TRI>
+                                      : (void*)k_batch<false, TRI_MINB, true, K_TRI>);
             if ((e = add_launch(fn, part[1], tri_per_sm)) != cudaSuccess) return fail(e);
+            launches.back().records = rec;
         }
     }
     if (!counter_fits()) {
@@ -307,9 +548,14 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
         count_launch();
     }
     if (cap_ok && has_tri) cap_ok = launch_pyramid<float>(t, d_field, b->d_pyr, cs) == OT_OK;
+    if (cap_ok && b->n_rec > 0) {
+        k_hot_records<<<grid_b(b->n_rec), 256, 0, cs>>>(v, b->d_hot_leaf, b->n_rec, d_field, b->d_pyr, b->d_rec);
+        count_launch();
+    }
     for (size_t i = 0; cap_ok && i < launches.size(); ++i) {
         unsigned* ctr = b->d_counter + i;
-        void* args[] = {&v, &launches[i].args, (void*)&d_field, (void*)&b->d_pyr, &ctr};
+        void* args[] = {&v, &launches[i].args, (void*)&d_field, (void*)&b->d_pyr, &ctr, (void*)&b->d_ent,
+                        (void*)&b->d_rec};
         cap_ok = cudaLaunchKernel(launches[i].fn, dim3(launches[i].grid), dim3(block), args, smem, cs) == cudaSuccess;
         count_launch();
     }
@@ -349,6 +595,9 @@ extern "C" ot_status ot_batch_destroy(ot_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_pyr) cudaFree(b->d_pyr);
+    if (b->d_ent) cudaFree(b->d_ent);
+    if (b->d_hot_leaf) cudaFree(b->d_hot_leaf);
+    if (b->d_rec) cudaFree(b->d_rec);
     for (void* p : b->bufs) cudaFree(p);
     delete b;
     return OT_OK;

@@ -353,6 +353,41 @@ __device__ __forceinline__ int trilinear_queued(const TreeView& t, const RootMod
     return h;
 }
 
+// Octant of the point with fixed-point coordinates X in its host leaf of level l (bit d: the
+// upper half on axis d) and the distances |t_d| of the point from the leaf's centre in cell
+// units (Sec. 2.3.2 trilinear weights).
+template <typename T>
+__device__ __forceinline__ int tri_octant(const uint64_t X[3], int l, T at[3]) {
+    int o = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        o |= (fix_upper_half(X[d], l) ? 1 : 0) << d;
+        const T td = fix_offset<T>(X[d], l);
+        at[d] = td < T(0) ? -td : td;
+    }
+    return o;
+}
+
+// The trilinear sum over the 8 level-mate values v (corner order: bit d of the corner set for
+// the neighbour on axis d), weights prod (1 - |t_d|) or |t_d|, accumulated in corner order.
+// Every form of the trilinear interpolation ends here, so their results are bit-identical.
+template <typename T>
+__device__ __forceinline__ void tri_sum(const T at[3], const T v[8][3], T out[3]) {
+    T acc0 = T(0), acc1 = T(0), acc2 = T(0);
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+        T wc = T(1);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) wc *= ((corner >> d) & 1) ? at[d] : T(1) - at[d];
+        acc0 += wc * v[corner][0];
+        acc1 += wc * v[corner][1];
+        acc2 += wc * v[corner][2];
+    }
+    out[0] = acc0;
+    out[1] = acc1;
+    out[2] = acc2;
+}
+
 // The same interpolation with the level-mates read from the octree's level-mate table (built
 // by ot_octree_build_mates): host leaf h of level l, octant o of its cell (bit d: the upper
 // half on axis d), then row 8h + o gives the 8 value slots -- a leaf index, or (top bit set)
@@ -373,38 +408,19 @@ __device__ __forceinline__ int trilinear_mates(const TreeView& t, const RootMode
         return -1;
     }
     const int l = hl >= 0 ? hl : (int)t.level[h];
-    int o = 0;
     T at[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        o |= (fix_upper_half(X[d], l) ? 1 : 0) << d;
-        const T td = fix_offset<T>(X[d], l);
-        at[d] = td < T(0) ? -td : td;
-    }
+    const int o = tri_octant<T>(X, l, at);
     const uint4* row = t.mates + 2 * (8 * (long long)h + o);
     const uint4 r0 = __ldg(row), r1 = __ldg(row + 1);
     const uint32_t sl[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-    T v[8][3], wt[8];
+    T v[8][3];
 #pragma unroll
     for (int corner = 0; corner < 8; ++corner) {
-        T wc = T(1);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) wc *= ((corner >> d) & 1) ? at[d] : T(1) - at[d];
-        wt[corner] = wc;
         const uint32_t sv = sl[corner];
         const auto f = V::load((sv >> 31) ? pyr : field, (long long)(sv & 0x7FFFFFFFu));
         v[corner][0] = f.x, v[corner][1] = f.y, v[corner][2] = f.z;
     }
-    T acc0 = T(0), acc1 = T(0), acc2 = T(0);
-#pragma unroll
-    for (int corner = 0; corner < 8; ++corner) {
-        acc0 += wt[corner] * v[corner][0];
-        acc1 += wt[corner] * v[corner][1];
-        acc2 += wt[corner] * v[corner][2];
-    }
-    out[0] = acc0;
-    out[1] = acc1;
-    out[2] = acc2;
+    tri_sum<T>(at, v, out);
     return h;
 }
 

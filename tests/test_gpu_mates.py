@@ -141,7 +141,8 @@ def test_batch_bit_identical_every_shape(ot, deep, search):
     M = c[:, None] + sph[0, 3] * dirs / np.linalg.norm(dirs, axis=0)
     mx, my, mz = pts(M)
     shapes = [dict(), dict(blocks_per_sm=2), dict(block=128, tile=1), dict(order_level=8, tile=8),
-              dict(tri_tile=1, tri_blocks_per_sm=1), dict(tile=2, tri_tile=8, tri_blocks_per_sm=4)]
+              dict(tri_tile=1, tri_blocks_per_sm=1), dict(tile=2, tri_tile=8, tri_blocks_per_sm=4),
+              dict(tri_records=-1), dict(tri_records=-1, order_level=8)]
 
     def run():
         outs = []
@@ -165,6 +166,48 @@ def test_batch_bit_identical_every_shape(ot, deep, search):
     ref = ot.ot_interpolate(t, ot.OT_TRILINEAR, x, y, z, f32)
     assert torch.equal(mates[0][0], ref)
     assert np.array_equal(mates[0][1].cpu().numpy(), oracle.locate_ub(ko, lo, *P.T))
+
+
+@pytest.mark.parametrize("search", [0, 1])
+@pytest.mark.parametrize("map_level", [5, 7])
+def test_value_records_bit_identical(ot, deep, search, map_level):
+    """Uniform points (most of them in coarse leaves, which get value records) give the same
+    results with and without the records, in the caller's order and Morton-ordered, and match
+    the oracle; points outside the cube get no host and NaN values either way."""
+    import torch
+    sph, ko, lo, _, field = deep
+    t = ot.ot_octree_build(sph, 3, 9)
+    ot.ot_octree_set_map_level(t, map_level)
+    if search == 1:
+        ot.ot_index_train(t, root=ot.OT_ROOT_MLP, n_leaf_models=4096, epochs=1, batch=16384)
+    ot.ot_octree_build_mates(t, True)
+    rng = np.random.default_rng(77)
+    P = np.concatenate([rng.uniform(0, 1, (300000, 3)), face_points(ko, lo, rng, 4000),
+                        np.array([[1.0, 0.5, 0.5], [0.5, -1e-9, 0.5], [np.nan, 0.5, 0.5]])])
+    x, y, z = pts(P.T)
+    f32 = dev(field.astype(np.float32))
+    outs = []
+    for lp in (dict(tri_records=-1), dict(), dict(tile=8, tri_tile=4), dict(order_level=6)):
+        up = torch.full((3, P.shape[0]), 7.0, device="cuda")
+        hp = torch.full((P.shape[0],), -5, dtype=torch.int32, device="cuda")
+        b = ot.ot_batch_create(t, [dict(kernel=ot.OT_TRILINEAR, x=x, y=y, z=z, u=up, host=hp)], f32, search=search,
+                               launch=lp)
+        ot.ot_batch_run(b)
+        torch.cuda.synchronize()
+        ot.ot_batch_destroy(b)
+        outs.append((up, hp))
+    for up, hp in outs[1:]:
+        assert torch.equal(hp, outs[0][1])
+        assert torch.equal(up.isnan(), outs[0][0].isnan())
+        assert torch.equal(torch.nan_to_num(up, nan=0.0), torch.nan_to_num(outs[0][0], nan=0.0))
+    hp = outs[1][1].cpu().numpy()
+    href = oracle.locate_ub(ko, lo, *P.T)
+    assert np.array_equal(hp, href)
+    inside = href >= 0
+    assert inside.sum() == P.shape[0] - 3
+    ref = oracle.interp_trilinear(ko, lo, field.astype(np.float32).astype(np.float64), *P[inside].T, href[inside])
+    assert rel_err(outs[1][0].cpu().numpy()[:, inside], ref) <= TOL32
+    assert torch.isnan(outs[1][0][:, ~torch.as_tensor(inside, device="cuda")]).all()
 
 
 def test_uniform_and_random_trees(ot):

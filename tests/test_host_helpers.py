@@ -43,7 +43,7 @@ def test_order_markers_permutes_every_marker_array():
 
 def test_launch_record_round_trip():
     import paper_2605_20565_gb300 as ot
-    d = dict(block=128, tile=2, blocks_per_sm=3, order_level=8, tri_tile=4, tri_blocks_per_sm=6)
+    d = dict(block=128, tile=2, blocks_per_sm=3, order_level=8, tri_tile=4, tri_blocks_per_sm=6, tri_records=-1)
     assert ot._Launch.of(d).as_dict() == d
     assert ot._Launch.of({}).as_dict() == {k: 0 for k in d}  # library defaults
 
