@@ -32,7 +32,7 @@ class Tracker:
     def __init__(self, w: synth.Workload, search: int = 1, rebuild_every: int = 10, tau_steps: float = 10.0,
                  re_coef: float = 0.0, n_leaf_models: int = 1 << 18, n_mid_models: int = 4096, device=None,
                  sort_points: bool = True, mates: bool = True, map_level: int | None = None,
-                 launch: dict | None = None, autotune: bool = True):
+                 launch: dict | None = None, autotune: bool = True, dt: float | None = None):
         import torch
         from . import OT_PESKIN4, OT_SORTED, OT_TRILINEAR
         self.torch = torch
@@ -95,8 +95,10 @@ class Tracker:
             self.launch = r["launch"]
             self.tuned = r
             self.batch = ot.ot_batch_create(self.tree, groups, self.field, search=self.search, launch=self.launch)
-        umax = float(self.field[:, :3].abs().max())
-        self.dt = self.h / max(umax, 1e-12)
+        if dt is None:
+            umax = float(self.field[:, :3].abs().max())
+            dt = self.h / max(umax, 1e-12)
+        self.dt = dt
         self.tau = tau_steps * self.dt
 
     def spheres_now(self) -> np.ndarray:
@@ -106,6 +108,12 @@ class Tracker:
     def _place_markers(self):
         c = self.torch.as_tensor(self.centres0 + self.vel * self.t, device=self.dev)  # (B, 3)
         self.mx.copy_(c[self.m_grp].T + self.m_off)
+
+    def markers_at(self, t: float) -> np.ndarray:
+        """The markers' positions (3, n) at time t in the input order, computed on the host from
+        the input positions and the bubble velocities (rigid translation)."""
+        w = self.w
+        return w.markers + (self.vel[w.marker_group] * t).T
 
     def _reorder(self):
         """Store the particles in Morton order of their cells (neighbouring particles share host
@@ -135,7 +143,9 @@ class Tracker:
             t = mark("reorder", t)
         prev = (ot.ot_index_get_root_params(self.tree)
                 if self.search == ot.OT_LEARNED and getattr(self, "tree", None) is not None else None)
-        self.tree = ot.ot_octree_build(self.spheres_now(), w.lmin, w.lmax)
+        # the spheres, time and step of this octree (for checks against an independent build)
+        self.tree_spheres, self.tree_time, self.tree_step = self.spheres_now(), self.t, self.step_no
+        self.tree = ot.ot_octree_build(self.tree_spheres, w.lmin, w.lmax)
         if self.map_level is not None:
             ot.ot_octree_set_map_level(self.tree, self.map_level)
         t = mark("octree_build", t)
