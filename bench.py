@@ -55,7 +55,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--launch", default="", help="block,tile,blocks_per_sm[,order_level[,tri_tile,tri_blocks_per_sm]]")
+    p.add_argument("--launch", default="",
+                   help="block,tile,blocks_per_sm[,order_level[,tri_tile,tri_blocks_per_sm[,tri_records]]]")
     p.add_argument("--map-level", type=int, default=None, help="level of the level map (default: autotuned)")
     p.add_argument("--no-autotune", action="store_true", help="default launch shape and level map")
     p.add_argument("--no-nomap", action="store_true", help="skip the forms without a level map")
@@ -66,6 +67,11 @@ def parse():
                    help="skip the informative form with the particles stored in Morton order")
     p.add_argument("--no-mates", action="store_true",
                    help="search the trilinear level-mates per query instead of reading the level-mate table")
+    p.add_argument("--only", action="store_true",
+                   help="the headline workload only (no compact lines of the other workloads)")
+    p.add_argument("--workloads", default="single_bubble,learned_index,tracking",
+                   help="the other workloads measured after the many-bubble headline (compact lines)")
+    p.add_argument("--tracking-steps", type=int, default=100, help="timed steps of the tracking workload")
     return p.parse_args()
 
 
@@ -272,32 +278,71 @@ def run_reference(args):
 # GPU path
 # ---------------------------------------------------------------------------------------
 
-def run_ours(args):
+def launch_of(text: str):
+    if not text:
+        return None
+    vals = [int(v) for v in text.split(",")]
+    return dict(zip(("block", "tile", "blocks_per_sm", "order_level", "tri_tile", "tri_blocks_per_sm",
+                     "tri_records"), vals))
+
+
+_ORACLE_TREES = {}
+
+
+def oracle_tree(w):
+    """The oracle's octree of a workload's spheres (kept for workloads that share them)."""
+    import oracle
+    key = (w.spheres.tobytes(), w.lmin, w.lmax)
+    if key not in _ORACLE_TREES:
+        t0 = time.time()
+        ko, lo = oracle.octree_build(w.spheres, w.lmin, w.lmax)
+        _ORACLE_TREES[key] = (ko, lo, time.time() - t0)
+    return _ORACLE_TREES[key]
+
+
+def synthetic_field32(w, ko, lo, dev):
+    """The workload's velocity field at the oracle's leaf centres, rounded to FP32 once: the one
+    array both the GPU path and the oracle read in the parity legs (an input, made by the
+    workload generator, not by the library under test)."""
+    import torch
+    import oracle
+    from paper_2605_20565_gb300 import synth
+    cen = oracle.leaf_centres(ko, lo)
+    if w.modes is None:
+        return torch.as_tensor(synth.sin_field(cen), device=dev).to(torch.float32).contiguous()
+    f = synth.fourier_field(w.modes, torch.as_tensor(cen, device=dev))
+    return f.to(torch.float32).contiguous()
+
+
+def gpu_numa_cpus(index: int):
+    """Host CPUs of the NUMA node the GPU hangs off (empty when the system does not say)."""
+    try:
+        bus = subprocess.run(["nvidia-smi", f"--id={index}", "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{dom[-4:].lower()}:{rest.lower()}/numa_node"
+        node = int(open(path).read().strip())
+        if node < 0:
+            return node, []
+        cpus = []
+        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            a, _, b = part.partition("-")
+            cpus.extend(range(int(a), int(b or a) + 1))
+        return node, cpus
+    except (OSError, ValueError, subprocess.SubprocessError):
+        return None, []
+
+
+def measure(args, name, light, ctx):
+    """One workload through the batched launch: timed steps, e2e with host buffers, the other
+    search forms, and the parity and CPU-baseline legs.  Returns the result dict."""
     import torch
     import paper_2605_20565_gb300 as ot
-    from paper_2605_20565_gb300 import _build, synth
+    from paper_2605_20565_gb300 import synth
+    dist, world, rank, local, dev = ctx["dist"], ctx["world"], ctx["rank"], ctx["local"], ctx["dev"]
+    barrier = ctx["barrier"]
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        dist = None
-        torch.cuda.set_device(0)
-    if rank == 0 or not os.path.exists(_build.LIB):
-        _build.build()
-    if dist:
-        dist.barrier()
-    dev = torch.device("cuda", local)
-
-    def barrier():
-        if dist:
-            dist.barrier()
-
-    w = make_workload(args.workload, args.scale, rank)
+    w = make_workload(name, args.scale, rank)
     if not args.markers_as_generated:
         synth.order_markers(w)  # the stored marker order: per bubble, Morton order of positions
     t0 = time.time()
@@ -341,51 +386,58 @@ def run_ours(args):
     Fm = torch.as_tensor(np.ascontiguousarray(w.forces, dtype=np.float32), device=dev)
     n_m, n_p = w.markers.shape[1], w.particles.shape[1]
     npts = n_m + n_p
+    # every located point's outputs: its velocity (3 planes) and its host leaf
     um = torch.empty((3, n_m), dtype=torch.float32, device=dev)
     up = torch.empty((3, n_p), dtype=torch.float32, device=dev)
+    hm = torch.empty(n_m, dtype=torch.int32, device=dev)
+    hp = torch.empty(n_p, dtype=torch.int32, device=dev)
     f = torch.zeros((n_leaves, 4), dtype=torch.float32, device=dev)
     mode = ot.OT_SORTED if args.spread == "sorted" else ot.OT_ATOMIC
     ws_bytes = ot.ot_spread_workspace_size(tree, ot.OT_PESKIN4, n_m) if mode == ot.OT_SORTED else 0
     ws = torch.empty(max(1, ws_bytes), dtype=torch.uint8, device=dev)
-    launch = None
-    if args.launch:
-        vals = [int(v) for v in args.launch.split(",")]
-        launch = dict(zip(("block", "tile", "blocks_per_sm", "order_level", "tri_tile", "tri_blocks_per_sm"), vals))
-    groups = [dict(kernel=ot.OT_PESKIN4, x=mx, y=my, z=mz, u=um), dict(kernel=ot.OT_TRILINEAR, x=px, y=py, z=pz, u=up)]
+    launch = launch_of(args.launch)
+
+    def groups_for(m_, p_, um_, up_, hm_, hp_):
+        return [dict(kernel=ot.OT_PESKIN4, x=m_[0], y=m_[1], z=m_[2], u=um_, host=hm_),
+                dict(kernel=ot.OT_TRILINEAR, x=p_[0], y=p_[1], z=p_[2], u=up_, host=hp_)]
+
+    groups = groups_for((mx, my, mz), (px, py, pz), um, up, hm, hp)
     stream = torch.cuda.current_stream()
 
     # search forms over the same groups: (search, level-map level, launch shape, level-mate
     # table).  "plain" and "learned" are autotuned (launch shape and level-map level) unless a
-    # launch or map level is given; the "_nomap" forms search the whole key array (level map of
-    # one cell), the plain one being Algorithm 1's binary search and the learned one the index
-    # without any map; "plain_search" searches every trilinear level-mate per query.
+    # launch or map level is given; "learned_same_staging" is the learned index with the plain
+    # form's level map, table and launch shape (the like-for-like comparison); the "_nomap"
+    # forms search the whole key array (a level map of one cell), the plain one being
+    # Algorithm 1's binary search; "plain_search" searches every level-mate per query.
     base_level = ot.ot_octree_get_map_level(tree)
     use_mates = not args.no_mates
     forms_cfg, tune = {}, {}
-    for name, sv in (("plain", ot.OT_BINARY), ("learned", ot.OT_LEARNED)):
+    for fname, sv in (("plain", ot.OT_BINARY), ("learned", ot.OT_LEARNED)):
         if launch is None and not args.no_autotune:
             r = ot.ot_batch_autotune(tree, groups, field, search=sv, tune_map_level=args.map_level is None, reps=2)
-            tune[name] = r
-            forms_cfg[name] = (sv, r["map_level"], r["launch"], use_mates)
+            tune[fname] = r
+            forms_cfg[fname] = (sv, r["map_level"], r["launch"], use_mates)
         else:
-            forms_cfg[name] = (sv, base_level, launch, use_mates)
-    if use_mates:
+            forms_cfg[fname] = (sv, base_level, launch, use_mates)
+    forms_cfg["learned_same_staging"] = (ot.OT_LEARNED,) + forms_cfg["plain"][1:]
+    if use_mates and not light:
         forms_cfg["plain_search"] = (ot.OT_BINARY,) + forms_cfg["plain"][1:3] + (False,)
-    if not args.no_nomap:
+    if not args.no_nomap and not light:
         forms_cfg["plain_nomap"] = (ot.OT_BINARY, 0, launch, use_mates)
         forms_cfg["learned_nomap"] = (ot.OT_LEARNED, 0, launch, use_mates)
 
-    def set_form(name):
-        sv, lvl, lp, mt = forms_cfg[name]
+    def set_form(fname):
+        sv, lvl, lp, mt = forms_cfg[fname]
         if ot.ot_octree_get_map_level(tree) != lvl:
             ot.ot_octree_set_map_level(tree, lvl)
         if ot.ot_octree_has_mates(tree) != mt:
             ot.ot_octree_build_mates(tree, mt)
         return sv, lp
 
-    def make_batch(name):
-        sv, lp = set_form(name)
-        return ot.ot_batch_create(tree, groups, field, search=sv, launch=lp)
+    def make_batch(fname, gs=None):
+        sv, lp = set_form(fname)
+        return ot.ot_batch_create(tree, gs or groups, field, search=sv, launch=lp)
 
     def step(batch, ev=None):
         if ev:
@@ -415,10 +467,10 @@ def run_ours(args):
 
     if args.search == "auto":
         cal = {}
-        for name in ("plain", "learned"):
-            bb = make_batch(name)
+        for fname in ("plain", "learned"):
+            bb = make_batch(fname)
             warm(bb)
-            cal[name] = time_steps(bb, 3)["step_ms"]
+            cal[fname] = time_steps(bb, 3)["step_ms"]
             del bb
         chosen = min(cal, key=cal.get)
     else:
@@ -429,7 +481,8 @@ def run_ours(args):
     ot.ot_index_get_stats(tree, reset=True)
 
     # timed region: the chosen form
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    steps = args.steps if not light else max(3, min(args.steps, 10))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
     clocks = Clocks(local) if rank == 0 else None
     barrier()
     torch.cuda.synchronize()
@@ -437,7 +490,7 @@ def run_ours(args):
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
     start.record(stream)
-    for k in range(args.steps):
+    for k in range(steps):
         step(batch, evs[k])
     stop.record(stream)
     torch.cuda.synchronize()
@@ -446,113 +499,297 @@ def run_ours(args):
     launches = ot.ot_launch_count() - launches0
     clk = clocks.stop() if clocks else None
     total_ms = max_over_ranks(start.elapsed_time(stop), dist, dev)
-    ms_step = total_ms / args.steps
+    ms_step = total_ms / steps
     batch_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     spread_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
     value = job_value(npts, world, ms_step)
     fb = ot.ot_index_get_stats(tree, reset=True)["fallbacks"] if chosen == "learned" else None
-    search = forms_cfg[chosen][0]
-    # end to end through the public API with host buffers
+
     e2e = None
     if not args.no_e2e:
-        hm = [torch.from_numpy(np.ascontiguousarray(w.markers[d])).pin_memory() for d in range(3)]
-        hp = [torch.from_numpy(np.ascontiguousarray(w.particles[d])).pin_memory() for d in range(3)]
-        hum = torch.empty((3, n_m), dtype=torch.float32).pin_memory()
-        hup = torch.empty((3, n_p), dtype=torch.float32).pin_memory()
-        hf = torch.empty((n_leaves, 4), dtype=torch.float32).pin_memory()
-        h2d = sum(t.numel() * t.element_size() for t in hm + hp)
-        d2h = (hum.numel() + hup.numel() + hf.numel()) * 4
+        e2e = measure_e2e(args, ctx, w, tree, field, forms_cfg[chosen], groups_for, step, batch,
+                          (mx, my, mz), (px, py, pz), Fm, um, up, hm, hp, f, ws, mode, npts, light)
 
-        def e2e_step():
-            for d in range(3):
-                (mx, my, mz)[d].copy_(hm[d], non_blocking=True)
-                (px, py, pz)[d].copy_(hp[d], non_blocking=True)
-            step(batch)
-            hum.copy_(um, non_blocking=True)
-            hup.copy_(up, non_blocking=True)
-            hf.copy_(f, non_blocking=True)
+    mdf = bodies = None
+    if not light:
+        mdf, bodies = measure_extras(args, ctx, w, tree, field, (mx, my, mz), to_dev)
 
+    # the other forms, same steps (the chosen form's level map is restored afterwards)
+    forms = {chosen: {"step_ms": ms_step, "locate_interpolate_ms": batch_ms, "spread_ms": spread_ms}}
+    groups_t = {}
+    del batch
+    for fname in forms_cfg:
+        if fname != chosen:
+            bb = make_batch(fname)
+            warm(bb)
+            forms[fname] = time_steps(bb, steps)
+            del bb
+        if light:
+            continue
+        # per-group timing (markers only, particles only) at the form's settings
+        for gname, gsel in (("markers", groups[:1]), ("particles", groups[1:])):
+            sv, lp = set_form(fname)
+            bb = ot.ot_batch_create(tree, gsel, field, search=sv, launch=lp)
+            for _ in range(2):
+                ot.ot_batch_run(bb)
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            for _ in range(5):
+                ot.ot_batch_run(bb)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            groups_t[f"{gname}_{fname}_ms"] = a_.elapsed_time(b_) / 5
+            del bb
+    # informative, not `value`: the plain step with the particles stored in Morton order of
+    # their level-8 cells (the order the tracking driver keeps them in; sorted once, untimed)
+    morton = None
+    if not light and not args.no_morton_form and n_p > 0 and forms_cfg["plain"][3]:
+        set_form("plain")
+        perm = ot.ot_points_morton_order(px, py, pz).long()
+        sx, sy, sz = [a_.index_select(0, perm).contiguous() for a_ in (px, py, pz)]
+        del perm
+        up_m, hp_m = torch.empty_like(up), torch.empty_like(hp)
+        gs = [groups[0], dict(kernel=ot.OT_TRILINEAR, x=sx, y=sy, z=sz, u=up_m, host=hp_m)]
+        lp_m = ot.ot_batch_autotune(tree, gs, field, search=ot.OT_BINARY, tune_map_level=False, reps=2)["launch"]
+        bb = ot.ot_batch_create(tree, gs, field, search=ot.OT_BINARY, launch=lp_m)
+        warm(bb)
+        morton = time_steps(bb, steps)
+        morton.update(points_per_s=npts / (morton["step_ms"] / 1e3),
+                      locate_interpolate_points_per_s=npts / (morton["locate_interpolate_ms"] / 1e3), launch=lp_m,
+                      map_level=forms_cfg["plain"][1], search="binary", level_mates="table",
+                      particle_order="Morton order of level-8 cells")
+        del bb, sx, sy, sz, gs, up_m, hp_m
+    for fname, v_ in forms.items():
+        v_["points_per_s"] = npts / (v_["step_ms"] / 1e3)
+        v_["locate_interpolate_points_per_s"] = npts / (v_["locate_interpolate_ms"] / 1e3)
+        v_["search"] = "learned" if forms_cfg[fname][0] == ot.OT_LEARNED else "binary"
+        v_["map_level"] = forms_cfg[fname][1]
+        v_["launch"] = forms_cfg[fname][2]
+        v_["level_mates"] = "table" if forms_cfg[fname][3] else "searched per query"
+
+    def ratio(a, b):
+        return {"locate_interpolate": forms[a]["locate_interpolate_ms"] / forms[b]["locate_interpolate_ms"],
+                "step": forms[a]["step_ms"] / forms[b]["step_ms"]}
+
+    # the target: the learned batched form >= 1.5x the plain form, like for like (same level
+    # map, table and launch shape); the autotuned pair and the whole-array comparisons are context
+    same = ratio("plain", "learned_same_staging")
+    learned_vs_plain = {"same_staging": same, "target": 1.5,
+                        "target_met": bool(same["locate_interpolate"] >= 1.5),
+                        "autotuned_forms": ratio("plain", "learned")}
+    if "plain_nomap" in forms:
+        learned_vs_plain["context_learned_vs_whole_array_binary"] = ratio("plain_nomap", "learned")
+        learned_vs_plain["context_without_level_map"] = ratio("plain_nomap", "learned_nomap")
+    if "plain_search" in forms:
+        learned_vs_plain["context_table_vs_search_plain_step"] = forms["plain_search"]["step_ms"] / forms["plain"]["step_ms"]
+    if morton:
+        forms["plain_particles_morton"] = morton
+    set_form(chosen)
+
+    peak, peak_kind = measured_peaks()
+    alg_bytes = npts * BYTES_PER_POINT + n_leaves * BYTES_PER_LEAF
+    achieved = alg_bytes / (batch_ms / 1e3) / 1e9
+    traffic, traffic_src = batch_traffic(w.name, chosen, forms_cfg[chosen][1], forms_cfg[chosen][3])
+    roof = {"bound": "hbm", "kernel": "batch graph replay (cell means, value records, k_batch delta-kernel launch, "
+                                      "trilinear launch): locate + interpolate of every point",
+            "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+            "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(alg_bytes),
+            "bytes_rule": f"{BYTES_PER_POINT} B/point + {BYTES_PER_LEAF} B/leaf"}
+
+    cpu = parity = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, parity = parity_and_baseline(args, w, tree, field, forms_cfg, make_batch, groups_for, chosen,
+                                          (mx, my, mz), (px, py, pz), Fm, dev, light)
+        set_form(chosen)
+
+    out = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": dict(describe(w, n_leaves, INDEX_DESC[args.index] if chosen == "learned" else
+                                   "plain: level map + subtree descriptors"),
+                          form=chosen, map_level=forms_cfg[chosen][1], launch=forms_cfg[chosen][2],
+                          level_mates="table" if forms_cfg[chosen][3] else "searched per query",
+                          marker_order=("as generated (Fibonacci spiral per bubble)" if args.markers_as_generated
+                                        else "per bubble, Morton order of level-10 cells"),
+                          particle_order="as generated"),
+           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": int(launches), "clocks": clk,
+           "breakdown_ms": {"locate_interpolate": batch_ms, "spread": spread_ms, "step": ms_step},
+           "locate_interpolate_points_per_s": world * npts / (batch_ms / 1e3),
+           "forms": forms, "learned_vs_plain": learned_vs_plain, "groups_ms": groups_t, "autotune": tune,
+           "mdf": mdf, "body_momenta": bodies,
+           "index": {"n_mid": n_mid, "n_leaf": n_leaf, "mean_window": istats["mean_window"],
+                     "max_window": istats["max_window"], "empty_models": istats["empty_models"],
+                     "fallbacks_timed": fb, "mean_probes": istats["mean_probes"],
+                     "final_loss": istats["final_loss"], "train_s": train_s},
+           "setup_s": {"octree_build": build_s, "index_train": train_s, "level_mate_table": mates_s},
+           "parity": parity}
+    return out
+
+
+def measure_e2e(args, ctx, w, tree, field, form_cfg, groups_for, step, batch, M, P, Fm, um, up, hm, hp, f, ws, mode,
+                npts, light):
+    """The step through the public API with host buffers: every step uploads its marker and
+    particle positions and marker forces from pinned host memory and downloads every point's
+    velocity and host leaf and the spread force field.  Pinned buffers are first touched by a
+    thread bound to the GPU's NUMA node.  Also the copy-only bandwidth of those transfers."""
+    import torch
+    import paper_2605_20565_gb300 as ot
+    dist, world, dev, barrier, local = ctx["dist"], ctx["world"], ctx["dev"], ctx["barrier"], ctx["local"]
+    stream = torch.cuda.current_stream()
+    node, cpus = gpu_numa_cpus(local)
+    old_aff = None
+    if cpus:
+        try:
+            old_aff = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, cpus)
+        except OSError:
+            old_aff = None
+    try:
+        hmk = [torch.from_numpy(np.ascontiguousarray(w.markers[d])).pin_memory() for d in range(3)]
+        hpt = [torch.from_numpy(np.ascontiguousarray(w.particles[d])).pin_memory() for d in range(3)]
+        hF = torch.from_numpy(np.ascontiguousarray(w.forces, dtype=np.float32)).pin_memory()
+    finally:
+        if old_aff is not None:
+            os.sched_setaffinity(0, old_aff)
+    mx, my, mz = M
+    px, py, pz = P
+    n_m, n_p = mx.numel(), px.numel()
+    n_leaves = f.shape[0]
+    h2d = sum(t.numel() * t.element_size() for t in hmk + hpt + [hF])
+    d2h = (um.numel() + up.numel() + f.numel()) * 4 + (hm.numel() + hp.numel()) * 4
+    k_e2e = 3 if light else max(3, min(args.steps, 10))
+
+    def outs_host():
+        return (torch.empty((3, n_m), dtype=torch.float32).pin_memory(),
+                torch.empty((3, n_p), dtype=torch.float32).pin_memory(),
+                torch.empty(n_m, dtype=torch.int32).pin_memory(), torch.empty(n_p, dtype=torch.int32).pin_memory(),
+                torch.empty((n_leaves, 4), dtype=torch.float32).pin_memory())
+
+    h_um, h_up, h_hm, h_hp, h_f = outs_host()
+
+    def upload(m_, p_, F_, s=None):
+        for d in range(3):
+            m_[d].copy_(hmk[d], non_blocking=True)
+            p_[d].copy_(hpt[d], non_blocking=True)
+        F_.copy_(hF, non_blocking=True)
+
+    def download(dst, src):
+        for a_, b_ in zip(dst, src):
+            a_.copy_(b_, non_blocking=True)
+
+    # copy-only bandwidth (no compute), each direction alone
+    a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    upload((mx, my, mz), (px, py, pz), Fm)
+    torch.cuda.synchronize()
+    a_.record(stream)
+    for _ in range(3):
+        upload((mx, my, mz), (px, py, pz), Fm)
+    b_.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = 3 * h2d / (a_.elapsed_time(b_) / 1e3) / 1e9
+    a_.record(stream)
+    for _ in range(3):
+        download((h_um, h_up, h_hm, h_hp, h_f), (um, up, hm, hp, f))
+    b_.record(stream)
+    torch.cuda.synchronize()
+    d2h_gbs = 3 * d2h / (a_.elapsed_time(b_) / 1e3) / 1e9
+
+    def e2e_step():
+        upload((mx, my, mz), (px, py, pz), Fm)
+        step(batch)
+        download((h_um, h_up, h_hm, h_hp, h_f), (um, up, hm, hp, f))
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
         e2e_step()
-        torch.cuda.synchronize()
-        k_e2e = max(3, min(args.steps, 10))
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(k_e2e):
-            e2e_step()
-        torch.cuda.synchronize()
-        barrier()
-        serial_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / k_e2e, dist, dev)
+    torch.cuda.synchronize()
+    barrier()
+    serial_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / k_e2e, dist, dev)
 
-        # Pipelined: two slots of device buffers (each with its own batch graph); step k computes
-        # on slot k % 2 while step k + 1's inputs go up and step k - 1's results come down on
-        # their own streams.  Every step still copies all its inputs and results.
-        class Slot:
-            pass
+    # Pipelined: two slots of device buffers (each with its own batch graph); step k computes
+    # on slot k % 2 while step k + 1's inputs go up and step k - 1's results come down on their
+    # own streams.  Every step still copies all its inputs and results.
+    class Slot:
+        pass
 
-        def make_slot(first):
-            sl = Slot()
-            if first:
-                sl.m, sl.p, sl.um, sl.up, sl.f, sl.ws, sl.batch = (mx, my, mz), (px, py, pz), um, up, f, ws, batch
-            else:
-                sl.m = tuple(torch.empty_like(a_) for a_ in (mx, my, mz))
-                sl.p = tuple(torch.empty_like(a_) for a_ in (px, py, pz))
-                sl.um, sl.up, sl.f, sl.ws = (torch.empty_like(um), torch.empty_like(up), torch.zeros_like(f),
-                                             torch.empty_like(ws))
-                sv_, _, lp_, _ = forms_cfg[chosen]
-                sl.batch = ot.ot_batch_create(tree, [dict(kernel=ot.OT_PESKIN4, x=sl.m[0], y=sl.m[1], z=sl.m[2], u=sl.um),
-                                                     dict(kernel=ot.OT_TRILINEAR, x=sl.p[0], y=sl.p[1], z=sl.p[2],
-                                                          u=sl.up)], field, search=sv_, launch=lp_)
-            sl.hum = torch.empty((3, n_m), dtype=torch.float32).pin_memory()
-            sl.hup = torch.empty((3, n_p), dtype=torch.float32).pin_memory()
-            sl.hf = torch.empty((n_leaves, 4), dtype=torch.float32).pin_memory()
-            sl.ev_in, sl.ev_comp, sl.ev_out = (torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event())
-            return sl
+    sv_, _, lp_, _ = form_cfg
 
-        slots = [make_slot(True), make_slot(False)]
-        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    def make_slot(first):
+        sl = Slot()
+        if first:
+            sl.m, sl.p, sl.F = (mx, my, mz), (px, py, pz), Fm
+            sl.um, sl.up, sl.hm, sl.hp, sl.f, sl.ws, sl.batch = um, up, hm, hp, f, ws, batch
+        else:
+            sl.m = tuple(torch.empty_like(x_) for x_ in (mx, my, mz))
+            sl.p = tuple(torch.empty_like(x_) for x_ in (px, py, pz))
+            sl.F = torch.empty_like(Fm)
+            sl.um, sl.up, sl.hm, sl.hp = (torch.empty_like(um), torch.empty_like(up), torch.empty_like(hm),
+                                          torch.empty_like(hp))
+            sl.f, sl.ws = torch.zeros_like(f), torch.empty_like(ws)
+            sl.batch = ot.ot_batch_create(tree, groups_for(sl.m, sl.p, sl.um, sl.up, sl.hm, sl.hp), field, search=sv_,
+                                          launch=lp_)
+        sl.h = outs_host()
+        sl.ev_in, sl.ev_comp, sl.ev_out = (torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event())
+        return sl
 
-        def piped_step(k):
-            sl = slots[k % 2]
-            with torch.cuda.stream(s_in):
-                s_in.wait_event(sl.ev_comp)  # the slot's previous step has read its inputs
-                for d in range(3):
-                    sl.m[d].copy_(hm[d], non_blocking=True)
-                    sl.p[d].copy_(hp[d], non_blocking=True)
-                sl.ev_in.record(s_in)
-            stream.wait_event(sl.ev_in)
-            stream.wait_event(sl.ev_out)  # the slot's previous results are on the host
-            ot.ot_batch_run(sl.batch)
-            sl.f.zero_()
-            ot.ot_spread(tree, ot.OT_PESKIN4, mode, sl.m[0], sl.m[1], sl.m[2], Fm, sl.f, workspace=sl.ws)
-            sl.ev_comp.record(stream)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(sl.ev_comp)
-                sl.hum.copy_(sl.um, non_blocking=True)
-                sl.hup.copy_(sl.up, non_blocking=True)
-                sl.hf.copy_(sl.f, non_blocking=True)
-                sl.ev_out.record(s_out)
+    slots = [make_slot(True), make_slot(False)]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
 
-        for k in range(2):
-            piped_step(k)
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        for k in range(k_e2e):
-            piped_step(k)
-        torch.cuda.synchronize()
-        barrier()
-        e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / k_e2e, dist, dev)
-        piped_ok = (torch.equal(slots[0].up, slots[1].up) and torch.equal(slots[0].f, slots[1].f)
-                    and torch.equal(slots[1].hup, slots[1].up.cpu()))
-        del slots
-        e2e = {"value": job_value(npts, world, e2e_ms), "unit": "points/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": k_e2e,
-               "pipeline": "2 slots; inputs up, compute, results down on three streams, overlapped across steps",
-               "pipelined_results_identical": bool(piped_ok),
-               "serial_ms_per_step": serial_ms, "serial_value": job_value(npts, world, serial_ms)}
+    def piped_step(k):
+        sl = slots[k % 2]
+        with torch.cuda.stream(s_in):
+            s_in.wait_event(sl.ev_comp)  # the slot's previous step has read its inputs
+            upload(sl.m, sl.p, sl.F)
+            sl.ev_in.record(s_in)
+        stream.wait_event(sl.ev_in)
+        stream.wait_event(sl.ev_out)  # the slot's previous results are on the host
+        ot.ot_batch_run(sl.batch)
+        sl.f.zero_()
+        ot.ot_spread(tree, ot.OT_PESKIN4, mode, sl.m[0], sl.m[1], sl.m[2], sl.F, sl.f, workspace=sl.ws)
+        sl.ev_comp.record(stream)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(sl.ev_comp)
+            download(sl.h, (sl.um, sl.up, sl.hm, sl.hp, sl.f))
+            sl.ev_out.record(s_out)
 
-    # multi-direct forcing (Sec. 2.2) on the same markers: 3 rounds towards a body at rest
-    mdf = None
+    for k in range(2):
+        piped_step(k)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(k_e2e):
+        piped_step(k)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / k_e2e, dist, dev)
+    piped_ok = (torch.equal(slots[0].up, slots[1].up) and torch.equal(slots[0].f, slots[1].f)
+                and torch.equal(slots[0].hp, slots[1].hp) and torch.equal(slots[1].h[1], slots[1].up.cpu()))
+    del slots
+    copy_ms = 1e3 * (h2d / (h2d_gbs * 1e9) + d2h / (d2h_gbs * 1e9))
+    return {"value": job_value(npts, world, e2e_ms), "unit": "points/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": k_e2e,
+            "pipeline": "2 slots; inputs up, compute, results down on three streams, overlapped across steps",
+            "pipelined_results_identical": bool(piped_ok),
+            "serial_ms_per_step": serial_ms, "serial_value": job_value(npts, world, serial_ms),
+            "copy_only": {"h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs, "ms_per_step_one_way_each": copy_ms,
+                          "pinned_numa_node": node, "pinned_first_touch_cpus": len(cpus)}}
+
+
+def measure_extras(args, ctx, w, tree, field, M, to_dev):
+    """Multi-direct forcing (Sec. 2.2) and the bodies' internal-fluid momenta (Sec. 2.3)."""
+    import torch
+    import paper_2605_20565_gb300 as ot
+    from paper_2605_20565_gb300 import synth
+    dev = ctx["dev"]
+    stream = torch.cuda.current_stream()
+    mx, my, mz = M
+    n_m = mx.numel()
+    mdf = bodies = None
     if not args.no_mdf and n_m > 0:
         U0 = torch.zeros((3, n_m), dtype=torch.float32, device=dev)
         # marker volumes dV_k = (S_b / N_b) h, the body's surface per marker times the finest cell
@@ -574,10 +811,6 @@ def run_ours(args):
                "slip_reduction": float(sl[-1] / sl[0]) if sl[0] > 0 else None,
                "note": "dV_k = (S_b / N_b) h; workspace allocation included; field sweeps over all leaves per round"}
         del um_, U0
-
-    # internal-fluid momenta of the bodies (Sec. 2.3): trilinear velocity at the internal markers
-    # (a lattice of the finest cell inside each bubble), then the per-body sums
-    bodies = None
     if not args.no_mdf and w.extra and "centres" in w.extra:
         hmin = 2.0 ** -w.lmax
         Xi, st_i = synth.internal_markers(w.extra["centres"], w.extra["diameters"], hmin)
@@ -585,9 +818,11 @@ def run_ours(args):
         d_start = torch.as_tensor(st_i, device=dev)
         xb = torch.as_tensor(np.ascontiguousarray(w.extra["centres"]), device=dev)
         ui = torch.empty((3, Xi.shape[1]), dtype=torch.float32, device=dev)
+        wsi = torch.empty(max(1, ot.ot_interpolate_workspace_size(tree, ot.OT_TRILINEAR)), dtype=torch.uint8,
+                          device=dev)
 
         def momenta():
-            ot.ot_interpolate(tree, ot.OT_TRILINEAR, xi, yi, zi, field, u=ui)
+            ot.ot_interpolate(tree, ot.OT_TRILINEAR, xi, yi, zi, field, u=ui, workspace=wsi)
             return ot.ot_body_sums(xi, yi, zi, ui, d_start, xb, 1.0, w=hmin ** 3)
 
         momenta()
@@ -600,160 +835,165 @@ def run_ours(args):
         bodies = {"bodies": int(len(st_i) - 1), "internal_markers": int(Xi.shape[1]),
                   "ms": a_.elapsed_time(b_) / 3, "what": "trilinear u at internal markers + per-body P and L"}
         del xi, yi, zi, ui
+    return mdf, bodies
 
-    # the other forms, same steps (the chosen form's level map is restored afterwards)
-    forms = {chosen: {"step_ms": ms_step, "locate_interpolate_ms": batch_ms, "spread_ms": spread_ms}}
-    groups_t = {}
-    del batch
-    for name in forms_cfg:
-        if name != chosen:
-            bb = make_batch(name)
-            warm(bb)
-            forms[name] = time_steps(bb, args.steps)
-            del bb
-        # per-group timing (markers only, particles only) at the form's settings
-        for gname, gsel in (("markers", groups[:1]), ("particles", groups[1:])):
-            sv, lp = set_form(name)
-            bb = ot.ot_batch_create(tree, gsel, field, search=sv, launch=lp)
-            for _ in range(2):
-                ot.ot_batch_run(bb)
-            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a_.record(stream)
-            for _ in range(5):
-                ot.ot_batch_run(bb)
-            b_.record(stream)
-            torch.cuda.synchronize()
-            groups_t[f"{gname}_{name}_ms"] = a_.elapsed_time(b_) / 5
-            del bb
-    # informative, not `value`: the plain step with the particles stored in Morton order of
-    # their level-8 cells (the order the tracking driver keeps them in; sorted once, untimed)
-    morton = None
-    if not args.no_morton_form and n_p > 0 and forms_cfg["plain"][3]:
-        set_form("plain")
-        perm = ot.ot_points_morton_order(px, py, pz).long()
-        sx, sy, sz = [a_.index_select(0, perm).contiguous() for a_ in (px, py, pz)]
-        del perm
-        up_m = torch.empty_like(up)  # its own outputs: `up` keeps the timed form's for the parity check
-        gs = [groups[0], dict(kernel=ot.OT_TRILINEAR, x=sx, y=sy, z=sz, u=up_m)]
-        lp_m = ot.ot_batch_autotune(tree, gs, field, search=ot.OT_BINARY, tune_map_level=False, reps=2)["launch"]
-        bb = ot.ot_batch_create(tree, gs, field, search=ot.OT_BINARY, launch=lp_m)
-        warm(bb)
-        morton = time_steps(bb, args.steps)
-        morton.update(points_per_s=npts / (morton["step_ms"] / 1e3),
-                      locate_interpolate_points_per_s=npts / (morton["locate_interpolate_ms"] / 1e3), launch=lp_m,
-                      map_level=forms_cfg["plain"][1], search="binary", level_mates="table",
-                      particle_order="Morton order of level-8 cells")
-        del bb, sx, sy, sz, gs, up_m
-    for name, v_ in forms.items():
-        v_["points_per_s"] = npts / (v_["step_ms"] / 1e3)
-        v_["locate_interpolate_points_per_s"] = npts / (v_["locate_interpolate_ms"] / 1e3)
-        v_["search"] = "learned" if forms_cfg[name][0] == ot.OT_LEARNED else "binary"
-        v_["map_level"] = forms_cfg[name][1]
-        v_["launch"] = forms_cfg[name][2]
-        v_["level_mates"] = "table" if forms_cfg[name][3] else "searched per query"
-    learned_vs_plain = {
-        "with_level_map": {
-            "locate_interpolate": forms["plain"]["locate_interpolate_ms"] / forms["learned"]["locate_interpolate_ms"],
-            "step": forms["plain"]["step_ms"] / forms["learned"]["step_ms"]}}
-    if "plain_nomap" in forms:
-        # the learned index with its level map against Algorithm 1's binary search of the whole
-        # key array (no staging of the top tree levels)
-        learned_vs_plain["learned_vs_whole_array_binary"] = {
-            "locate_interpolate": forms["plain_nomap"]["locate_interpolate_ms"] /
-            forms["learned"]["locate_interpolate_ms"],
-            "step": forms["plain_nomap"]["step_ms"] / forms["learned"]["step_ms"]}
-        learned_vs_plain["without_level_map"] = {
-            "locate_interpolate": forms["plain_nomap"]["locate_interpolate_ms"] /
-            forms["learned_nomap"]["locate_interpolate_ms"],
-            "step": forms["plain_nomap"]["step_ms"] / forms["learned_nomap"]["step_ms"]}
-    if "plain_search" in forms:
-        learned_vs_plain["table_vs_search_plain_step"] = forms["plain_search"]["step_ms"] / forms["plain"]["step_ms"]
-    if morton:
-        forms["plain_particles_morton"] = morton
-    set_form(chosen)
 
-    if rank != 0:
+def parity_and_baseline(args, w, tree, field, forms_cfg, make_batch, groups_for, chosen, M, P, Fm, dev, light):
+    """The oracle against the timed launch on a bounded sample, for BOTH search forms, with
+    one FP32 field (the workload's field at the oracle's leaf centres) fed to both sides;
+    the octree leaf set compared whole; the timed CPU baseline."""
+    import torch
+    import oracle
+    import paper_2605_20565_gb300 as ot
+    ko, lo, setup_s = oracle_tree(w)
+    kg, lg = ot.ot_octree_copy_leaves(tree)
+    tree_exact = bool(np.array_equal(kg.cpu().numpy().view(np.uint64), ko) and np.array_equal(lg.cpu().numpy(), lo))
+    del kg, lg
+    f32 = synthetic_field32(w, ko, lo, dev)
+    field.copy_(f32)  # the batches read `field`: every form now sees the synthetic FP32 field
+    fref = f32.double().cpu().numpy()
+    del f32
+    fscale = float(np.abs(fref[:, :3]).max())
+    n_ps, n_ms = size_cpu_sample(w, ko, lo, fref, args.cpu_seconds * (0.5 if light else 1.0))
+    dt, host_ref, up_ref, um_ref = oracle_step(w, ko, lo, fref, n_ps, n_ms)
+    cpu = {"value": (n_ps + n_ms) / dt, "unit": "points/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{n_ps} particles + {n_ms} markers of {w.name} (locate, interpolate, spread), "
+                     f"one step, {dt:.1f} s; oracle tree build {setup_s:.1f} s untimed"}
+    mhost_ref = oracle.locate_ub(ko, lo, *w.markers[:, :n_ms]) if n_ms else np.zeros(0, np.int32)
+    mx, my, mz = M
+    px, py, pz = P
+    n_m, n_p = mx.numel(), px.numel()
+    res, first = {}, None
+    for fname in ("plain", "learned"):
+        um_ = torch.empty((3, n_m), dtype=torch.float32, device=dev)
+        up_ = torch.empty((3, n_p), dtype=torch.float32, device=dev)
+        hm_ = torch.empty(n_m, dtype=torch.int32, device=dev)
+        hp_ = torch.empty(n_p, dtype=torch.int32, device=dev)
+        b = make_batch(fname, groups_for(M, P, um_, up_, hm_, hp_))
+        ot.ot_batch_run(b)
+        torch.cuda.synchronize()
+        del b
+        r = {"hosts_bit_exact": bool(np.array_equal(hp_[:n_ps].cpu().numpy(), host_ref) and
+                                     np.array_equal(hm_[:n_ms].cpu().numpy(), mhost_ref)),
+             "particles_max_rel_err": float(np.abs(up_[:, :n_ps].cpu().numpy() - up_ref).max() / fscale),
+             "markers_max_rel_err": (float(np.abs(um_[:, :n_ms].cpu().numpy() - um_ref).max() / fscale)
+                                     if n_ms else None)}
+        if first is None:
+            first = (up_, hp_, um_, hm_)
+        else:  # every point of the full workload: the two forms give the same bits
+            r["all_points_equal_plain_form"] = bool(torch.equal(up_, first[0]) and torch.equal(hp_, first[1]) and
+                                                    torch.equal(um_, first[2]) and torch.equal(hm_, first[3]))
+        res[fname] = r
+        del um_, up_, hm_, hp_
+    del first
+    # spreading of the sampled markers against the oracle's
+    spread = None
+    if n_ms:
+        fs = torch.zeros((tree_leaves(tree), 4), dtype=torch.float32, device=dev)
+        ot.ot_spread(tree, ot.OT_PESKIN4, ot.OT_SORTED, mx[:n_ms].contiguous(), my[:n_ms].contiguous(),
+                     mz[:n_ms].contiguous(), Fm[:, :n_ms].contiguous(), fs)
+        f_ref, _ = oracle.spread_delta(ko, lo, w.lmax, 2, *w.markers[:, :n_ms], w.forces[:, :n_ms].astype(np.float64))
+        spread = float(np.abs(fs[:, :3].cpu().numpy() - f_ref[:, :3]).max() / max(np.abs(f_ref[:, :3]).max(), 1e-300))
+        del fs
+    parity = {"octree_bit_exact": tree_exact, "forms": res, "spread_max_rel_err": spread,
+              "sampled_points": n_ps + n_ms, "tolerance": 1e-5,
+              "field": "the workload's field at the oracle's leaf centres in FP32, the same array on both sides",
+              "all_ok": bool(tree_exact and all(v["hosts_bit_exact"] and v["particles_max_rel_err"] <= 1e-5 and
+                                                (v["markers_max_rel_err"] or 0.0) <= 1e-5 and
+                                                v.get("all_points_equal_plain_form", True) for v in res.values())
+                             and (spread is None or spread <= 1e-5))}
+    return cpu, parity
+
+
+def tree_leaves(tree):
+    import paper_2605_20565_gb300 as ot
+    return ot.ot_octree_info(tree)[0]
+
+
+def compact(d):
+    """The fields of a secondary workload's line that the headline line carries."""
+    keep = ("value", "unit", "ms_per_step", "steps", "config", "roofline", "cpu_baseline", "e2e", "parity",
+            "learned_vs_plain", "breakdown_ms", "locate_interpolate_points_per_s", "gpu_launches", "clocks",
+            "step_parts_ms", "rebuild")
+    out = {k: d[k] for k in keep if k in d}
+    if "forms" in d:
+        out["forms"] = {k: {kk: v.get(kk) for kk in ("step_ms", "locate_interpolate_ms", "map_level", "search")}
+                        for k, v in d["forms"].items()}
+    return out
+
+
+def run_ours(args):
+    import torch
+    from paper_2605_20565_gb300 import _build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    if rank == 0 or not os.path.exists(_build.LIB):
+        _build.build()
+    if dist:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+
+    def barrier():
         if dist:
-            dist.destroy_process_group()
-        return 0
+            dist.barrier()
 
-    peak, peak_kind = measured_peaks()
-    alg_bytes = npts * BYTES_PER_POINT + n_leaves * BYTES_PER_LEAF
-    achieved = alg_bytes / (batch_ms / 1e3) / 1e9
-    traffic, traffic_src = batch_traffic(w.name, chosen, forms_cfg[chosen][1], forms_cfg[chosen][3])
-    roof = {"bound": "hbm", "kernel": "batch graph replay (cell means + k_batch delta-kernel launch + k_batch "
-                                      "trilinear launch): locate + interpolate of every point",
-            "achieved": achieved,
-            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
-            "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(alg_bytes),
-            "bytes_rule": f"{BYTES_PER_POINT} B/point + {BYTES_PER_LEAF} B/leaf"}
-
-    cpu = None
-    parity = None
-    if not args.no_cpu_baseline:
-        import oracle
-        ko, lo, fref, setup_s = oracle_setup(w)
-        kg, lg = ot.ot_octree_copy_leaves(tree)
-        tree_exact = bool(np.array_equal(kg.cpu().numpy().view(np.uint64), ko) and
-                          np.array_equal(lg.cpu().numpy(), lo))
-        n_ps, n_ms = size_cpu_sample(w, ko, lo, fref, args.cpu_seconds)
-        dt, host_ref, up_ref, um_ref = oracle_step(w, ko, lo, fref, n_ps, n_ms)
-        cpu = {"value": (n_ps + n_ms) / dt, "unit": "points/s", "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": f"{n_ps} particles + {n_ms} markers of {w.name} (locate, interpolate, spread), "
-                         f"one step, {dt:.1f} s; oracle tree build {setup_s:.1f} s untimed"}
-        # sampled parity of the timed launch's outputs (same field values, FP32 inputs)
-        fscale = float(np.abs(fref[:, :3]).max())
-        hp_gpu = ot.ot_locate(tree, px[:n_ps], py[:n_ps], pz[:n_ps], search=search).cpu().numpy()
-        parity = {"octree_bit_exact": tree_exact,
-                  "hosts_bit_exact": bool(np.array_equal(hp_gpu, host_ref)),
-                  "particles_max_rel_err": float(np.abs(up[:, :n_ps].cpu().numpy() - up_ref).max() / fscale),
-                  "markers_max_rel_err": (float(np.abs(um[:, :n_ms].cpu().numpy() - um_ref).max() / fscale)
-                                          if n_ms else None),
-                  "sampled_points": n_ps + n_ms}
-
-    out = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": dict(describe(w, n_leaves, INDEX_DESC[args.index] if chosen == "learned" else
-                                   "plain: level map + binary search"),
-                          form=chosen, map_level=forms_cfg[chosen][1], launch=forms_cfg[chosen][2],
-                          level_mates="table" if forms_cfg[chosen][3] else "searched per query",
-                          marker_order=("as generated (Fibonacci spiral per bubble)" if args.markers_as_generated
-                                        else "per bubble, Morton order of level-10 cells"),
-                          particle_order="as generated (uniform random)"),
-           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-           "gpu_launches": int(launches), "clocks": clk,
-           "breakdown_ms": {"locate_interpolate": batch_ms, "spread": spread_ms, "step": ms_step},
-           "locate_interpolate_points_per_s": world * npts / (batch_ms / 1e3),
-           "forms": forms, "learned_vs_plain": learned_vs_plain, "groups_ms": groups_t, "autotune": tune,
-           "mdf": mdf, "body_momenta": bodies,
-           "index": {"n_mid": n_mid, "n_leaf": n_leaf, "mean_window": istats["mean_window"], "max_window": istats["max_window"],
-                     "empty_models": istats["empty_models"], "fallbacks_timed": fb,
-                     "mean_probes": istats["mean_probes"],
-                     "final_loss": istats["final_loss"], "train_s": train_s},
-           "setup_s": {"octree_build": build_s, "index_train": train_s, "level_mate_table": mates_s},
-           "parity": parity}
-    print(json.dumps(out), flush=True)
+    ctx = dict(dist=dist, world=world, rank=rank, local=local, dev=dev, barrier=barrier)
+    t_run = time.time()
+    out = measure(args, args.workload, False, ctx)
+    print(f"[bench] {args.workload}: {time.time() - t_run:.1f} s", file=sys.stderr, flush=True)
+    torch.cuda.empty_cache()
+    # the other workloads, compact lines in the same run (rank 0 prints them with the headline)
+    others = [] if (args.only or args.workload != "many_bubbles" or world > 1) else \
+        [x for x in args.workloads.split(",") if x]
+    if others:
+        out["workloads"] = {}
+        for name in others:
+            t0 = time.time()
+            try:
+                if name == "tracking":
+                    d = run_tracking(args, light=True, ctx=ctx)
+                else:
+                    d = measure(args, name, True, ctx)
+                d = compact(d)
+            except Exception as exc:  # a secondary workload never takes the headline line down
+                d = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.empty_cache()
+            d["wall_s"] = time.time() - t0
+            print(f"[bench] {name}: {d['wall_s']:.1f} s", file=sys.stderr, flush=True)
+            out["workloads"][name] = d
+    if rank == 0:
+        print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
 
 
-def run_tracking(args):
+def run_tracking(args, light=False, ctx=None):
     """The time-stepped workload: 256 bubbles moving, 200M particles advected by AB2, markers
-    spread every step, octree rebuilt and index retrained every 10 steps (all timed)."""
+    spread every step, octree rebuilt (and, for the learned form, the index retrained) every 10
+    steps -- all inside the timed region.  Parity: the octree of the last re-adaptation against
+    the oracle's octree of the same moved spheres, and the GPU's locate, interpolation, spreading
+    and AB2 step on a sample of synthetic points against the oracle on the same inputs."""
     import torch
     import paper_2605_20565_gb300 as ot
     from paper_2605_20565_gb300 import _build, synth, tracking
-    torch.cuda.set_device(0)
-    _build.build()
+    if ctx is None:
+        torch.cuda.set_device(0)
+        _build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
     w = synth.tracking(n_particles=int(200_000_000 * args.scale))
     search = ot.OT_LEARNED if args.search == "learned" else ot.OT_BINARY
     t0 = time.time()
-    launch = None
-    if args.launch:
-        vals = [int(v) for v in args.launch.split(",")]
-        launch = dict(zip(("block", "tile", "blocks_per_sm", "order_level", "tri_tile", "tri_blocks_per_sm"), vals))
+    launch = launch_of(args.launch)
     tr = tracking.Tracker(w, search=search, rebuild_every=10, mates=not args.no_mates, map_level=args.map_level,
                           launch=launch)
     setup_s = time.time() - t0
@@ -762,38 +1002,145 @@ def run_tracking(args):
         tr.step()
     torch.cuda.synchronize()
     tr.timings = {"rebuild_s": 0.0, "rebuilds": 0}
+    steps = args.tracking_steps
     clocks = Clocks(0)
     launches0 = ot.ot_launch_count()
     t0 = time.perf_counter()
     pts = 0
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
-    for k in range(args.steps):
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+    for k in range(steps):
         pts += tr.step(evs[k])
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
+    launches = ot.ot_launch_count() - launches0
     parts = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs)
              for i, name in enumerate(("batch", "advect", "spread", "markers"))}
     clk = clocks.stop()
-    out = {"metric": METRIC, "value": pts / el, "unit": "points/s", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+    ms_step = 1e3 * el / steps
+    n_p, n_m = tr.x.shape[1], tr.mx.shape[1]
+    # e2e: the state stays on the device; each step a host reads the step's results a coupled
+    # solver needs -- the marker velocities and the spread force field -- from pinned memory
+    h_um = torch.empty_like(tr.um, device="cpu").pin_memory()
+    # the leaf count changes at every re-adaptation: a host buffer with room to spare
+    h_f = torch.empty((n_leaves + n_leaves // 5 + 1024, 4), dtype=torch.float32).pin_memory()
+    k_e2e = 10
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        tr.step()
+        nl = tr.f.shape[0]
+        h_um.copy_(tr.um, non_blocking=True)
+        h_f[:nl].copy_(tr.f, non_blocking=True)
+        d2h += h_um.numel() * 4 + nl * 16
+    torch.cuda.synchronize()
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / k_e2e
+    e2e = {"value": (n_p + n_m) / (e2e_ms / 1e3), "unit": "points/s", "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": int(d2h / k_e2e), "ms_per_step": e2e_ms, "steps": k_e2e,
+           "what": "state resident on the device (uploaded once); marker velocities and force field read back "
+                   "every step; re-adaptations inside"}
+    peak, peak_kind = measured_peaks()
+    # algorithmic bytes of one step: locate+interpolate (40 B/point + 21 B/leaf), AB2 (read x,
+    # v, a_prev, v_prev, u: 72 B; write x, v, a_prev, v_prev: 60 B per particle), spreading
+    # (position and force 36 B per marker in; the force field zeroed and accumulated, 16 B per
+    # leaf)
+    step_bytes = (n_p + n_m) * BYTES_PER_POINT + n_leaves * BYTES_PER_LEAF + n_p * 132 + n_m * 36 + n_leaves * 16
+    achieved = step_bytes / (ms_step / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "whole tracking step (batch, AB2 advection, sorted spreading, marker "
+                                      "motion; re-adaptations amortised)", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_step": int(step_bytes),
+            "bytes_rule": "40 B/point + 21 B/leaf + 132 B/particle (AB2) + 36 B/marker + 16 B/leaf (spread)"}
+    cpu = parity = None
+    if not args.no_cpu_baseline:
+        cpu, parity = tracking_parity(args, tr, w, dev, light)
+    out = {"metric": METRIC, "value": pts / el, "unit": "points/s", "n_gpus": 1, "steps": steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": w.name, "bubbles": int(w.spheres.shape[0]), "levels": [w.lmin, w.lmax],
-                      "leaves": int(n_leaves), "markers_peskin4": int(w.markers.shape[1]),
-                      "particles_trilinear": int(w.particles.shape[1]),
+                      "leaves": int(n_leaves), "markers_peskin4": int(n_m), "particles_trilinear": int(n_p),
                       "search": "learned" if search == ot.OT_LEARNED else "binary",
                       "level_mates": "searched per query" if args.no_mates else "table",
                       "map_level": ot.ot_octree_get_map_level(tr.tree),
                       "launch": tr.launch, "launch_autotuned": launch is None,
                       "step": "locate+interpolate all points, AB2 advect particles, sorted spread of markers; "
-                              "octree rebuild + index retrain + field resample every 10 steps",
+                              "octree rebuild (+ index retrain for the learned form) + field resample every 10 steps",
                       "l2": "inputs larger than L2; no flush"},
            "rebuild": {"rebuilds_timed": tr.timings["rebuilds"], "rebuild_s_timed": tr.timings["rebuild_s"],
                        "parts_s_timed": tr.timings.get("rebuild_parts_s"), "setup_s": setup_s},
-           "step_parts_ms": parts,
-           "gpu_launches": int(ot.ot_launch_count() - launches0), "clocks": clk,
-           "roofline": None, "cpu_baseline": None, "e2e": None}
-    print(json.dumps(out), flush=True)
-    return 0
+           "step_parts_ms": parts, "gpu_launches": int(launches), "clocks": clk,
+           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "parity": parity}
+    if ctx is None:
+        print(json.dumps(out), flush=True)
+    return out
+
+
+def tracking_parity(args, tr, w, dev, light):
+    """Oracle checks of the tracking workload's last re-adaptation on inputs that do not come
+    from the CUDA path: the moved spheres (octree), synthetic points (locate + trilinear), the
+    markers' rigidly moved positions (Peskin-4 interpolation and spreading), the workload's field
+    at the oracle's leaf centres in FP32 (both sides), and an AB2 step from a synthetic state."""
+    import torch
+    import oracle
+    import paper_2605_20565_gb300 as ot
+    t0 = time.time()
+    sph = tr.tree_spheres
+    ko, lo = oracle.octree_build(sph, w.lmin, w.lmax)
+    build_s = time.time() - t0
+    kg, lg = ot.ot_octree_copy_leaves(tr.tree)
+    tree_exact = bool(np.array_equal(kg.cpu().numpy().view(np.uint64), ko) and np.array_equal(lg.cpu().numpy(), lo))
+    del kg, lg
+    fld = synthetic_field32(w, ko, lo, dev)
+    fref = fld.double().cpu().numpy()
+    fscale = float(np.abs(fref[:, :3]).max())
+    # sample: synthetic uniform points and the markers at the re-adaptation's time
+    n_s = int(min(w.particles.shape[1], 2_000_000 if not light else 1_000_000))
+    P = np.ascontiguousarray(w.particles[:, :n_s])
+    Mk = tr.markers_at(tr.tree_time)
+    n_ms = int(min(Mk.shape[1], 200_000))
+    Mk = np.ascontiguousarray(Mk[:, :n_ms])
+    Fk = np.ascontiguousarray(w.forces[:, :n_ms], dtype=np.float32)
+    t1 = time.perf_counter()
+    host_ref = oracle.locate_ub(ko, lo, *P)
+    up_ref = oracle.interp_trilinear(ko, lo, fref, *P, host_ref)
+    um_ref, _ = oracle.interp_delta(ko, lo, w.lmax, 2, fref, *Mk)
+    f_ref, _ = oracle.spread_delta(ko, lo, w.lmax, 2, *Mk, Fk.astype(np.float64))
+    st = {"x": P.copy(), "v": np.zeros_like(P), "a_prev": np.zeros_like(P), "v_prev": np.zeros_like(P)}
+    oracle.advect_ab2(st, up_ref, tr.tau, tr.re_coef, tr.dt, True, periodic=True)
+    cpu_s = time.perf_counter() - t1
+    cpu = {"value": (n_s + n_ms) / cpu_s, "unit": "points/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{n_s} particles (locate, trilinear, AB2) + {n_ms} markers (Peskin-4 interpolation and "
+                     f"spreading) on the {ko.size}-leaf octree of the last re-adaptation, {cpu_s:.1f} s; oracle "
+                     f"octree build {build_s:.1f} s untimed"}
+    x, y, z = [torch.as_tensor(P[d], device=dev) for d in range(3)]
+    h = torch.empty(n_s, dtype=torch.int32, device=dev)
+    u = ot.ot_interpolate(tr.tree, ot.OT_TRILINEAR, x, y, z, fld, host_out=h)
+    mx_, my_, mz_ = [torch.as_tensor(Mk[d], device=dev) for d in range(3)]
+    um = ot.ot_interpolate(tr.tree, ot.OT_PESKIN4, mx_, my_, mz_, fld)
+    fs = torch.zeros_like(fld)
+    ot.ot_spread(tr.tree, ot.OT_PESKIN4, ot.OT_SORTED, mx_, my_, mz_, torch.as_tensor(Fk, device=dev), fs)
+    # one AB2 step from the same synthetic state with the oracle's velocities
+    xs = torch.as_tensor(P, device=dev).contiguous()
+    vs = torch.zeros((3, n_s), dtype=torch.float32, device=dev)
+    a0, v0 = torch.zeros_like(vs), torch.zeros_like(vs)
+    ot.ot_advect_ab2(xs, vs, a0, v0, torch.as_tensor(up_ref.astype(np.float32), device=dev), tr.tau, tr.re_coef,
+                     tr.dt, first=True, periodic=True)
+    torch.cuda.synchronize()
+    dx = np.abs(xs.cpu().numpy() - st["x"])
+    dx = np.minimum(dx, 1.0 - dx)
+    vscale = max(float(np.abs(st["v"]).max()), 1e-30)
+    parity = {"octree_bit_exact": tree_exact, "octree_leaves": int(ko.size),
+              "hosts_bit_exact": bool(np.array_equal(h.cpu().numpy(), host_ref)),
+              "particles_max_rel_err": float(np.abs(u.cpu().numpy() - up_ref).max() / fscale),
+              "markers_max_rel_err": float(np.abs(um.cpu().numpy() - um_ref).max() / fscale),
+              "spread_max_rel_err": float(np.abs(fs[:, :3].cpu().numpy() - f_ref[:, :3]).max() /
+                                          max(np.abs(f_ref[:, :3]).max(), 1e-300)),
+              "ab2_v_max_rel_err": float(np.abs(vs.cpu().numpy() - st["v"]).max() / vscale),
+              "ab2_x_max_abs_err": float(dx.max()),
+              "sampled_points": n_s + n_ms, "tolerance": 1e-5, "step_of_tree": tr.tree_step}
+    parity["all_ok"] = bool(tree_exact and parity["hosts_bit_exact"] and parity["particles_max_rel_err"] <= 1e-5
+                            and parity["markers_max_rel_err"] <= 1e-5 and parity["spread_max_rel_err"] <= 1e-5
+                            and parity["ab2_v_max_rel_err"] <= 1e-5)
+    return cpu, parity
 
 
 def main():
@@ -801,7 +1148,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "tracking":
-        return run_tracking(args)
+        run_tracking(args)
+        return 0
     return run_ours(args)
 
 
