@@ -389,7 +389,8 @@ typedef struct {
                           the field at every replay; a point in a level-map cell inside a hot
                           leaf reads the cell's 8-byte entry and one record instead of the
                           level-mate row and 8 scattered values; identical results.  Costs
-                          8 bytes per level-map cell and 768 bytes per hot leaf.  -1: off    */
+                          8 bytes per level-map cell and 768 bytes per hot leaf.  k > 0: the
+                          same with the hot level capped at k (a smaller record set); -1: off */
 } ot_launch;
 
 /* Create a batch over groups (copied) reading d_field (float4 per leaf).  search selects

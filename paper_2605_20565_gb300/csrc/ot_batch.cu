@@ -169,11 +169,24 @@ __global__ void __launch_bounds__(256) k_hot_records(TreeView t, const int* __re
     }
 }
 
-// 32 bytes from global memory in one load (sm_100 and later), read-only path.
-__device__ __forceinline__ void ld_nc_v8(const float* p, float* r) {
-    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+// L2 policy that keeps lines resident ahead of others (evict-last), for the reused tables.
+__device__ __forceinline__ uint64_t policy_keep() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// 32 bytes from global memory in one load (sm_100 and later), read-only path, L2 policy pol.
+__device__ __forceinline__ void ld_nc_v8(const float* p, float* r, uint64_t pol) {
+    asm("ld.global.nc.L2::cache_hint.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
         : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
-        : "l"(p));
+        : "l"(p), "l"(pol));
+}
+
+__device__ __forceinline__ uint2 ld_nc_u2(const uint2* p, uint64_t pol) {
+    uint2 e;
+    asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(e.x), "=r"(e.y) : "l"(p), "l"(pol));
+    return e;
 }
 
 // The trilinear launch with value records.  Per 32-point row: quantise, read the level-map
@@ -189,14 +202,21 @@ __global__ void __launch_bounds__(256, TRI_MINB) k_tri_rec(TreeView t, BatchArgs
     __shared__ HostQueue s_queue[256 / 32];
     __shared__ RootModel s_root;
     __shared__ long long s_cold[256 / 32][64];
+    // Morton spreading of 8-bit cell coordinates (bit b -> bit 3b): the level-map cell of a point
+    // is spread[cx] | spread[cy] << 1 | spread[cz] << 2 (map levels are at most 8)
+    __shared__ uint32_t s_spread[256];
+    for (int v = threadIdx.x; v < 256; v += blockDim.x) s_spread[v] = (uint32_t)part1by2((uint32_t)v);
     const int wid = threadIdx.x >> 5;
     HostQueue& wq = s_queue[wid];
     long long* cq = s_cold[wid];
     stage_root<LEARNED>(t, s_root);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int ent_shift = 3 * (MAXLEVEL - t.lmap_level);
+    const int cell_shift = MAXLEVEL - t.lmap_level;  // of the 21-bit coordinates
     const int64_t tile_pts = 32 * (int64_t)a.tile;
+    // the cell entries and records are read again and again: evict-last in L2; the positions
+    // and results stream through once: evict-first (.cs), so they do not push those out
+    const uint64_t keep = policy_keep();
     int qn = 0;  // queued cold points (warp-uniform)
     // the first cnt queued points, one per lane (warp-wide)
     auto drain = [&](int cnt) {
@@ -227,13 +247,16 @@ __global__ void __launch_bounds__(256, TRI_MINB) k_tri_rec(TreeView t, BatchArgs
             const int64_t i = base + (int64_t)j * 32 + lane;
             const bool active = i < gr.n;
             if (!__any_sync(0xffffffffu, active)) break;  // warp-uniform
-            const double x = active ? gr.x[i] : 0.0, y = active ? gr.y[i] : 0.0, z = active ? gr.z[i] : 0.0;
+            const double x = active ? __ldcs(gr.x + i) : 0.0, y = active ? __ldcs(gr.y + i) : 0.0,
+                         z = active ? __ldcs(gr.z + i) : 0.0;
             uint64_t X[3];
             const bool ok = active && fixpoint3(x, y, z, X);
             uint2 e = make_uint2(0u, REC_NONE);
             if (ok) {
-                const uint64_t q = morton3((uint32_t)(X[0] >> 32), (uint32_t)(X[1] >> 32), (uint32_t)(X[2] >> 32));
-                e = __ldg(ent + (q >> ent_shift));
+                const uint32_t c = s_spread[(uint32_t)(X[0] >> 32) >> cell_shift] |
+                                   (s_spread[(uint32_t)(X[1] >> 32) >> cell_shift] << 1) |
+                                   (s_spread[(uint32_t)(X[2] >> 32) >> cell_shift] << 2);
+                e = ld_nc_u2(ent + c, keep);
             }
             const bool hot = e.y != REC_NONE;
             if (hot) {
@@ -241,18 +264,18 @@ __global__ void __launch_bounds__(256, TRI_MINB) k_tri_rec(TreeView t, BatchArgs
                 const int oc = tri_octant<float>(X, (int)(e.y >> 27), at);
                 const float* rp = rec + (8 * (size_t)(e.y & 0x7FFFFFFu) + oc) * REC_FLOATS;
                 float vv[REC_FLOATS];
-                ld_nc_v8(rp, vv);
-                ld_nc_v8(rp + 8, vv + 8);
-                ld_nc_v8(rp + 16, vv + 16);
+                ld_nc_v8(rp, vv, keep);
+                ld_nc_v8(rp + 8, vv + 8, keep);
+                ld_nc_v8(rp + 16, vv + 16, keep);
                 float v[8][3];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) v[c][0] = vv[3 * c], v[c][1] = vv[3 * c + 1], v[c][2] = vv[3 * c + 2];
                 float o[3];
                 tri_sum<float>(at, v, o);
-                gr.u[i] = o[0];
-                gr.u[gr.n + i] = o[1];
-                gr.u[2 * gr.n + i] = o[2];
-                if (gr.host) gr.host[i] = (int)e.x;
+                __stcs(gr.u + i, o[0]);
+                __stcs(gr.u + gr.n + i, o[1]);
+                __stcs(gr.u + 2 * gr.n + i, o[2]);
+                if (gr.host) __stcs(gr.host + i, (int)e.x);
             } else if (active && !ok) {  // outside the cube: no host, no value
                 atomicOr(t.err, (unsigned)OT_DEV_OUTSIDE);
                 const float nan = qnan<float>();
@@ -371,7 +394,7 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
     const int tri_tile = (launch && launch->tri_tile) ? launch->tri_tile : tile;
     const int tri_per_sm = (launch && launch->tri_blocks_per_sm) ? launch->tri_blocks_per_sm : 2;
     const int tri_records = launch ? launch->tri_records : 0;
-    if (tri_records < -1 || tri_records > 1) return OT_ERR_ARG;
+    if (tri_records < -1 || tri_records > MAXLEVEL) return OT_ERR_ARG;
     if (block < 64 || block > 256 || block % 32 || tile < 1 || tile > 64) return OT_ERR_ARG;
     if (tri_tile < 1 || tri_tile > 64 || tri_per_sm < 1 || (launch && launch->blocks_per_sm < 0)) return OT_ERR_ARG;
     if (order_level < 0 || order_level > MAXLEVEL) return OT_ERR_ARG;
@@ -507,6 +530,7 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
             int hot_l = 0;
             while (hot_l < MAXLEVEL && (n_tri >> (3 * (hot_l + 1))) >= 4) ++hot_l;
             hot_l = std::min(hot_l, t->lmap_level);
+            if (tri_records > 0) hot_l = std::min(hot_l, tri_records);
             if (tri_records >= 0 && t->d_lmap) {
                 ot_status st = build_hot_records(t, hot_l, b);
                 if (st != OT_OK) {

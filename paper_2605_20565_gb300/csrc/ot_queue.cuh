@@ -373,12 +373,13 @@ __device__ __forceinline__ int tri_octant(const uint64_t X[3], int l, T at[3]) {
 // Every form of the trilinear interpolation ends here, so their results are bit-identical.
 template <typename T>
 __device__ __forceinline__ void tri_sum(const T at[3], const T v[8][3], T out[3]) {
+    // corner weight (f_0 f_1) f_2 with f_d = |t_d| or 1 - |t_d|: the four x-y products once
+    const T b0 = T(1) - at[0], b1 = T(1) - at[1], b2 = T(1) - at[2];
+    const T wxy[4] = {b0 * b1, at[0] * b1, b0 * at[1], at[0] * at[1]};
     T acc0 = T(0), acc1 = T(0), acc2 = T(0);
 #pragma unroll
     for (int corner = 0; corner < 8; ++corner) {
-        T wc = T(1);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) wc *= ((corner >> d) & 1) ? at[d] : T(1) - at[d];
+        const T wc = wxy[corner & 3] * ((corner & 4) ? at[2] : b2);
         acc0 += wc * v[corner][0];
         acc1 += wc * v[corner][1];
         acc2 += wc * v[corner][2];
