@@ -312,6 +312,12 @@ ot_status ot_spread_noalloc(const ot_octree* t, int kernel, const double* d_x, c
                             const double* d_z, const float* d_F, const float* d_dV, int64_t n, float* d_f,
                             void* stream);
 
+/* Marker force of the direct-forcing step (Sec. 2.2): F_k = (U_k - u*_k) / dt, evaluated as
+ * (U_k - u*_k) * (1 / dt) in FP32, for the interpolated velocities d_u (3 planes of n floats)
+ * and the markers' prescribed velocities d_U (3 planes, or NULL for markers at rest, U = 0);
+ * d_F: 3 planes of n floats (may alias neither input).  dt > 0.  Asynchronous on `stream`. */
+ot_status ot_marker_force(const float* d_U, const float* d_u, int64_t n, float dt, float* d_F, void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * Multi-direct forcing (Sec. 2.2): n_iter rounds of
  *   u_k = I u (Eq. ibm_interpolate, the delta kernel `kernel`),  F_k = (U_k - u_k) / dt,

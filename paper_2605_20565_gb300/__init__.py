@@ -24,7 +24,7 @@ __all__ = [
     "ot_field_mean_workspace_size", "ot_spread_workspace_size",
     "ot_spread", "ot_spread_f64", "ot_batch_create", "ot_batch_autotune", "ot_ibm_mdf", "ot_points_morton_order", "ot_field_fourier", "ot_body_sums", "ot_octree_set_periodic",
     "ot_octree_build_mates", "ot_octree_has_mates", "ot_octree_mates_bytes", "ot_octree_build_mates_in", "ot_field_subtract_mean", "ot_batch_run", "ot_batch_destroy", "ot_advect_ab2",
-    "ot_last_error", "ot_launch_count",
+    "ot_last_error", "ot_launch_count", "ot_marker_force",
 ]
 
 OT_TRILINEAR, OT_PESKIN4, OT_ROMA3 = 1, 2, 3
@@ -141,6 +141,7 @@ def _L():
                 "ot_batch_run": (st, [P, P]),
                 "ot_batch_destroy": (st, [P]),
                 "ot_advect_ab2": (st, [P, P, P, P, P, i64, C.c_float, C.c_float, C.c_float, i32, i32, P]),
+                "ot_marker_force": (st, [P, P, i64, C.c_float, P, P]),
                 "ot_last_error": (st, [P, P, i32, P]),
             }
             for name, (res, args) in sigs.items():
@@ -582,6 +583,17 @@ def ot_advect_ab2(x, v, a_prev, v_prev, u, tau: float, re_coef: float, dt: float
                               _dptr(a_prev, torch.float32, "a_prev"), _dptr(v_prev, torch.float32, "v_prev"),
                               _dptr(u, torch.float32, "u"), n, tau, re_coef, dt, int(first), int(periodic),
                               _stream(stream)))
+
+
+def ot_marker_force(u, dt: float, F=None, U=None, stream=None):
+    """F = (U - u) / dt for markers (u, U: (3, n) float32; U None: markers at rest)."""
+    torch = _torch()
+    n = u.shape[1]
+    if F is None:
+        F = torch.empty_like(u)
+    _check(_L().ot_marker_force(_dptr(U, torch.float32, "U"), _dptr(u, torch.float32, "u"), n, dt,
+                                _dptr(F, torch.float32, "F"), _stream(stream)))
+    return F
 
 
 def ot_last_error(tree: Octree, clear: bool = True, stream=None) -> int:

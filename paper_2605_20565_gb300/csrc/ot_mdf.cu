@@ -34,6 +34,13 @@ __global__ void __launch_bounds__(256) k_mdf_force(const float* __restrict__ U, 
     }
 }
 
+// F_k = (0 - u_k) / dt: markers of a body at rest.
+__global__ void __launch_bounds__(256) k_rest_force(const float* __restrict__ uk, int64_t n, float inv_dt,
+                                                    float* __restrict__ Fk) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * n; i += (int64_t)gridDim.x * blockDim.x)
+        Fk[i] = (0.0f - uk[i]) * inv_dt;
+}
+
 // u += scale F, f += F over the leaves (component 3 untouched).
 __global__ void __launch_bounds__(256) k_mdf_correct(float4* __restrict__ u, float4* __restrict__ f,
                                                      const float4* __restrict__ F, int64_t n, float scale) {
@@ -108,6 +115,20 @@ ot_status launch_mdf(const ot_octree* t, int kernel, const double* x, const doub
 } // namespace ot
 
 using namespace ot;
+
+extern "C" ot_status ot_marker_force(const float* d_U, const float* d_u, int64_t n, float dt, float* d_F,
+                                     void* stream) {
+    if (n < 0 || !(dt > 0.0f) || (n > 0 && (!d_u || !d_F))) return OT_ERR_ARG;
+    if (n == 0) return OT_OK;
+    if (d_U) {
+        k_mdf_force<<<grid_of(3 * n), 256, 0, (cudaStream_t)stream>>>(d_U, d_u, n, 1.0f / dt, d_F, nullptr);
+    } else {
+        k_rest_force<<<grid_of(3 * n), 256, 0, (cudaStream_t)stream>>>(d_u, n, 1.0f / dt, d_F);
+    }
+    count_launch();
+    OT_CUDA(cudaGetLastError());
+    return OT_OK;
+}
 
 extern "C" ot_status ot_ibm_mdf_workspace_size(const ot_octree* t, int kernel, int64_t n, int n_iter, size_t* bytes) {
     if (!t || !bytes || n < 0 || n_iter < 0 || (kernel != OT_PESKIN4 && kernel != OT_ROMA3)) return OT_ERR_ARG;

@@ -723,3 +723,21 @@ def test_field_subtract_mean(ot, tiny, torch_mod):
     assert np.abs(out[:, :3] - (f[:, :3] - ref.astype(np.float32))).max() <= 1e-6
     assert np.array_equal(out[:, 3], f[:, 3])
     assert np.abs(oracle.field_mean(lo, out.astype(np.float64))).max() <= 1e-6
+
+
+@pytest.mark.parametrize("at_rest", [False, True])
+def test_marker_force(ot, torch_mod, at_rest):
+    """Direct-forcing marker force (Sec. 2.2): F = (U - u) / dt, evaluated as (U - u) * (1/dt) in
+    FP32 -- bit for bit the same FP32 operations on the host -- and within FP32 rounding of the
+    FP64 quotient."""
+    torch = torch_mod
+    rng = np.random.default_rng(12)
+    n = 5003
+    u = rng.normal(size=(3, n)).astype(np.float32)
+    U = np.zeros_like(u) if at_rest else rng.normal(size=(3, n)).astype(np.float32)
+    dt = 0.37
+    F = ot.ot_marker_force(dev(u), dt, U=None if at_rest else dev(U)).cpu().numpy()
+    ref32 = (U - u) * (np.float32(1.0) / np.float32(dt))
+    assert np.array_equal(F, ref32)
+    ref64 = (U.astype(np.float64) - u.astype(np.float64)) / np.float64(np.float32(dt))
+    assert np.abs(F - ref64).max() <= 4e-7 * np.abs(ref64).max()
