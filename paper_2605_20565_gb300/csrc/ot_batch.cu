@@ -65,9 +65,12 @@ enum { K_ALL = 0, K_DELTA = 1, K_TRI = 2 };
 template <bool LEARNED, int MINB, bool MATES, int KINDS = K_ALL>
 __global__ void __launch_bounds__(256, MINB) k_batch(TreeView t, BatchArgs a, const float* __restrict__ field,
                                                const float* __restrict__ pyr, unsigned* __restrict__ counter) {
-    // with the table a trilinear-only launch searches hosts only: a 32-task list per warp
-    // (more of the SM's memory left to the L1 cache)
-    using Q = typename std::conditional<MATES && KINDS == K_TRI, HostQueue, WarpQueue>::type;
+    // with the table a trilinear-only launch searches hosts only: a 32-task list per warp; the
+    // delta-kernel launch needs none (one task slot): the less shared memory, the more of the
+    // SM's memory is left to the L1 cache
+    using Q = typename std::conditional<
+        KINDS == K_DELTA, WarpQueueN<1>,
+        typename std::conditional<MATES && KINDS == K_TRI, HostQueue, WarpQueue>::type>::type;
     __shared__ Q s_queue[256 / 32];
     __shared__ RootModel s_root;
     Q& wq = s_queue[threadIdx.x >> 5];
@@ -90,11 +93,17 @@ __global__ void __launch_bounds__(256, MINB) k_batch(TreeView t, BatchArgs a, co
             float o[3];
             int h;
             const double x = active ? gr.x[i] : 0.0, y = active ? gr.y[i] : 0.0, z = active ? gr.z[i] : 0.0;
-            if (KINDS != K_DELTA && (KINDS == K_TRI || gr.kernel == OT_TRILINEAR)) {
-                if constexpr (MATES)
-                    h = trilinear_mates<float, LEARNED>(t, s_root, field, pyr, wq, active, x, y, z, -1, o);
-                else
-                    h = trilinear_queued<float, LEARNED>(t, s_root, field, pyr, wq, active, x, y, z, -1, o);
+            bool tri = false;
+            if constexpr (KINDS != K_DELTA) {
+                tri = KINDS == K_TRI || gr.kernel == OT_TRILINEAR;
+                if (tri) {
+                    if constexpr (MATES)
+                        h = trilinear_mates<float, LEARNED>(t, s_root, field, pyr, wq, active, x, y, z, -1, o);
+                    else
+                        h = trilinear_queued<float, LEARNED>(t, s_root, field, pyr, wq, active, x, y, z, -1, o);
+                }
+            }
+            if (tri) {
             } else if (!active) {
                 h = -1;
             } else if (gr.kernel == OT_PESKIN4) {
@@ -199,9 +208,12 @@ __global__ void __launch_bounds__(256, TRI_MINB) k_tri_rec(TreeView t, BatchArgs
                                                           unsigned* __restrict__ counter,
                                                           const uint2* __restrict__ ent,
                                                           const float* __restrict__ rec) {
-    __shared__ HostQueue s_queue[256 / 32];
+    // per warp of the block: its host task list and its queue of cold points (dynamic shared
+    // memory sized by the block's warps: what the block does not use is left to the L1 cache)
+    extern __shared__ __align__(16) unsigned char tri_smem[];
+    HostQueue* s_queue = reinterpret_cast<HostQueue*>(tri_smem);
+    long long (*s_cold)[64] = reinterpret_cast<long long (*)[64]>(tri_smem + sizeof(HostQueue) * (blockDim.x >> 5));
     __shared__ RootModel s_root;
-    __shared__ long long s_cold[256 / 32][64];
     // Morton spreading of 8-bit cell coordinates (bit b -> bit 3b): the level-map cell of a point
     // is spread[cx] | spread[cy] << 1 | spread[cz] << 2 (map levels are at most 8)
     __shared__ uint32_t s_spread[256];
@@ -480,15 +492,16 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
         BatchArgs args;
         unsigned grid;
         bool records;  // k_tri_rec: two more arguments
+        size_t dsmem;  // dynamic shared memory per block
     };
     std::vector<Launch> launches;
-    auto add_launch = [&](void* fn, const BatchArgs& args, int cap) -> cudaError_t {
+    auto add_launch = [&](void* fn, const BatchArgs& args, int cap, size_t dsmem = 0) -> cudaError_t {
         int per_sm = 0;
-        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
+        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, dsmem);
         if (err != cudaSuccess) return err;
         if (cap > 0) per_sm = std::min(per_sm, cap);
         per_sm = std::max(per_sm, 1);
-        launches.push_back(Launch{fn, args, (unsigned)(num_sms() * per_sm), false});
+        launches.push_back(Launch{fn, args, (unsigned)(num_sms() * per_sm), false, dsmem});
         return cudaSuccess;
     };
     // every warp takes one tile number past the last tile before it stops: the 32-bit tile
@@ -542,7 +555,8 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
             void* fn = rec ? (learned ? (void*)k_tri_rec<true> : (void*)k_tri_rec<false>)
                            : (learned ? (void*)k_batch<true, TRI_MINB, true, K_TRI>
                                       : (void*)k_batch<false, TRI_MINB, true, K_TRI>);
-            if ((e = add_launch(fn, part[1], tri_per_sm)) != cudaSuccess) return fail(e);
+            const size_t dsmem = rec ? (sizeof(HostQueue) + 64 * sizeof(long long)) * (size_t)(block / 32) : 0;
+            if ((e = add_launch(fn, part[1], tri_per_sm, dsmem)) != cudaSuccess) return fail(e);
             launches.back().records = rec;
         }
     }
@@ -580,7 +594,8 @@ extern "C" ot_status ot_batch_create(const ot_octree* t, const ot_group* groups,
         unsigned* ctr = b->d_counter + i;
         void* args[] = {&v, &launches[i].args, (void*)&d_field, (void*)&b->d_pyr, &ctr, (void*)&b->d_ent,
                         (void*)&b->d_rec};
-        cap_ok = cudaLaunchKernel(launches[i].fn, dim3(launches[i].grid), dim3(block), args, smem, cs) == cudaSuccess;
+        cap_ok = cudaLaunchKernel(launches[i].fn, dim3(launches[i].grid), dim3(block), args, launches[i].dsmem, cs) ==
+                 cudaSuccess;
         count_launch();
     }
     for (size_t i = 0; cap_ok && i < ordered.size(); ++i) {
