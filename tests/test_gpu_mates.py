@@ -169,17 +169,21 @@ def test_batch_bit_identical_every_shape(ot, deep, search):
 
 
 @pytest.mark.parametrize("search", [0, 1])
-@pytest.mark.parametrize("map_level", [5, 7])
-def test_value_records_bit_identical(ot, deep, search, map_level):
+@pytest.mark.parametrize("map_level,periodic", [(5, False), (7, False), (7, True)])
+def test_value_records_bit_identical(ot, deep, search, map_level, periodic):
     """Uniform points (most of them in coarse leaves, which get value records) give the same
-    results with and without the records, in the caller's order and Morton-ordered, and match
-    the oracle; points outside the cube get no host and NaN values either way."""
+    results with the records (hot level set by the point count, and capped at 1, 3 and 4) and
+    without them, in the caller's order and Morton-ordered, over two replays, and match the
+    oracle (periodic cube too: the octant's neighbour wraps); points outside the cube get no
+    host and NaN values either way."""
     import torch
     sph, ko, lo, _, field = deep
     t = ot.ot_octree_build(sph, 3, 9)
     ot.ot_octree_set_map_level(t, map_level)
     if search == 1:
         ot.ot_index_train(t, root=ot.OT_ROOT_MLP, n_leaf_models=4096, epochs=1, batch=16384)
+    if periodic:
+        ot.ot_octree_set_periodic(t, True)
     ot.ot_octree_build_mates(t, True)
     rng = np.random.default_rng(77)
     P = np.concatenate([rng.uniform(0, 1, (300000, 3)), face_points(ko, lo, rng, 4000),
@@ -187,26 +191,31 @@ def test_value_records_bit_identical(ot, deep, search, map_level):
     x, y, z = pts(P.T)
     f32 = dev(field.astype(np.float32))
     outs = []
-    for lp in (dict(tri_records=-1), dict(), dict(tile=8, tri_tile=4), dict(order_level=6)):
+    shapes = [dict(tri_records=-1), dict(), dict(tile=8, tri_tile=4), dict(order_level=6)]
+    shapes += [dict(tri_records=k) for k in (1, 3, 4)]
+    for lp in shapes:
         up = torch.full((3, P.shape[0]), 7.0, device="cuda")
         hp = torch.full((P.shape[0],), -5, dtype=torch.int32, device="cuda")
         b = ot.ot_batch_create(t, [dict(kernel=ot.OT_TRILINEAR, x=x, y=y, z=z, u=up, host=hp)], f32, search=search,
                                launch=lp)
         ot.ot_batch_run(b)
+        ot.ot_batch_run(b)  # a second replay: means and records recomputed over the same buffers
         torch.cuda.synchronize()
         ot.ot_batch_destroy(b)
         outs.append((up, hp))
-    for up, hp in outs[1:]:
-        assert torch.equal(hp, outs[0][1])
-        assert torch.equal(up.isnan(), outs[0][0].isnan())
-        assert torch.equal(torch.nan_to_num(up, nan=0.0), torch.nan_to_num(outs[0][0], nan=0.0))
+    for (up, hp), lp in zip(outs[1:], shapes[1:]):
+        assert torch.equal(hp, outs[0][1]), lp
+        assert torch.equal(up.isnan(), outs[0][0].isnan()), lp
+        assert torch.equal(torch.nan_to_num(up, nan=0.0), torch.nan_to_num(outs[0][0], nan=0.0)), lp
     hp = outs[1][1].cpu().numpy()
     href = oracle.locate_ub(ko, lo, *P.T)
     assert np.array_equal(hp, href)
     inside = href >= 0
     assert inside.sum() == P.shape[0] - 3
-    ref = oracle.interp_trilinear(ko, lo, field.astype(np.float32).astype(np.float64), *P[inside].T, href[inside])
-    assert rel_err(outs[1][0].cpu().numpy()[:, inside], ref) <= TOL32
+    ref = oracle.interp_trilinear(ko, lo, field.astype(np.float32).astype(np.float64), *P[inside].T, href[inside],
+                                  periodic=periodic)
+    for up, _ in outs:
+        assert rel_err(up.cpu().numpy()[:, inside], ref) <= TOL32
     assert torch.isnan(outs[1][0][:, ~torch.as_tensor(inside, device="cuda")]).all()
 
 
