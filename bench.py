@@ -136,10 +136,10 @@ def kernel_sources_hash() -> str:
 
 
 def batch_traffic(workload: str, form: str, map_level: int, mates: bool):
-    """DRAM bytes of one batch graph replay (every kernel in it) from the committed ncu summary,
-    when it was taken on this workload, form, level map and level-mate form with the current
-    kernel sources; else (None, reason)."""
-    path = os.path.join(ROOT, "profiles", f"k_batch_{workload.split('_l')[0]}_traffic.txt")
+    """DRAM bytes of one replay of the particles' graph (every kernel in it) from the committed
+    ncu summary, when it was taken on this workload, form, level map and level-mate form with
+    the current kernel sources; else (None, reason)."""
+    path = os.path.join(ROOT, "profiles", f"particles_graph_{workload.split('_l')[0]}_traffic.txt")
     if not os.path.exists(path):
         return None, "no capture"
     d = {}

@@ -51,7 +51,7 @@ def test_launch_record_round_trip():
 def test_traffic_summary_is_read_only_for_its_own_capture():
     sys.path.insert(0, ROOT)
     import bench
-    path = os.path.join(ROOT, "profiles", "k_batch_many_bubbles_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "particles_graph_many_bubbles_traffic.txt")
     fields = dict(line.split(":", 1) for line in open(path) if ":" in line and not line.startswith("#"))
     fields = {k.strip(): v.strip() for k, v in fields.items()}
     assert int(fields["bytes_per_replay"]) == int(fields["dram_bytes_read"]) + int(fields["dram_bytes_write"])
@@ -64,6 +64,6 @@ def test_traffic_summary_is_read_only_for_its_own_capture():
     assert bench.batch_traffic(wl, form, lvl, not mates)[0] is None
     value, source = bench.batch_traffic(wl, form, lvl, mates)
     if fields["kernel_sources_sha256"] == bench.kernel_sources_hash():
-        assert value == int(fields["bytes_per_replay"]) and source.endswith("k_batch_many_bubbles_traffic.txt")
+        assert value == int(fields["bytes_per_replay"]) and source.endswith("particles_graph_many_bubbles_traffic.txt")
     else:  # sources edited since the capture: reported as unknown, never stale
         assert value is None and "changed" in source
