@@ -178,10 +178,15 @@ __global__ void __launch_bounds__(256) k_hot_records(TreeView t, const int* __re
     }
 }
 
-// L2 policy that keeps lines resident ahead of others (evict-last), for the reused tables.
+// L2 policies: keep lines resident ahead of others (evict-last), or the default priority.
 __device__ __forceinline__ uint64_t policy_keep() {
     uint64_t pol;
     asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t policy_normal() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
 
@@ -226,9 +231,11 @@ __global__ void __launch_bounds__(256, TRI_MINB) k_tri_rec(TreeView t, BatchArgs
     const unsigned lt = (1u << lane) - 1u;
     const int cell_shift = MAXLEVEL - t.lmap_level;  // of the 21-bit coordinates
     const int64_t tile_pts = 32 * (int64_t)a.tile;
-    // the cell entries and records are read again and again: evict-last in L2; the positions
-    // and results stream through once: evict-first (.cs), so they do not push those out
-    const uint64_t keep = policy_keep();
+    // the cell entries (16 MB at map level 7) are read by every point: evict-last in L2; the
+    // records (about 100 MB) at the default priority (evict-last on them as well measured 3%
+    // slower on the many-bubble step, evict-first 15% slower); the positions and results
+    // stream through once: evict-first (.cs), so they push out neither
+    const uint64_t keep = policy_keep(), normal = policy_normal();
     int qn = 0;  // queued cold points (warp-uniform)
     // the first cnt queued points, one per lane (warp-wide)
     auto drain = [&](int cnt) {
@@ -276,9 +283,9 @@ __global__ void __launch_bounds__(256, TRI_MINB) k_tri_rec(TreeView t, BatchArgs
                 const int oc = tri_octant<float>(X, (int)(e.y >> 27), at);
                 const float* rp = rec + (8 * (size_t)(e.y & 0x7FFFFFFu) + oc) * REC_FLOATS;
                 float vv[REC_FLOATS];
-                ld_nc_v8(rp, vv, keep);
-                ld_nc_v8(rp + 8, vv + 8, keep);
-                ld_nc_v8(rp + 16, vv + 16, keep);
+                ld_nc_v8(rp, vv, normal);
+                ld_nc_v8(rp + 8, vv + 8, normal);
+                ld_nc_v8(rp + 16, vv + 16, normal);
                 float v[8][3];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) v[c][0] = vv[3 * c], v[c][1] = vv[3 * c + 1], v[c][2] = vv[3 * c + 2];
