@@ -240,74 +240,101 @@ __global__ void __launch_bounds__(256) k_spread_emit_rec(TreeView t, const doubl
     }
 }
 
-// Reduce pass over the sorted pairs (chunk ownership as k_spread_reduce), reading each pair's
-// marker record instead of recomputing its weights: a child (cx, cy, cz) of parent slot
-// (bx, by, bz) is stencil cell 2 b + c - parity on each axis.  Same products, same order: the
-// result is bit-identical to k_spread_reduce's.
+// Reduce pass over the sorted pairs, reading each pair's marker record instead of recomputing
+// its weights: a child (cx, cy, cz) of parent slot (bx, by, bz) is stencil cell 2 b + c - parity
+// on each axis.  Same products, same order as k_spread_reduce: the result is bit-identical.
+// Work split: runs (all pairs of one parent block) average ~50 pairs (1 to ~100), so instead
+// of a thread per fixed chunk (idle when no run starts in it) every warp owns an equal range
+// of the sorted pairs, lists the runs that start in it (32 pairs per ballot) and hands them
+// to its lanes round-robin in batches of up to 128, each lane reducing whole runs in order
+// (reading past the range's end to finish its last one).
+constexpr int RB = 128;  // run heads per warp batch
+
+template <typename T, int K>
+__device__ __forceinline__ void reduce_run(const uint64_t* __restrict__ pairs, int64_t npairs, int64_t j,
+                                           const MarkerRec<T>* __restrict__ recs, T* __restrict__ f) {
+    constexpr int W = Stencil<K>::W;
+    constexpr int PW = ParentSlots<K>::PW, PS = ParentSlots<K>::PS;
+    const uint32_t a0 = (uint32_t)(pairs[j] >> 32);
+    T acc[8][3];
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) acc[ch][0] = acc[ch][1] = acc[ch][2] = T(0);
+    unsigned touched = 0;
+    for (; j < npairs; ++j) {
+        const uint64_t pj = pairs[j];
+        if ((uint32_t)(pj >> 32) != a0) break;
+        const uint32_t id = (uint32_t)pj;
+        const int64_t k = id / PS;
+        const int sl = (int)(id - (uint32_t)(k * PS));
+        const MarkerRec<T> r = recs[k];
+        const int b[3] = {sl % PW, (sl / PW) % PW, sl / (PW * PW)};
+        // per axis, the two children's stencil cells 2 b + e - parity (register selects)
+        T wa[3][2];
+        bool va[3][2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int cc = 2 * b[d] + e - ((r.par >> d) & 1);
+                va[d][e] = cc >= 0 && cc < W;
+                wa[d][e] = cc == 1 ? r.w[d][1] : cc == 2 ? r.w[d][2] : cc == 3 ? r.w[d][3] : r.w[d][0];
+            }
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+            const int ex = ch & 1, ey = (ch >> 1) & 1, ez = (ch >> 2) & 1;
+            if (!(va[0][ex] && va[1][ey] && va[2][ez])) continue;
+            const T wt = wa[0][ex] * wa[1][ey] * wa[2][ez];
+            acc[ch][0] += r.F[0] * wt;
+            acc[ch][1] += r.F[1] * wt;
+            acc[ch][2] += r.F[2] * wt;
+            touched |= 1u << ch;
+        }
+    }
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+        if (!((touched >> ch) & 1u)) continue;
+        T* fp = f + 4 * ((size_t)a0 + ch);
+        fp[0] += acc[ch][0];
+        fp[1] += acc[ch][1];
+        fp[2] += acc[ch][2];
+    }
+}
+
 template <typename T, int K>
 __global__ void __launch_bounds__(256) k_spread_reduce_rec(const uint64_t* __restrict__ pairs,
                                                            const uint32_t* __restrict__ d_np,
                                                            const MarkerRec<T>* __restrict__ recs,
                                                            T* __restrict__ f) {
-    constexpr int W = Stencil<K>::W;
-    constexpr int PW = ParentSlots<K>::PW, PS = ParentSlots<K>::PS;
+    __shared__ uint32_t s_heads[256 / 32][RB];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t* heads = s_heads[threadIdx.x >> 5];
     const int64_t npairs = *d_np;
-    const int64_t nchunks = (npairs + RC - 1) / RC;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t j = c * RC;
-        const int64_t jend = min(j + RC, npairs);
-        if (j > 0) {  // the run in progress at the chunk start belongs to an earlier chunk
-            const uint32_t prev = (uint32_t)(pairs[j - 1] >> 32);
-            while (j < jend && (uint32_t)(pairs[j] >> 32) == prev) ++j;
-        }
-        while (j < jend) {
-            const uint32_t a0 = (uint32_t)(pairs[j] >> 32);
-            if (a0 == (uint32_t)INVALID_HI) break;  // invalid pairs sort last
-            T acc[8][3];
-#pragma unroll
-            for (int ch = 0; ch < 8; ++ch) acc[ch][0] = acc[ch][1] = acc[ch][2] = T(0);
-            unsigned touched = 0;
-            for (; j < npairs; ++j) {
-                const uint64_t pj = pairs[j];
-                if ((uint32_t)(pj >> 32) != a0) break;
-                const uint32_t id = (uint32_t)pj;
-                const int64_t k = id / PS;
-                const int sl = (int)(id - (uint32_t)(k * PS));
-                const MarkerRec<T> r = recs[k];
-                const int b[3] = {sl % PW, (sl / PW) % PW, sl / (PW * PW)};
-                // per axis, the two children's stencil cells 2 b + e - parity (register selects)
-                T wa[3][2];
-                bool va[3][2];
-#pragma unroll
-                for (int d = 0; d < 3; ++d)
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int cc = 2 * b[d] + e - ((r.par >> d) & 1);
-                        va[d][e] = cc >= 0 && cc < W;
-                        wa[d][e] = cc == 1 ? r.w[d][1] : cc == 2 ? r.w[d][2] : cc == 3 ? r.w[d][3] : r.w[d][0];
-                    }
-#pragma unroll
-                for (int ch = 0; ch < 8; ++ch) {
-                    const int ex = ch & 1, ey = (ch >> 1) & 1, ez = (ch >> 2) & 1;
-                    if (!(va[0][ex] && va[1][ey] && va[2][ez])) continue;
-                    const T wt = wa[0][ex] * wa[1][ey] * wa[2][ez];
-                    acc[ch][0] += r.F[0] * wt;
-                    acc[ch][1] += r.F[1] * wt;
-                    acc[ch][2] += r.F[2] * wt;
-                    touched |= 1u << ch;
-                }
-            }
-#pragma unroll
-            for (int ch = 0; ch < 8; ++ch) {
-                if (!((touched >> ch) & 1u)) continue;
-                T* fp = f + 4 * ((size_t)a0 + ch);
-                fp[0] += acc[ch][0];
-                fp[1] += acc[ch][1];
-                fp[2] += acc[ch][2];
-            }
-        }
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t wg = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t j0 = npairs * wg / nwarps, j1 = npairs * (wg + 1) / nwarps;
+    int nh = 0;  // listed run heads (warp-uniform)
+    auto run_batch = [&]() {
+        __syncwarp();
+        for (int r = lane; r < nh; r += 32) reduce_run<T, K>(pairs, npairs, (int64_t)heads[r], recs, f);
+        __syncwarp();
+        nh = 0;
+    };
+    bool tail = false;  // invalid pairs (blocks outside the cube or not refined) sort last
+    for (int64_t base = j0; base < j1 && !tail; base += 32) {
+        const int64_t j = base + lane;
+        uint32_t a = (uint32_t)INVALID_HI;
+        if (j < j1) a = (uint32_t)(pairs[j] >> 32);
+        uint32_t prev = __shfl_up_sync(0xffffffffu, a, 1);
+        if (lane == 0) prev = j > 0 ? (uint32_t)(pairs[j - 1] >> 32) : (uint32_t)INVALID_HI;
+        const bool head = j < j1 && a != (uint32_t)INVALID_HI && (j == 0 || a != prev);
+        tail = __any_sync(0xffffffffu, j < j1 && a == (uint32_t)INVALID_HI);
+        const unsigned m = __ballot_sync(0xffffffffu, head);
+        if (head) heads[nh + __popc(m & lt)] = (uint32_t)j;
+        nh += __popc(m);
+        if (nh > RB - 32) run_batch();
     }
+    if (nh > 0) run_batch();
 }
 
 template <typename Kern>
@@ -371,7 +398,7 @@ ot_status spread_sorted(const ot_octree* t, const double* x, const double* y, co
     uint64_t* sorted = pairs;
     if ((st = radix_sort_u64_dn(pairs, tmp, np, d_np, 35, 32 + bits, rws, &sorted, s)) != OT_OK) return st;
     auto kr = k_spread_reduce_rec<T, K>;
-    kr<<<grid_for(kr, 256, 0, (np + RC - 1) / RC), 256, 0, s>>>(sorted, d_np, recs, f);
+    kr<<<grid_for(kr, 256, 0, (np + RC - 1) / RC), 256, 0, s>>>(sorted, d_np, recs, f);  // warps split the pairs
     count_launch();
     OT_CUDA(cudaGetLastError());
     return OT_OK;
