@@ -246,9 +246,9 @@ __global__ void __launch_bounds__(256) k_spread_emit_rec(TreeView t, const doubl
 // Work split: runs (all pairs of one parent block) average ~50 pairs (1 to ~100), so instead
 // of a thread per fixed chunk (idle when no run starts in it) every warp owns an equal range
 // of the sorted pairs, lists the runs that start in it (32 pairs per ballot) and hands them
-// to its lanes round-robin in batches of up to 128, each lane reducing whole runs in order
+// to its lanes round-robin in batches of up to 256, each lane reducing whole runs in order
 // (reading past the range's end to finish its last one).
-constexpr int RB = 128;  // run heads per warp batch
+constexpr int RB = 256;  // run heads per warp batch
 
 template <typename T, int K>
 __device__ __forceinline__ void reduce_run(const uint64_t* __restrict__ pairs, int64_t npairs, int64_t j,
