@@ -299,8 +299,8 @@ ot_status ot_spread_f64(const ot_octree* t, int kernel, int mode, const double* 
  * device, or code that must not risk an allocation's synchronisation or failure mid-step).
  * Same result as ot_spread(kernel, OT_SORTED, ...) for FP32: d_f is accumulated, d_dV may be
  * NULL.  The scratch is a fixed library array of OT_NOALLOC_SCRATCH_BYTES per device; it
- * holds about 459 bytes per marker for OT_PESKIN4 (at most 146,202 markers) and 136 bytes per
- * marker for OT_ROMA3 (at most 493,432); larger n returns OT_ERR_LIMIT and launches nothing.
+ * holds about 446 bytes per marker for OT_PESKIN4 (at most 150,635 markers) and 132 bytes per
+ * marker for OT_ROMA3 (at most 508,394); larger n returns OT_ERR_LIMIT and launches nothing.
  * The first call on a device (with that device current) looks up the scratch address; make
  * that first call before any stream capture.  The address is looked up again when the device's
  * context changed (after cudaDeviceReset, say): make the first call after such a change

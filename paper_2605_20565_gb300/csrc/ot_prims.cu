@@ -143,7 +143,7 @@ ot_status scan_u32(const uint32_t* d_in, uint32_t* d_out, int64_t n, uint32_t* d
 // round r thread t owns element r*RT + t, so (round, warp, lane) order is input order and the
 // scatter ranks each element after every earlier element of the tile with the same digit.
 // ------------------------------------------------------------------------------------------
-constexpr int RT = 256, RI = 8, RTILE = RT * RI, RW = RT / 32;
+constexpr int RT = 256, RI = 16, RTILE = RT * RI, RW = RT / 32;
 
 // d_n (nullable): the element count in device memory, at most n (tiles past it stay empty).
 __global__ void k_radix_hist(const uint64_t* __restrict__ in, int64_t n, int shift, uint32_t mask,

@@ -12,7 +12,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-5
-MAX_MARKERS = {2: 146_202, 3: 493_432}  # the limits stated in include/octtrack.h
+MAX_MARKERS = {2: 150_635, 3: 508_394}  # the limits stated in include/octtrack.h
 
 
 @pytest.fixture(scope="module")
