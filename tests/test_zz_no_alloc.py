@@ -103,3 +103,41 @@ def test_noalloc_refuses_sizes_beyond_its_scratch(env):
     too_many = 10_000_000  # far beyond the fixed scratch; refused before any launch
     assert fn(tree.handle, 2, p(x), p(x), p(x), p(F), None, too_many, p(f), s) == -8
     assert fn(tree.handle, 1, p(x), p(x), p(x), p(F), None, 1, p(f), s) == -1  # trilinear has no spreading
+
+
+@pytest.mark.parametrize("case", ["one_block", "small_1", "small_2", "small_33", "with_coarse"])
+def test_noalloc_and_sorted_agree_on_run_edge_cases(env, case):
+    """The allocating sorted spreading splits the sorted pairs into equal shares per warp and
+    deals the parent-block runs that start in each share to its lanes; the allocation-free one
+    reduces fixed chunks with the weights recomputed.  They must agree bit for bit where that
+    split is stressed -- runs far longer than a warp's share (20,000 markers on one spot:
+    every pair in the same few blocks), fewer pairs than warps (1, 2, 33 markers), and pairs
+    of blocks that are not refined to the finest level (sorted last, dropped) -- and both must
+    match the oracle."""
+    import oracle
+    torch, ot, fn, w, tree = env
+    n_leaves = ot.ot_octree_info(tree)[0]
+    rng = np.random.default_rng(7)
+    m0 = w.markers[:, :1]
+    if case == "one_block":
+        Xh = m0 + rng.uniform(-1e-7, 1e-7, (3, 20000))
+    elif case.startswith("small_"):
+        Xh = w.markers[:, :int(case.split("_")[1])]
+    else:  # a third of the markers near a corner of the cube, where the tree is coarse
+        Xh = np.concatenate([w.markers[:, :600], rng.uniform(0.0, 0.05, (3, 300))], axis=1)
+    Xh = np.ascontiguousarray(Xh)
+    X = [torch.as_tensor(np.ascontiguousarray(Xh[d]), device="cuda") for d in range(3)]
+    n = Xh.shape[1]
+    F = torch.as_tensor(rng.normal(size=(3, n)).astype(np.float32), device="cuda")
+    ref = torch.zeros((n_leaves, 4), dtype=torch.float32, device="cuda")
+    ot.ot_spread(tree, 2, ot.OT_SORTED, X[0], X[1], X[2], F, ref)
+    f = torch.zeros_like(ref)
+    assert _call(torch, fn, tree, 2, X, F, None, f) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(f, ref)
+    ot.ot_last_error(tree, clear=True)
+    ko, lo = oracle.octree_build(w.spheres, w.lmin, w.lmax)
+    f_ref, bad = oracle.spread_delta(ko, lo, w.lmax, 2, *Xh, F.double().cpu().numpy())
+    assert (bad > 0) == (case == "with_coarse")
+    scale = float(np.abs(f_ref[:, :3]).max())
+    assert float(np.abs(ref.cpu().numpy()[:, :3] - f_ref[:, :3]).max()) <= TOL32 * scale
