@@ -306,17 +306,52 @@ __global__ void __launch_bounds__(256) k_spread_reduce_rec(const uint64_t* __res
                                                            const MarkerRec<T>* __restrict__ recs,
                                                            T* __restrict__ f) {
     __shared__ uint32_t s_heads[256 / 32][RB];
+    __shared__ uint32_t s_len[256 / 32][RB];
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t* heads = s_heads[threadIdx.x >> 5];
+    uint32_t* len = s_len[threadIdx.x >> 5];
     const int64_t npairs = *d_np;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t wg = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t j0 = npairs * wg / nwarps, j1 = npairs * (wg + 1) / nwarps;
     int nh = 0;  // listed run heads (warp-uniform)
-    auto run_batch = [&]() {
+    // the listed runs, longest first (lengths up to the scan position end; the last one's is a
+    // lower bound), dealt to the lanes in snake order so that every lane gets about the same
+    // number of pairs
+    auto run_batch = [&](int64_t end) {
         __syncwarp();
-        for (int r = lane; r < nh; r += 32) reduce_run<T, K>(pairs, npairs, (int64_t)heads[r], recs, f);
+        int P = 32;
+        while (P < nh) P <<= 1;
+        for (int r = lane; r < P; r += 32) {
+            if (r < nh) {
+                const int64_t e = r + 1 < nh ? (int64_t)heads[r + 1] : end;
+                const int64_t l_ = e - (int64_t)heads[r];
+                len[r] = (uint32_t)(l_ > 1 ? l_ : 1);
+            } else {
+                len[r] = 0;
+            }
+        }
+        __syncwarp();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int i = lane; i < P; i += 32) {
+                    const int ix = i ^ jj;
+                    if (ix > i) {
+                        const uint32_t li = len[i], lx = len[ix];
+                        if (((i & k) == 0) ? (li < lx) : (li > lx)) {
+                            len[i] = lx, len[ix] = li;
+                            const uint32_t h = heads[i];
+                            heads[i] = heads[ix], heads[ix] = h;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        for (int q = 0; q * 32 < nh; ++q) {
+            const int r = q * 32 + ((q & 1) ? 31 - lane : lane);
+            if (r < nh) reduce_run<T, K>(pairs, npairs, (int64_t)heads[r], recs, f);
+        }
         __syncwarp();
         nh = 0;
     };
@@ -332,9 +367,9 @@ __global__ void __launch_bounds__(256) k_spread_reduce_rec(const uint64_t* __res
         const unsigned m = __ballot_sync(0xffffffffu, head);
         if (head) heads[nh + __popc(m & lt)] = (uint32_t)j;
         nh += __popc(m);
-        if (nh > RB - 32) run_batch();
+        if (nh > RB - 32) run_batch(base + 32);
     }
-    if (nh > 0) run_batch();
+    if (nh > 0) run_batch(j1);
 }
 
 template <typename Kern>
