@@ -175,6 +175,34 @@ struct __align__(16) MarkerRec {
     int par;  // bit d: i0[d] & 1
 };
 
+// A marker's record in two 32-byte loads (sm_100 and later; FP32 records are 64 bytes and
+// 64-byte aligned in the workspace), read-only path, default L2 priority; FP64 records whole.
+template <typename T>
+__device__ __forceinline__ MarkerRec<T> load_rec(const MarkerRec<T>* p) {
+    return *p;
+}
+template <>
+__device__ __forceinline__ MarkerRec<float> load_rec<float>(const MarkerRec<float>* p) {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+    float v[16];
+    const float* q = reinterpret_cast<const float*>(p);
+    asm("ld.global.nc.L2::cache_hint.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(q), "l"(pol));
+    asm("ld.global.nc.L2::cache_hint.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+        : "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
+        : "l"(q + 8), "l"(pol));
+    MarkerRec<float> r;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) r.w[d][a] = v[4 * d + a];
+    r.F[0] = v[12], r.F[1] = v[13], r.F[2] = v[14];
+    r.par = __float_as_int(v[15]);
+    return r;
+}
+
 // Parent blocks overlapping a marker's stencil (2 or 3 per axis for Peskin-4, by the parity
 // of the stencil's first cell); 0 outside the cube.
 template <int K>
@@ -266,7 +294,7 @@ __device__ __forceinline__ void reduce_run(const uint64_t* __restrict__ pairs, i
         const uint32_t id = (uint32_t)pj;
         const int64_t k = id / PS;
         const int sl = (int)(id - (uint32_t)(k * PS));
-        const MarkerRec<T> r = recs[k];
+        const MarkerRec<T> r = load_rec<T>(recs + k);
         const int b[3] = {sl % PW, (sl / PW) % PW, sl / (PW * PW)};
         // per axis, the two children's stencil cells 2 b + e - parity (register selects)
         T wa[3][2];
@@ -409,6 +437,8 @@ ot_status spread_sorted(const ot_octree* t, const double* x, const double* y, co
     const size_t smem = 0;
     ot_status st;
     char* p = static_cast<char*>(rws) + align_up(radix_ws_bytes(np));
+    // records 64-byte aligned (the reduce reads an FP32 record as two 32-byte loads)
+    p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 63) & ~(uintptr_t)63);
     MarkerRec<T>* recs = reinterpret_cast<MarkerRec<T>*>(p);
     p += align_up((size_t)n * sizeof(MarkerRec<double>));
     uint32_t* cnt = reinterpret_cast<uint32_t*>(p);
@@ -445,7 +475,7 @@ size_t spread_ws_bytes(const ot_octree* t, int kernel, int64_t n) {
     (void)t;
     const int64_t np = n * stencil_cells(kernel);
     return (size_t)np * 16 + align_up(radix_ws_bytes(np)) + align_up((size_t)n * sizeof(MarkerRec<double>)) +
-           2 * align_up((size_t)n * sizeof(uint32_t)) + 256 + align_up(scan_ws_bytes(n)) + 512;
+           2 * align_up((size_t)n * sizeof(uint32_t)) + 256 + align_up(scan_ws_bytes(n)) + 512 + 64;
 }
 
 template <typename T>
