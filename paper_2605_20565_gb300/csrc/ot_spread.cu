@@ -284,6 +284,15 @@ __device__ __forceinline__ void reduce_run(const uint64_t* __restrict__ pairs, i
     constexpr int W = Stencil<K>::W;
     constexpr int PW = ParentSlots<K>::PW, PS = ParentSlots<K>::PS;
     const uint32_t a0 = (uint32_t)(pairs[j] >> 32);
+    // the 8 children's lines of f, fetched into L2 now: the read-modify-write at the run's end
+    // then hits L2 instead of waiting on DRAM (runs are short on trees with many markers)
+    {
+        const char* fa = reinterpret_cast<const char*>(f + 4 * (size_t)a0);
+        constexpr int span = 8 * 4 * (int)sizeof(T);
+#pragma unroll
+        for (int o = 0; o < span; o += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(fa + o));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(fa + span - 1));
+    }
     T acc[8][3];
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) acc[ch][0] = acc[ch][1] = acc[ch][2] = T(0);
