@@ -704,7 +704,7 @@ def measure_e2e(args, ctx, w, tree, field, form_cfg, groups_for, step, batch, M,
     n_leaves = f.shape[0]
     h2d = sum(t.numel() * t.element_size() for t in hmk + hpt + [hF])
     d2h = (um.numel() + up.numel() + f.numel()) * 4 + (hm.numel() + hp.numel()) * 4
-    k_e2e = 3 if light else max(3, min(args.steps, 10))
+    k_e2e = max(3, min(args.steps, 10))  # a few steps: one slow host-side step would skew fewer
 
     def outs_host():
         return (torch.empty((3, n_m), dtype=torch.float32).pin_memory(),
