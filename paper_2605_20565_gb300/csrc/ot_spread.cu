@@ -370,7 +370,8 @@ __global__ void __launch_bounds__(256) k_spread_reduce_rec(const uint64_t* __res
             }
         }
         __syncwarp();
-        for (int k = 2; k <= P; k <<= 1)
+        // (with at most one run per lane there is nothing to balance)
+        for (int k = 2; nh > 32 && k <= P; k <<= 1)
             for (int jj = k >> 1; jj > 0; jj >>= 1) {
                 for (int i = lane; i < P; i += 32) {
                     const int ix = i ^ jj;
