@@ -69,7 +69,7 @@ def parse():
                    help="search the trilinear level-mates per query instead of reading the level-mate table")
     p.add_argument("--only", action="store_true",
                    help="the headline workload only (no compact lines of the other workloads)")
-    p.add_argument("--workloads", default="single_bubble,learned_index,tracking",
+    p.add_argument("--workloads", default="tiny,single_bubble,learned_index,tracking",
                    help="the other workloads measured after the many-bubble headline (compact lines)")
     p.add_argument("--tracking-steps", type=int, default=100, help="timed steps of the tracking workload")
     return p.parse_args()
