@@ -141,3 +141,32 @@ def test_noalloc_and_sorted_agree_on_run_edge_cases(env, case):
     assert (bad > 0) == (case == "with_coarse")
     scale = float(np.abs(f_ref[:, :3]).max())
     assert float(np.abs(ref.cpu().numpy()[:, :3] - f_ref[:, :3]).max()) <= TOL32 * scale
+
+
+def test_noalloc_and_sorted_agree_with_many_runs_per_warp(env):
+    """150,000 markers scattered through the single bubble's finest shell: about 2M pairs in
+    short runs, hundreds of runs per warp share, so the allocating reduce sorts each batch of run
+    heads by length before dealing it to the lanes.  Bit for bit against the allocation-free
+    reduce, which splits the same pairs into fixed chunks instead."""
+    torch, ot, fn, _, _ = env
+    from paper_2605_20565_gb300 import synth
+    wb = synth.single_bubble(n_markers=10, n_particles=10)
+    tree = ot.ot_octree_build(wb.spheres, wb.lmin, wb.lmax)
+    n_leaves = ot.ot_octree_info(tree)[0]
+    c, r, shell = wb.spheres[0, :3], wb.spheres[0, 3], wb.spheres[0, 4]
+    rng = np.random.default_rng(11)
+    n = 150_000
+    d = rng.normal(size=(3, n))
+    d /= np.linalg.norm(d, axis=0)
+    Xh = np.ascontiguousarray(c[:, None] + d * (r + rng.uniform(-0.4, 0.4, n) * shell))
+    assert np.all((Xh > 0) & (Xh < 1))
+    X = [torch.as_tensor(np.ascontiguousarray(Xh[k]), device="cuda") for k in range(3)]
+    F = torch.as_tensor(rng.normal(size=(3, n)).astype(np.float32), device="cuda")
+    ref = torch.zeros((n_leaves, 4), dtype=torch.float32, device="cuda")
+    ot.ot_spread(tree, 2, ot.OT_SORTED, X[0], X[1], X[2], F, ref)
+    f = torch.zeros_like(ref)
+    assert _call(torch, fn, tree, 2, X, F, None, f) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(f, ref)
+    assert ot.ot_last_error(tree) & ot.OT_DEV_STENCIL == 0
+    assert float(ref[:, :3].abs().sum()) > 0
